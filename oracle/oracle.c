@@ -1,0 +1,792 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the potential and field of charged
+ * constant-density BEM triangles and rectangles (Glueck & Hilk,
+ * "Electric potential and field calculation of charged BEM triangles and
+ * rectangles by Gaussian cubature", arXiv:1606.03743).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark load this file.  It shares
+ * no code, header, table or constant with the CUDA library: every number
+ * below is typed in here from the paper's appendix tables, and every formula
+ * is written out from the equation or section it cites.
+ *
+ * It is deliberately plain: one field point at a time, every element in
+ * index order, every step in the paper's order and notation, double
+ * precision throughout (the paper's own arithmetic, Sec. 2 and Sec. 6).
+ * The only parallelism is over independent field points, which does not
+ * change any per-point arithmetic.
+ *
+ * Layers (the paper's):
+ *   rule tables ........ App. A (Tables A1-A5), App. B (Tables B1-B5)
+ *   natural coords ..... Eq. 3.2 (rectangle), Eq. 3.3 (barycentric, triangle)
+ *   cubature formula ... Eq. 3.1
+ *   point charges ...... Eq. 4.1
+ *   distance ratio ..... Sec. 2 (DR = D / L)
+ *   rule bands ......... Sec. 4 (DR-banded choice, analytic below DR = 3)
+ *   analytic near field  Sec. 2 cites it without printing it; written here
+ *                        from the divergence-theorem decomposition of a
+ *                        uniformly charged planar polygon (edge logarithms
+ *                        plus the solid angle, Van Oosterom & Strackee 1983).
+ *   GL2 reference ...... Sec. 2 (two nested 16-node Gauss-Legendre rules)
+ *
+ * Pinned by tests/test_oracle_*.py against what the paper and mathematics
+ * fix (rule exactness, closed forms, point-charge limit, E = -grad phi,
+ * brute-force subdivision, Gauss's law, symmetry, the paper's printed rule
+ * bands).  Nothing here is "parity unpinned".
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                */
+/* ------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void sub3(const double a[3], const double b[3], double o[3]) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+
+/* ------------------------------------------------------------------ */
+/* Cubature rules, App. A and App. B                                   */
+/* ------------------------------------------------------------------ */
+/* Rule index 0..4 <-> N = 4, 7, 12, 19, 33 (triangles, Tables A1-A5)
+ *                 <-> N = 4, 7, 12, 17, 33 (rectangles, Tables B1-B5).
+ * Triangle nodes are barycentric (lambda_A, lambda_B, lambda_C), Eq. 3.3.
+ * Rectangle nodes are natural coordinates (x, y) in [-1, 1]^2, Eq. 3.2.
+ * Weights sum to 1 (Eq. 3.1). */
+#define MAXN 33
+typedef struct {
+    int n;
+    double a[MAXN], b[MAXN], c[MAXN], w[MAXN];
+} rule_t;
+
+static rule_t TRI[5], RECT[5];
+static int rules_ready = 0;
+
+static void tri_add(rule_t* r, double la, double lb, double lc, double w)
+{
+    r->a[r->n] = la; r->b[r->n] = lb; r->c[r->n] = lc; r->w[r->n] = w; r->n++;
+}
+/* the three points with lambda_A = p and lambda_B = lambda_C = q, permuted
+ * (caption of Table A2: "all possible different permutations of lambda_A
+ * and lambda_B = lambda_C") */
+static void tri_perm3(rule_t* r, double p, double q, double w)
+{
+    tri_add(r, p, q, q, w);
+    tri_add(r, q, p, q, w);
+    tri_add(r, q, q, p, w);
+}
+/* cyclic permutations (A,B,C) -> (B,C,A) -> (C,A,B), caption of Table A3 */
+static void tri_cyc3(rule_t* r, double la, double lb, double lc, double w)
+{
+    tri_add(r, la, lb, lc, w);
+    tri_add(r, lb, lc, la, w);
+    tri_add(r, lc, la, lb, w);
+}
+/* all six permutations, captions of Tables A4 and A5 */
+static void tri_perm6(rule_t* r, double la, double lb, double lc, double w)
+{
+    tri_add(r, la, lb, lc, w);
+    tri_add(r, la, lc, lb, w);
+    tri_add(r, lb, la, lc, w);
+    tri_add(r, lb, lc, la, w);
+    tri_add(r, lc, la, lb, w);
+    tri_add(r, lc, lb, la, w);
+}
+static void rect_add(rule_t* r, double x, double y, double w)
+{
+    r->a[r->n] = x; r->b[r->n] = y; r->c[r->n] = 0.0; r->w[r->n] = w; r->n++;
+}
+/* all sign changes (x,y),(x,-y),(-x,y),(-x,-y), captions of Tables B2, B3 */
+static void rect_sign4(rule_t* r, double x, double y, double w)
+{
+    rect_add(r, x, y, w);
+    rect_add(r, x, -y, w);
+    rect_add(r, -x, y, w);
+    rect_add(r, -x, -y, w);
+}
+/* rotations by 0, 180, +90, -90 degrees: (x,y) -> +-(x,y), +-(-y,x),
+ * captions of Tables B4 and B5 */
+static void rect_rot4(rule_t* r, double x, double y, double w)
+{
+    rect_add(r, x, y, w);
+    rect_add(r, -x, -y, w);
+    rect_add(r, -y, x, w);
+    rect_add(r, y, -x, w);
+}
+
+static void build_rules(void)
+{
+    rule_t* r;
+    if (rules_ready) return;
+    memset(TRI, 0, sizeof TRI);
+    memset(RECT, 0, sizeof RECT);
+
+    /* Table A1: 4 points, degree 3 */
+    r = &TRI[0];
+    tri_add(r, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, -9.0 / 16.0);
+    tri_perm3(r, 3.0 / 5.0, 1.0 / 5.0, 25.0 / 48.0);
+
+    /* Table A2: 7 points, degree 5; t = 1/3, s = (1-sqrt15)/7, r = (1+sqrt15)/7 */
+    {
+        const double q15 = sqrt(15.0), t = 1.0 / 3.0;
+        const double s = (1.0 - q15) / 7.0, rr = (1.0 + q15) / 7.0;
+        r = &TRI[1];
+        tri_add(r, t, t, t, 9.0 / 40.0);
+        tri_perm3(r, t + 2.0 * t * s, t - t * s, (155.0 + q15) / 1200.0);
+        tri_perm3(r, t + 2.0 * t * rr, t - t * rr, (155.0 - q15) / 1200.0);
+    }
+
+    /* Table A3: 12 points, degree 7 (cyclic permutations) */
+    r = &TRI[2];
+    tri_cyc3(r, 0.06238226509439084, 0.06751786707392436, 0.8700998678316848, 0.05303405631486900);
+    tri_cyc3(r, 0.05522545665692000, 0.3215024938520156, 0.6232720494910644, 0.08776281742889622);
+    tri_cyc3(r, 0.03432430294509488, 0.6609491961867980, 0.3047265008681072, 0.05755008556995056);
+    tri_cyc3(r, 0.5158423343536001, 0.2777161669764050, 0.2064414986699949, 0.13498637401961758);
+
+    /* Table A4: 19 points, degree 9 */
+    r = &TRI[3];
+    tri_add(r, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 0.09713579628279610);
+    tri_perm3(r, 0.02063496160252593, 0.48968251919873704, 0.03133470022713983);
+    tri_perm3(r, 0.1258208170141290, 0.4370895914929355, 0.07782754100477543);
+    tri_perm3(r, 0.6235929287619356, 0.18820353561903219, 0.07964773892720910);
+    tri_perm3(r, 0.9105409732110941, 0.04472951339445297, 0.02557767565869810);
+    tri_perm6(r, 0.03683841205473626, 0.7411985987844980, 0.22196298916076573, 0.04328353937728940);
+
+    /* Table A5: 33 points, degree 12 */
+    r = &TRI[4];
+    tri_perm3(r, 0.4570749859701478, 0.27146250701492611, 0.06254121319590276);
+    tri_perm3(r, 0.1197767026828138, 0.44011164865859310, 0.04991833492806094);
+    tri_perm3(r, 0.0235924981089169, 0.48820375094554155, 0.02426683808145203);
+    tri_perm3(r, 0.7814843446812914, 0.10925782765935432, 0.02848605206887754);
+    tri_perm3(r, 0.9507072731273288, 0.02464636343633558, 0.00793164250997364);
+    tri_perm6(r, 0.1162960196779266, 0.2554542286385173, 0.62824975168355610, 0.04322736365941421);
+    tri_perm6(r, 0.02303415635526714, 0.2916556797383410, 0.68531016390639186, 0.02178358503860756);
+    tri_perm6(r, 0.02138249025617059, 0.1272797172335894, 0.85133779251024000, 0.01508367757651144);
+
+    /* Table B1: 4 points, degree 3; s = 1/sqrt3 */
+    r = &RECT[0];
+    rect_sign4(r, 1.0 / sqrt(3.0), 1.0 / sqrt(3.0), 0.25);
+
+    /* Table B2: 7 points, degree 5; t = sqrt(14/15), r = sqrt(3/5), s = sqrt(1/3).
+     * The (0, +-t) nodes lie on the local y axis exactly as printed. */
+    r = &RECT[1];
+    rect_add(r, 0.0, 0.0, 2.0 / 7.0);
+    rect_add(r, 0.0, sqrt(14.0 / 15.0), 5.0 / 63.0);
+    rect_add(r, 0.0, -sqrt(14.0 / 15.0), 5.0 / 63.0);
+    rect_sign4(r, sqrt(3.0 / 5.0), sqrt(1.0 / 3.0), 5.0 / 36.0);
+
+    /* Table B3: 12 points, degree 7 */
+    {
+        const double q583 = sqrt(583.0);
+        const double rr = sqrt(6.0 / 7.0);
+        const double s = sqrt((114.0 - 3.0 * q583) / 287.0);
+        const double t = sqrt((114.0 + 3.0 * q583) / 287.0);
+        const double B1 = 49.0 / 810.0;
+        const double B2 = (178981.0 + 2769.0 * q583) / 1888920.0;
+        const double B3 = (178981.0 - 2769.0 * q583) / 1888920.0;
+        r = &RECT[2];
+        rect_add(r, rr, 0.0, B1);
+        rect_add(r, -rr, 0.0, B1);
+        rect_add(r, 0.0, rr, B1);
+        rect_add(r, 0.0, -rr, B1);
+        rect_sign4(r, s, s, B2);
+        rect_sign4(r, t, t, B3);
+    }
+
+    /* Table B4: 17 points, degree 9 */
+    r = &RECT[3];
+    rect_add(r, 0.0, 0.0, 0.131687242798353921);
+    rect_rot4(r, 0.968849966361977720, 0.630680119731668854, 0.022219844542549678);
+    rect_rot4(r, 0.750277099978900533, 0.927961645959569667, 0.028024900532399120);
+    rect_rot4(r, 0.523735820214429336, 0.453339821135647190, 0.099570609815517519);
+    rect_rot4(r, 0.076208328192617173, 0.852615729333662307, 0.067262834409945196);
+
+    /* Table B5: 33 points, degree 13 */
+    r = &RECT[4];
+    rect_add(r, 0.0, 0.0, 0.075095528857806335);
+    rect_rot4(r, 0.778809711554419422, 0.983486682439872263, 0.007497959716124783);
+    rect_rot4(r, 0.957297699786307365, 0.859556005641638928, 0.009543605329270918);
+    rect_rot4(r, 0.138183459862465353, 0.958925170287534857, 0.015106230954437494);
+    rect_rot4(r, 0.941327225872925236, 0.390736216129461000, 0.019373184633276336);
+    rect_rot4(r, 0.475808625218275905, 0.850076673699748575, 0.029711166825148901);
+    rect_rot4(r, 0.755805356572081436, 0.647821637187010732, 0.032440887592500675);
+    rect_rot4(r, 0.696250078491749413, 0.070741508996444936, 0.053335395364297350);
+    rect_rot4(r, 0.342716556040406789, 0.409304561694038843, 0.064217687370491966);
+
+    rules_ready = 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Element geometry: Sec. 2 (centroid, L), Eq. 3.2, Eq. 3.3              */
+/* ------------------------------------------------------------------ */
+/* type 0 = triangle with corners A, B, C (v[0..2]);
+ * type 1 = rectangle with corners P0, P1, P2, P3 in order around the
+ * boundary, side a along P0->P1 (u_x), side b along P0->P3 (u_y). */
+typedef struct {
+    int type;
+    double v[4][3];
+    double cen[3];   /* Q_cen */
+    double L;        /* average side length */
+    double area;     /* cal A */
+    double ux[3], uy[3], a, b; /* rectangle frame, Eq. 3.2 */
+} elem_t;
+
+static void elem_setup(elem_t* e, int type, const double* verts)
+{
+    int i, k;
+    e->type = type;
+    for (i = 0; i < 4; ++i)
+        for (k = 0; k < 3; ++k) e->v[i][k] = verts[3 * i + k];
+    if (type == 0) {
+        double ab[3], ac[3], bc[3], cr[3];
+        sub3(e->v[1], e->v[0], ab);
+        sub3(e->v[2], e->v[0], ac);
+        sub3(e->v[2], e->v[1], bc);
+        cross3(ab, ac, cr);
+        e->area = 0.5 * norm3(cr);
+        for (k = 0; k < 3; ++k) e->cen[k] = (e->v[0][k] + e->v[1][k] + e->v[2][k]) / 3.0;
+        /* L = (a + b + c) / 3, Sec. 2 */
+        e->L = (norm3(ab) + norm3(bc) + norm3(ac)) / 3.0;
+    } else {
+        double d1[3], d3[3];
+        sub3(e->v[1], e->v[0], d1);
+        sub3(e->v[3], e->v[0], d3);
+        e->a = norm3(d1);
+        e->b = norm3(d3);
+        for (k = 0; k < 3; ++k) {
+            e->ux[k] = d1[k] / e->a;
+            e->uy[k] = d3[k] / e->b;
+            e->cen[k] = (e->v[0][k] + e->v[1][k] + e->v[2][k] + e->v[3][k]) / 4.0;
+        }
+        e->area = e->a * e->b;
+        /* mean of the four side lengths (the paper states L for the triangle
+         * only; the rectangle reading is (a + b) / 2) */
+        e->L = 0.5 * (e->a + e->b);
+    }
+}
+
+/* i-th node of a rule, Eq. 3.3 (triangle) or Eq. 3.2 (rectangle) */
+static void rule_node(const elem_t* e, const rule_t* r, int i, double Q[3])
+{
+    int k;
+    if (e->type == 0) {
+        for (k = 0; k < 3; ++k) Q[k] = r->a[i] * e->v[0][k] + r->b[i] * e->v[1][k] + r->c[i] * e->v[2][k];
+    } else {
+        for (k = 0; k < 3; ++k)
+            Q[k] = e->cen[k] + 0.5 * e->a * r->a[i] * e->ux[k] + 0.5 * e->b * r->b[i] * e->uy[k];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Point-charge cubature, Eq. 4.1 (unit sigma; 1/(4 pi eps0) applied by  */
+/* the caller)                                                          */
+/* ------------------------------------------------------------------ */
+static void cubature_field(const elem_t* e, int rule, const double P[3], double out[4])
+{
+    const rule_t* r = e->type == 0 ? &TRI[rule] : &RECT[rule];
+    double phi = 0.0, Ex = 0.0, Ey = 0.0, Ez = 0.0;
+    int i;
+    for (i = 0; i < r->n; ++i) {
+        double Q[3], d[3], dist, qi;
+        rule_node(e, r, i, Q);
+        sub3(P, Q, d);
+        dist = norm3(d);
+        qi = r->w[i] * e->area; /* q_i = w_i q with q = sigma * area, sigma = 1 */
+        phi += qi / dist;
+        Ex += qi * d[0] / (dist * dist * dist);
+        Ey += qi * d[1] / (dist * dist * dist);
+        Ez += qi * d[2] / (dist * dist * dist);
+    }
+    out[0] = phi; out[1] = Ex; out[2] = Ey; out[3] = Ez;
+}
+
+/* ------------------------------------------------------------------ */
+/* Analytic near field of a uniformly charged planar polygon (unit       */
+/* sigma, no 1/(4 pi eps0)).                                            */
+/*                                                                      */
+/* The paper uses analytical integration below DR = 3 (Sec. 4) and      */
+/* cites the formulas without printing them.  This is the standard      */
+/* decomposition from potential theory.  With n the unit normal of the  */
+/* polygon (corners counter-clockwise seen from +n), h = (P - V)·n the  */
+/* signed height, and for each edge e from V1 to V2 the unit tangent t,  */
+/* the in-plane outward normal m = t x n, d = (V1 - P)·m, s_k = (V_k-P)·t,*/
+/* R_k = |P - V_k| and l = ln((s2 + R2) / (s1 + R1)) = integral of ds/R  */
+/* along the edge:                                                      */
+/*   int dA / R            = sum_e d_e l_e - h Omega                    */
+/*   int (P-Q) / R^3 dA    = sum_e m_e l_e + n Omega                    */
+/* where Omega is the solid angle of the polygon seen from P, signed     */
+/* like h.  (The first line is the 2-D divergence theorem applied to the */
+/* in-plane field rho (R - |h|) / rho^2; the second follows from         */
+/* grad_Q (1/R) on the edges and from h / R^3 being the solid-angle      */
+/* density.)                                                            */
+/* ------------------------------------------------------------------ */
+
+/* integral of ds / R over an edge, written so that no sum of nearly
+ * opposite terms occurs: s1 < s2 always (s grows along the edge). */
+static double edge_log(double s1, double s2, double R1, double R2, double perp2)
+{
+    if (s1 >= 0.0) return log((R2 + s2) / (R1 + s1));
+    if (s2 <= 0.0) return log((R1 - s1) / (R2 - s2));
+    /* s1 < 0 < s2: (R1 + s1) = perp^2 / (R1 - s1) */
+    return log((R2 + s2) * (R1 - s1) / perp2);
+}
+
+/* solid angle of triangle (a, b, c) seen from P, Van Oosterom & Strackee
+ * (1983), returned with the sign of h for a triangle that is counter-
+ * clockwise about n. */
+static double tri_solid_angle(const double a[3], const double b[3], const double c[3], const double P[3])
+{
+    double Ra[3], Rb[3], Rc[3], bxc[3], num, den, ra, rb, rc;
+    sub3(a, P, Ra);
+    sub3(b, P, Rb);
+    sub3(c, P, Rc);
+    ra = norm3(Ra); rb = norm3(Rb); rc = norm3(Rc);
+    cross3(Rb, Rc, bxc);
+    num = dot3(Ra, bxc);
+    den = ra * rb * rc + dot3(Ra, Rb) * rc + dot3(Ra, Rc) * rb + dot3(Rb, Rc) * ra;
+    /* num = -2 * area * h for a counter-clockwise triangle */
+    return 2.0 * atan2(-num, den);
+}
+
+static void analytic_field(const elem_t* e, const double P[3], double out[4])
+{
+    const int nv = e->type == 0 ? 3 : 4;
+    double n[3], e1[3], e2[3], nl, h, phi = 0.0, E[3] = {0.0, 0.0, 0.0}, omega;
+    int k, j;
+    sub3(e->v[1], e->v[0], e1);
+    sub3(e->v[2], e->v[0], e2);
+    cross3(e1, e2, n);
+    nl = norm3(n);
+    for (k = 0; k < 3; ++k) n[k] /= nl;
+    {
+        double pv[3];
+        sub3(P, e->v[0], pv);
+        h = dot3(pv, n);
+    }
+    for (j = 0; j < nv; ++j) {
+        const double* V1 = e->v[j];
+        const double* V2 = e->v[(j + 1) % nv];
+        double t[3], m[3], r1[3], r2[3], len, s1, s2, R1, R2, d, perp2, l;
+        sub3(V2, V1, t);
+        len = norm3(t);
+        for (k = 0; k < 3; ++k) t[k] /= len;
+        cross3(t, n, m);
+        sub3(V1, P, r1);
+        sub3(V2, P, r2);
+        s1 = dot3(r1, t);
+        s2 = dot3(r2, t);
+        R1 = norm3(r1);
+        R2 = norm3(r2);
+        d = dot3(r1, m);
+        perp2 = d * d + h * h;
+        l = edge_log(s1, s2, R1, R2, perp2);
+        phi += d * l;
+        for (k = 0; k < 3; ++k) E[k] += m[k] * l;
+    }
+    if (h == 0.0) {
+        /* field point in the element plane: h * Omega = 0; on the element
+         * the normal field jumps, and the mean of both sides (0) is used */
+        omega = 0.0;
+    } else {
+        omega = tri_solid_angle(e->v[0], e->v[1], e->v[2], P);
+        if (nv == 4) omega += tri_solid_angle(e->v[0], e->v[2], e->v[3], P);
+    }
+    phi -= h * omega;
+    for (k = 0; k < 3; ++k) E[k] += n[k] * omega;
+    out[0] = phi; out[1] = E[0]; out[2] = E[1]; out[3] = E[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* GL2 reference integrator, Sec. 2: two nested 16-node Gauss-Legendre   */
+/* quadratures.                                                         */
+/* ------------------------------------------------------------------ */
+#define NGL_MAX 64
+/* Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n */
+static void gauss_legendre(int n, double* x, double* w)
+{
+    int i, it, j;
+    for (i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+        for (it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z, z1;
+            for (j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            /* p1 = P_n(z), p0 = P_{n-1}(z) */
+            pp = n * (z * p1 - p0) / (z * z - 1.0);
+            z1 = z;
+            z = z1 - p1 / pp;
+            if (fabs(z - z1) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            pp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[i] = -z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+/* GL2 over one element with n x n nodes.  Rectangle: tensor product over
+ * (x, y) in [-1,1]^2 of Eq. 3.2, Jacobian a b / 4.  Triangle: collapsed map
+ * Q(u, v) = A + u (B - A) + u v (C - B), (u, v) in [0,1]^2, Jacobian
+ * 2 area u (the paper does not state its triangle mapping). */
+static void gl2_field(const elem_t* e, int n, const double P[3], double out[4])
+{
+    double x[NGL_MAX], w[NGL_MAX], acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int i, j, k;
+    gauss_legendre(n, x, w);
+    for (i = 0; i < n; ++i) {
+        for (j = 0; j < n; ++j) {
+            double Q[3], d[3], dist, wt;
+            if (e->type == 1) {
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->cen[k] + 0.5 * e->a * x[i] * e->ux[k] + 0.5 * e->b * x[j] * e->uy[k];
+                wt = w[i] * w[j] * e->a * e->b / 4.0;
+            } else {
+                const double u = 0.5 * (x[i] + 1.0), v = 0.5 * (x[j] + 1.0);
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->v[0][k] + u * (e->v[1][k] - e->v[0][k]) + u * v * (e->v[2][k] - e->v[1][k]);
+                wt = 0.25 * w[i] * w[j] * 2.0 * e->area * u;
+            }
+            sub3(P, Q, d);
+            dist = norm3(d);
+            acc[0] += wt / dist;
+            for (k = 0; k < 3; ++k) acc[k + 1] += wt * d[k] / (dist * dist * dist);
+        }
+    }
+    for (k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+/* Brute force: split the element into 2^level x 2^level congruent pieces
+ * (triangle: midpoint subdivision into 4 per level; rectangle: quadrants)
+ * and sum GL2 over the pieces. */
+static void subdiv_field(const elem_t* e, int level, int n, const double P[3], double out[4])
+{
+    int k;
+    if (level == 0) {
+        gl2_field(e, n, P, out);
+        return;
+    }
+    for (k = 0; k < 4; ++k) out[k] = 0.0;
+    if (e->type == 0) {
+        double m01[3], m12[3], m20[3], tris[4][4][3], part[4];
+        int c, t;
+        for (k = 0; k < 3; ++k) {
+            m01[k] = 0.5 * (e->v[0][k] + e->v[1][k]);
+            m12[k] = 0.5 * (e->v[1][k] + e->v[2][k]);
+            m20[k] = 0.5 * (e->v[2][k] + e->v[0][k]);
+        }
+        for (k = 0; k < 3; ++k) {
+            tris[0][0][k] = e->v[0][k]; tris[0][1][k] = m01[k];     tris[0][2][k] = m20[k];
+            tris[1][0][k] = m01[k];     tris[1][1][k] = e->v[1][k]; tris[1][2][k] = m12[k];
+            tris[2][0][k] = m20[k];     tris[2][1][k] = m12[k];     tris[2][2][k] = e->v[2][k];
+            tris[3][0][k] = m12[k];     tris[3][1][k] = m20[k];     tris[3][2][k] = m01[k];
+            for (c = 0; c < 4; ++c) tris[c][3][k] = 0.0;
+        }
+        for (t = 0; t < 4; ++t) {
+            elem_t sub;
+            elem_setup(&sub, 0, &tris[t][0][0]);
+            subdiv_field(&sub, level - 1, n, P, part);
+            for (c = 0; c < 4; ++c) out[c] += part[c];
+        }
+    } else {
+        int qx, qy, c;
+        for (qx = 0; qx < 2; ++qx) {
+            for (qy = 0; qy < 2; ++qy) {
+                double corners[4][3], part[4];
+                const double x0 = qx - 1.0, y0 = qy - 1.0; /* quadrant [x0, x0+1] x [y0, y0+1] */
+                const double xs[4] = {x0, x0 + 1.0, x0 + 1.0, x0};
+                const double ys[4] = {y0, y0, y0 + 1.0, y0 + 1.0};
+                elem_t sub;
+                for (c = 0; c < 4; ++c)
+                    for (k = 0; k < 3; ++k)
+                        corners[c][k] = e->cen[k] + 0.5 * e->a * xs[c] * e->ux[k] + 0.5 * e->b * ys[c] * e->uy[k];
+                elem_setup(&sub, 1, &corners[0][0]);
+                subdiv_field(&sub, level - 1, n, P, part);
+                for (c = 0; c < 4; ++c) out[c] += part[c];
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Rule bands by distance ratio, Sec. 4                                 */
+/* ------------------------------------------------------------------ */
+/* lim[type][0..4] ascending DR limits.  DR < lim[0]: analytic;
+ * lim[0] <= DR < lim[1]: 33 points; lim[1] <= DR < lim[2]: 19 (triangle) or
+ * 17 (rectangle) points; lim[2] <= DR < lim[3]: 12 points;
+ * lim[3] <= DR < lim[4]: 7 points; DR >= lim[4]: 4 points.
+ * Sec. 4 prints the triangle-potential limits for 2e-15 (3, 8, 20, 80, 1500)
+ * and says the field needs slightly higher ones, which then serve potential
+ * and field together.  No field or rectangle limits are printed: the default
+ * table below is the smallest DR per rule at which the mean err(phi) and
+ * err(E) of the paper's experiment (oracle/dr_experiment.py, 2000 random
+ * unit-cube elements per DR) stay below 2e-15, rounded up. */
+static const double DEFAULT_LIMITS[2][5] = {
+    {3.0, 12.0, 30.0, 120.0, 2250.0}, /* triangles */
+    {3.0, 18.0, 45.0, 160.0, 2800.0}, /* rectangles */
+};
+
+/* band: 0 = analytic, else the rule index (4 = 33 points ... 0 = 4 points)
+ * encoded as 1 + rule index */
+static int choose_band(const elem_t* e, const double P[3], const double* lim, double* dr_out)
+{
+    double d[3], D, DR;
+    int nb = 0, k;
+    sub3(P, e->cen, d);
+    D = norm3(d);          /* D = |P - Q_cen|, Sec. 2 */
+    DR = D / e->L;         /* DR = D / L */
+    if (dr_out) *dr_out = DR;
+    for (k = 0; k < 5; ++k)
+        if (DR >= lim[k]) nb++;
+    if (nb == 0) return 0;
+    return 1 + (5 - nb); /* nb = 1 -> 33 points (rule 4), nb = 5 -> 4 points (rule 0) */
+}
+
+/* ------------------------------------------------------------------ */
+/* Neumaier-compensated summation (the element sum of Sec. 5 evaluated   */
+/* as accurately as double precision allows)                            */
+/* ------------------------------------------------------------------ */
+static void nsum_add(double* s, double* c, double x)
+{
+    const double t = *s + x;
+    if (fabs(*s) >= fabs(x)) *c += (*s - t) + x;
+    else *c += (x - t) + *s;
+    *s = t;
+}
+
+#define EPS0_SI 8.8541878128e-12 /* CODATA 2018 vacuum permittivity, F/m */
+
+static double coulomb_k(double eps0)
+{
+    if (!(eps0 > 0.0)) eps0 = EPS0_SI;
+    return 1.0 / (4.0 * M_PI * eps0);
+}
+
+/* ------------------------------------------------------------------ */
+/* Public entry points (ctypes)                                         */
+/* ------------------------------------------------------------------ */
+
+/* method codes for single-element and field evaluations */
+#define OR_METHOD_PAPER 0    /* rule bands + analytic near field (the method) */
+#define OR_METHOD_GL2 1      /* GL2 with n nodes per dimension */
+#define OR_METHOD_ANALYTIC 2 /* analytic everywhere */
+#define OR_METHOD_RULE 3     /* one fixed cubature rule (param = rule index) */
+#define OR_METHOD_SUBDIV 4   /* 2^param x 2^param pieces, 16 x 16 GL2 on each */
+
+int oracle_rule(int type, int rule, double* nodes /* 33 x 4 */)
+{
+    const rule_t* r;
+    int i;
+    build_rules();
+    if (type < 0 || type > 1 || rule < 0 || rule > 4) return -1;
+    r = type == 0 ? &TRI[rule] : &RECT[rule];
+    for (i = 0; i < r->n; ++i) {
+        nodes[4 * i + 0] = r->a[i];
+        nodes[4 * i + 1] = r->b[i];
+        nodes[4 * i + 2] = r->c[i];
+        nodes[4 * i + 3] = r->w[i];
+    }
+    return r->n;
+}
+
+void oracle_gauss_legendre(int n, double* x, double* w) { gauss_legendre(n, x, w); }
+
+void oracle_default_limits(double* out /* 10 */)
+{
+    int t, k;
+    for (t = 0; t < 2; ++t)
+        for (k = 0; k < 5; ++k) out[5 * t + k] = DEFAULT_LIMITS[t][k];
+}
+
+/* centroid (3), L, area of one element */
+void oracle_element_geometry(int type, const double* verts, double* out /* 5 */)
+{
+    elem_t e;
+    elem_setup(&e, type, verts);
+    out[0] = e.cen[0]; out[1] = e.cen[1]; out[2] = e.cen[2];
+    out[3] = e.L;
+    out[4] = e.area;
+}
+
+/* phi and E of ONE element with sigma = 1 and without 1/(4 pi eps0) */
+int oracle_element(int type, const double* verts, const double* P, int method, int param,
+                   const double* limits, double* out /* 4 */, int* band_out)
+{
+    elem_t e;
+    int band = -1;
+    build_rules();
+    elem_setup(&e, type, verts);
+    switch (method) {
+    case OR_METHOD_PAPER:
+        band = choose_band(&e, P, limits ? limits + 5 * type : DEFAULT_LIMITS[type], NULL);
+        if (band == 0) analytic_field(&e, P, out);
+        else cubature_field(&e, band - 1, P, out);
+        break;
+    case OR_METHOD_GL2:
+        if (param < 1 || param > NGL_MAX) return -1;
+        gl2_field(&e, param, P, out);
+        break;
+    case OR_METHOD_ANALYTIC:
+        analytic_field(&e, P, out);
+        break;
+    case OR_METHOD_RULE:
+        if (param < 0 || param > 4) return -1;
+        cubature_field(&e, param, P, out);
+        break;
+    case OR_METHOD_SUBDIV:
+        if (param < 0 || param > 12) return -1;
+        subdiv_field(&e, param, 16, P, out);
+        break;
+    default:
+        return -1;
+    }
+    if (band_out) *band_out = band;
+    return 0;
+}
+
+/* phi and E at n_pts field points, summed over n_el elements in index
+ * order (Sec. 5), each element with constant sigma, times 1/(4 pi eps0).
+ *   verts:  n_el x 4 x 3 (triangles use the first three corners)
+ *   method: OR_METHOD_PAPER (the method) or OR_METHOD_GL2 (param nodes)
+ *   hist:   optional 2 x 6 pair counts per (type, band) -- band 0 is the
+ *           analytic branch, band 1 + r is cubature rule r
+ *   min_dr: optional per-point minimum distance ratio over all elements
+ */
+int oracle_eval(int64_t n_el, const int32_t* type, const double* verts, const double* sigma,
+                const double* limits, double eps0, int64_t n_pts, const double* pts,
+                double* phi, double* E, int method, int param, int nthreads,
+                int64_t* hist, double* min_dr)
+{
+    const double kc = coulomb_k(eps0);
+    int64_t p, j;
+    int64_t hist_local[12];
+    build_rules();
+    if (n_el < 0 || n_pts < 0) return -1;
+    for (j = 0; j < n_el; ++j)
+        if (type[j] != 0 && type[j] != 1) return -1;
+    memset(hist_local, 0, sizeof hist_local);
+    if (nthreads < 1) nthreads = 1;
+
+#pragma omp parallel num_threads(nthreads)
+    {
+        int64_t h_thr[12];
+        memset(h_thr, 0, sizeof h_thr);
+#pragma omp for schedule(dynamic, 4)
+        for (p = 0; p < n_pts; ++p) {
+            const double* P = pts + 3 * p;
+            double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0}, mdr = INFINITY;
+            int64_t jj;
+            int k;
+            for (jj = 0; jj < n_el; ++jj) {
+                elem_t e;
+                double f[4], dr;
+                elem_setup(&e, type[jj], verts + 12 * jj);
+                if (method == OR_METHOD_GL2) {
+                    gl2_field(&e, param, P, f);
+                    {
+                        double d[3];
+                        sub3(P, e.cen, d);
+                        dr = norm3(d) / e.L;
+                    }
+                } else {
+                    const int band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], &dr);
+                    if (band == 0) analytic_field(&e, P, f);
+                    else cubature_field(&e, band - 1, P, f);
+                    h_thr[6 * type[jj] + band]++;
+                }
+                if (dr < mdr) mdr = dr;
+                for (k = 0; k < 4; ++k) nsum_add(&s[k], &c[k], sigma[jj] * f[k]);
+            }
+            phi[p] = kc * (s[0] + c[0]);
+            for (k = 0; k < 3; ++k) E[3 * p + k] = kc * (s[k + 1] + c[k + 1]);
+            if (min_dr) min_dr[p] = mdr;
+        }
+#pragma omp critical
+        for (j = 0; j < 12; ++j) hist_local[j] += h_thr[j];
+    }
+    if (hist)
+        for (j = 0; j < 12; ++j) hist[j] = hist_local[j];
+    return 0;
+}
+
+/* BEM collocation coefficients (the sigma-to-potential matrix of the
+ * charge-density solve that the paper's BEM context describes, Sec. 5):
+ * A[i][j] = potential at colloc point i of element j with sigma = 1, by the
+ * same rule bands and analytic near field, times 1/(4 pi eps0).
+ * rows [row0, row0 + n_rows) only; A is n_rows x n_el, row-major. */
+int oracle_assemble(int64_t n_el, const int32_t* type, const double* verts, const double* limits,
+                    double eps0, int64_t row0, int64_t n_rows, const double* colloc, double* A,
+                    int nthreads)
+{
+    const double kc = coulomb_k(eps0);
+    int64_t i;
+    build_rules();
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (i = 0; i < n_rows; ++i) {
+        const double* P = colloc + 3 * (row0 + i);
+        int64_t j;
+        for (j = 0; j < n_el; ++j) {
+            elem_t e;
+            double f[4];
+            int band;
+            elem_setup(&e, type[j], verts + 12 * j);
+            band = choose_band(&e, P, limits ? limits + 5 * type[j] : DEFAULT_LIMITS[type[j]], NULL);
+            if (band == 0) analytic_field(&e, P, f);
+            else cubature_field(&e, band - 1, P, f);
+            A[i * n_el + j] = kc * f[0];
+        }
+    }
+    return 0;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* oracle_element for n independent (element, point) pairs: verts n x 4 x 3,
+ * P n x 3, out n x 4 (used by the distance-ratio experiment of Sec. 4) */
+int oracle_element_batch(int64_t n, const int32_t* type, const double* verts, const double* P, int method,
+                         int param, const double* limits, double* out, int32_t* band, int nthreads)
+{
+    int64_t i;
+    int bad = 0;
+    build_rules();
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : bad)
+    for (i = 0; i < n; ++i) {
+        int b = -1;
+        if (oracle_element(type[i], verts + 12 * i, P + 3 * i, method, param, limits, out + 4 * i, &b) != 0) bad |= 1;
+        if (band) band[i] = b;
+    }
+    return bad ? -1 : 0;
+}
