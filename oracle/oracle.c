@@ -337,13 +337,19 @@ static void cubature_field(const elem_t* e, int rule, const double P[3], double 
 /* ------------------------------------------------------------------ */
 
 /* integral of ds / R over an edge, written so that no sum of nearly
- * opposite terms occurs: s1 < s2 always (s grows along the edge). */
+ * opposite terms occurs: s1 < s2 always (s grows along the edge).
+ * A field point ON the closed edge makes the integral diverge (only
+ * logarithmically); the edge then contributes d l -> 0 to the potential
+ * (d = 0 there) and its singular in-plane field is left out: 0 is
+ * returned.  (The paper does not treat field points on an element.) */
 static double edge_log(double s1, double s2, double R1, double R2, double perp2)
 {
-    if (s1 >= 0.0) return log((R2 + s2) / (R1 + s1));
-    if (s2 <= 0.0) return log((R1 - s1) / (R2 - s2));
-    /* s1 < 0 < s2: (R1 + s1) = perp^2 / (R1 - s1) */
-    return log((R2 + s2) * (R1 - s1) / perp2);
+    double num, den;
+    if (s1 >= 0.0) { num = R2 + s2; den = R1 + s1; }
+    else if (s2 <= 0.0) { num = R1 - s1; den = R2 - s2; }
+    else { num = (R2 + s2) * (R1 - s1); den = perp2; } /* s1 < 0 < s2: R1 + s1 = perp^2 / (R1 - s1) */
+    if (den == 0.0) return 0.0;
+    return log(num / den);
 }
 
 /* solid angle of triangle (a, b, c) seen from P, Van Oosterom & Strackee

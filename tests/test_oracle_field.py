@@ -323,3 +323,19 @@ def test_assembly_times_sigma_is_potential():
     # self terms use the analytic branch: a field point on its own element
     rows = oracle.assemble(mesh.types, mesh.verts, col, rows=(0, 3))
     assert np.array_equal(rows, A[:3])
+
+
+@pytest.mark.parametrize("type_", [TRI, RECT])
+def test_potential_continuous_onto_an_edge(type_):
+    """A field point on an element edge (or corner) has a finite potential,
+    the limit of points approaching it; the oracle returns that limit."""
+    verts = synth.random_elements(type_, 1, seed=71)[0]
+    nv = 3 if type_ == TRI else 4
+    a, b = verts[0], verts[1]
+    cen = verts[:nv].mean(0)
+    for P in (0.3 * a + 0.7 * b, a.copy()):
+        on, _ = oracle.element(type_, verts, P, oracle.METHOD_ANALYTIC)
+        assert np.isfinite(on).all()
+        for eps in (1e-9, 1e-11):
+            near, _ = oracle.element(type_, verts, P + eps * (cen - P), oracle.METHOD_ANALYTIC)
+            assert abs(near[0] - on[0]) < 1e-7 * abs(on[0])
