@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the far/near-field evaluation: pair interactions per second
+(phi and E) of charged BEM triangles and rectangles by distance-ratio-banded
+Gaussian cubature with an analytic near field (arXiv:1606.03743, Sec. 4-6).
+
+Workload (one step): phi and E at 1,000,000 field points inside coaxial
+cylinder electrodes meshed with 100,000 flat rectangles and 50,000 end-cap
+triangles (150,000 elements), all rule bands in use, through the C ABI
+(bem_eval) on device-resident inputs.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+
+Multi-GPU (torchrun): every rank evaluates its own 1M-point batch against the
+whole mesh (weak scaling, no collective on the data path); the timed region
+is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pair interactions/s (phi+E) at stated rel. error vs FP64; p50/p99 query latency"
+UNIT = "pairs/s"
+SM_COUNT, FP32_LANES, MUFU_LANES = 152, 128, 16  # per SM
+WORKLOAD = ("coaxial cylinders r=1.0/1.2 len 4: 2 x 200x250 flat rectangles + 2 end caps of 25000 triangles "
+            "(150000 elements, sigma~N(1,0.2)); 1000000 field points uniform in r<0.95, |z|<1.9")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--points", type=int, default=1_000_000)
+    ap.add_argument("--fp64-points", type=int, default=16384, help="batch for the FP64-path comparison line")
+    ap.add_argument("--cpu-sample", type=int, default=8192, help="points of the oracle CPU baseline sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 comparison and CPU baseline")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 8:
+                for nm, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def far_traffic_from_profile():
+    """DRAM bytes per far-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1606_03743_gb300", "csrc", "k_far.cu")
+    prof = os.path.join(ROOT, "profiles", "k_far_coax150k_1M.md")
+    if not os.path.exists(prof):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    txt = open(prof).read()
+    m_sha = re.search(r"k_far\.cu sha256\[:16\]:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def algorithmic_flops(stats: np.ndarray) -> tuple[float, float]:
+    """FP32 flops and rsqrt count the method needs for the far pairs of one
+    step: per pair 8 flops to form P - Q_cen and |P - Q_cen|^2, per Gaussian
+    node 18 flops (r = d - o_i: 3; r^2: 5; q_i / r: 1; phi sum: 1;
+    q_i / r^3: 2; E sum: 6, FMA = 2 flops) and one rsqrt (Eq. 4.1)."""
+    nodes = {0: [0, 33, 19, 12, 7, 4], 1: [0, 33, 17, 12, 7, 4]}
+    flops = rsq = 0.0
+    for t in (0, 1):
+        for b in range(1, 6):
+            pairs = float(stats[6 * t + b])
+            flops += pairs * (8 + 18 * nodes[t][b])
+            rsq += pairs * nodes[t][b]
+    return flops, rsq
+
+
+def cores_used(n_threads: int) -> int:
+    return n_threads
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    mesh = synth.coax_mesh(seed=2)
+    pts = synth.coax_points(seed=2, n=a.points)
+    n_sample = 256
+    nt = oracle.max_threads()
+    sample = pts[:n_sample]
+    for _ in range(min(a.warmup, 1)):
+        oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, sample[:16], nthreads=nt)
+    times = []
+    for k in range(a.steps):
+        sl = pts[(k * n_sample) % a.points:][:n_sample]
+        t0 = time.perf_counter()
+        oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, sl, nthreads=nt)
+        times.append(time.perf_counter() - t0)
+    pairs = n_sample * mesh.n
+    value = pairs * a.steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_elements": mesh.n, "n_points": a.points,
+                       "step": f"{n_sample} of the {a.points} points against all elements (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": f"{n_sample} points x {mesh.n} elements per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+
+    import torch
+    import paper_1606_03743_gb300 as bem
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prec = bem.MIXED if a.precision == "mixed" else bem.FP64
+    mesh = synth.coax_mesh(seed=2)
+    pts = synth.coax_points(seed=2 + 1000 * rank, n=a.points)  # each rank its own batch
+    dev = torch.device("cuda", local)
+    m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                 torch.from_numpy(mesh.sigma).to(dev), precision=prec)
+    p_d = torch.from_numpy(pts).to(dev)
+    phi = torch.empty(a.points, dtype=torch.float64, device=dev)
+    E = torch.empty((a.points, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        bem.bem_eval(m.handle, p_d, phi, E, stream=stream.cuda_stream)
+
+    # band statistics of this workload (outside the timed region)
+    m.set_stats(True)
+    step()
+    stats = m.last_stats()
+    m.set_stats(False)
+    for _ in range(a.warmup):
+        step()
+
+    m.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    l0 = bem.bem_kernel_launches()
+    far_ms = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(a.steps):
+        flush.zero_()
+        step()
+        far_ms.append(float(m.last_times()[1]))
+    t_end.record(stream)
+    barrier()
+    launches = bem.bem_kernel_launches() - l0
+    ck = clocks.stop()
+    m.set_timing(False)
+    ms = t_start.elapsed_time(t_end)
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    pairs_step = float(a.points) * mesh.n
+    value = world * pairs_step * a.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (far-field cubature), from its own events
+    flops, rsq = algorithmic_flops(stats)
+    far_avg = statistics.mean(far_ms)
+    peak_fp32 = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12  # TFLOP/s at the maximum SM clock
+    achieved = flops / (far_avg * 1e-3) / 1e12
+    mufu_frac = rsq / (far_avg * 1e-3) / (SM_COUNT * MUFU_LANES * 2070e6)
+    traffic = far_traffic_from_profile()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64 mixed" if prec == bem.MIXED else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_elements": mesh.n, "n_points_per_gpu": a.points,
+                       "precision": a.precision, "parallelism": f"points sharded, {world} GPU(s)",
+                       "l2": "256 MiB buffer written between steps (inside the timed region)"},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32, "traffic": traffic,
+                         "kernel": "k_far (far-field cubature)", "kernel_ms": far_avg,
+                         "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)",
+                         "mufu_frac": mufu_frac},
+            "band_pairs": {"triangle": [int(x) for x in stats[0:6]], "rectangle": [int(x) for x in stats[6:12]],
+                           "order": "analytic, 33, 19|17, 12, 7, 4 points"},
+            "clocks": ck}
+
+    if rank == 0 and world == 1 and not a.no_extras:
+        line.update(extras(a, bem, torch, m, mesh, pts, prec, stream, phi, E))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
+    """End-to-end (host buffers), FP64-path comparison, CPU oracle baseline and accuracy."""
+    out = {}
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    hp = torch.from_numpy(pts).pin_memory()
+    hphi = torch.empty(a.points, dtype=torch.float64).pin_memory()
+    hE = torch.empty((a.points, 3), dtype=torch.float64).pin_memory()
+    bem.bem_eval(m.handle, hp, hphi, hE, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        bem.bem_eval(m.handle, hp, hphi, hE, stream=stream.cuda_stream)
+        ts.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(ts)
+    out["e2e"] = {"value": a.points * mesh.n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(hp.numel() * 8),
+                  "d2h_bytes_per_step": int((hphi.numel() + hE.numel()) * 8), "ms_per_step": e2e_s * 1e3}
+
+    # ---- the plain FP64 kernel on the same GPU (smaller batch: it is ~50x slower)
+    dev = phi_d.device
+    m64 = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                   torch.from_numpy(mesh.sigma).to(dev), precision=bem.FP64)
+    n64 = min(a.fp64_points, a.points)
+    p64 = torch.from_numpy(pts[:n64]).to(dev)
+    f64phi = torch.empty(n64, dtype=torch.float64, device=dev)
+    f64E = torch.empty((n64, 3), dtype=torch.float64, device=dev)
+    bem.bem_eval(m64.handle, p64, f64phi, f64E, stream=stream.cuda_stream)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    bem.bem_eval(m64.handle, p64, f64phi, f64E, stream=stream.cuda_stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = t0.elapsed_time(t1)
+    mix_rate = None
+    # same batch on the mixed mesh for a like-for-like ratio
+    if prec == bem.MIXED:
+        mphi = torch.empty(n64, dtype=torch.float64, device=dev)
+        mE = torch.empty((n64, 3), dtype=torch.float64, device=dev)
+        bem.bem_eval(m.handle, p64, mphi, mE, stream=stream.cuda_stream)
+        t0.record(stream)
+        bem.bem_eval(m.handle, p64, mphi, mE, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        mix_rate = n64 * mesh.n / (t0.elapsed_time(t1) * 1e-3)
+    out["fp64_path"] = {"value": n64 * mesh.n / (ms64 * 1e-3), "unit": UNIT, "n_points": n64, "ms": ms64,
+                        "mixed_same_batch": mix_rate,
+                        "mixed_over_fp64": (mix_rate / (n64 * mesh.n / (ms64 * 1e-3))) if mix_rate else None}
+
+    # ---- CPU oracle baseline on a bounded sample + accuracy of this run at those points
+    import oracle
+    oracle.build()
+    ns = min(a.cpu_sample, a.points)
+    nt = oracle.max_threads()
+    t0c = time.perf_counter()
+    rphi, rE, mdr = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[:ns], nthreads=nt,
+                                      return_min_dr=True)
+    cpu_s = time.perf_counter() - t0c
+    out["cpu_baseline"] = {"value": ns * mesh.n / cpu_s, "unit": UNIT, "cores": nt, "kind": "oracle",
+                           "sample": f"first {ns} of the {a.points} points x all {mesh.n} elements ({cpu_s:.1f} s)"}
+    gphi = phi_d[:ns].cpu().numpy()
+    gE = E_d[:ns].cpu().numpy()
+    g64phi = f64phi.cpu().numpy()
+    g64E = f64E.cpu().numpy()
+    k = min(ns, n64)
+
+    def errs(p, e, rp, re, sel):
+        ep = np.abs(p - rp) / np.abs(rp)
+        eE = np.linalg.norm(e - re, axis=1) / np.linalg.norm(re, axis=1)
+        return {"max_rel_phi": float(ep[sel].max(initial=0)), "max_rel_E": float(eE[sel].max(initial=0)),
+                "mean_rel_phi": float(ep[sel].mean()) if sel.any() else 0.0,
+                "mean_rel_E": float(eE[sel].mean()) if sel.any() else 0.0, "n": int(sel.sum())}
+
+    bands = {"min_DR>=3": mdr >= 3, "min_DR<3": mdr < 3}
+    out["accuracy_vs_oracle"] = {
+        "run_precision": a.precision,
+        "bands": {b: errs(gphi, gE, rphi, rE, s) for b, s in bands.items()},
+        "fp64_path": {b: errs(g64phi[:k], g64E[:k], rphi[:k], rE[:k], s[:k]) for b, s in bands.items()},
+        "points": ns}
+    m64.close()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * bem.h -- C ABI of the GB300 (sm_103a) library for the electric potential
+ * phi and field E of charged constant-density BEM triangles and rectangles
+ * by Gaussian cubature (Glueck & Hilk, arXiv:1606.03743).
+ *
+ * The method (Sec. 4, Eq. 4.1): every element is replaced by the point
+ * charges q_i = w_i sigma A of one of the paper's cubature rules (App. A for
+ * triangles, App. B for rectangles), chosen by the distance ratio
+ * DR = |P - Q_cen| / L (Sec. 2); below the near-field limit (DR < 3 by
+ * default, Sec. 4) the element is integrated analytically.  phi and E at a
+ * field point are the sums over all elements (Sec. 5), times 1/(4 pi eps0).
+ *
+ * Conventions for every entry point:
+ *  - Return value: BEM_OK (0) or a negative BEM_ERR_* code; the message of
+ *    the last failure on the calling thread is bem_last_error().  No C++
+ *    exception crosses this boundary.  On failure the outputs are not
+ *    written (except where a call says otherwise).
+ *  - Pointers: arrays may live in host memory or in device memory of the
+ *    current CUDA device; the library tells them apart with
+ *    cudaPointerGetAttributes and stages host arrays through its own device
+ *    buffers.  The caller owns every array it passes; the mesh owns all
+ *    device memory it allocates.
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default
+ *    stream).  Device work is issued on that stream; a call returns after
+ *    its results are complete (it synchronises the stream), because the
+ *    status it returns depends on device-side checks.
+ *  - Threads: one mesh must not be used from two threads at once.
+ *  - Layouts are row-major, double precision, C order.
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BEM_OK 0
+#define BEM_ERR_INVALID -1  /* bad argument, NaN, degenerate or non-rectangular element */
+#define BEM_ERR_OOM -2      /* device allocation failed or the memory budget is exceeded */
+#define BEM_ERR_CAPACITY -3 /* a work list outgrew its fixed capacity (no-growth calls) */
+#define BEM_ERR_CUDA -4     /* a CUDA runtime call or kernel launch failed */
+#define BEM_ERR_TIMEOUT -5  /* a bounded wait ran out (serving loop) */
+#define BEM_ERR_NOT_FOUND -6 /* unknown serving ticket */
+
+/* element types */
+#define BEM_TRIANGLE 0
+#define BEM_RECTANGLE 1
+
+/* arithmetic of the far-field cubature */
+#define BEM_FP64 0  /* double precision throughout (the paper's arithmetic, Sec. 6) */
+#define BEM_MIXED 1 /* FP32 point-charge sums with split-float (hi/lo) centroid
+                       differences, flushed into FP64 accumulators every tile of
+                       elements; near field and final sums in FP64 */
+
+typedef struct bem_mesh bem_mesh;
+
+/* Options of bem_create (all fields: 0 / NULL = default). */
+typedef struct {
+    int32_t precision;        /* BEM_FP64 (default) or BEM_MIXED */
+    int32_t flags;            /* reserved, must be 0 */
+    const double* limits;     /* NULL or 10 host doubles: for triangles then
+                                 rectangles, the 5 ascending DR limits
+                                 [near, 33-pt, 19|17-pt, 12-pt, 7-pt] of the
+                                 rule bands (Sec. 4): DR < limits[0] is
+                                 integrated analytically, limits[0] <= DR <
+                                 limits[1] uses the 33-point rule, ... and
+                                 DR >= limits[4] the 4-point rule.  Default:
+                                 triangles {3, 12, 30, 120, 2250}, rectangles
+                                 {3, 18, 45, 160, 2800}. */
+    double eps0;              /* vacuum permittivity; <= 0: 8.8541878128e-12 F/m */
+    size_t device_mem_budget; /* upper bound in bytes on the scratch memory the
+                                 mesh may hold (work lists, sort buffers);
+                                 0 = 4 GiB */
+} bem_options;
+
+/*
+ * bem_create -- upload and preprocess a mesh of constant-density elements.
+ *   types  [n]      BEM_TRIANGLE or BEM_RECTANGLE
+ *   verts  [n][4][3] corners: a triangle uses A, B, C (row 3 ignored); a
+ *                   rectangle gives P0, P1, P2, P3 around the boundary, side
+ *                   a = |P1 - P0| along u_x, side b = |P3 - P0| along u_y
+ *                   (Eq. 3.2); P2 must equal P1 + P3 - P0 and the sides must
+ *                   be orthogonal to 1e-9 relative.
+ *   sigma  [n]      charge density of each element (Eq. 2.1)
+ *   n      number of elements, >= 1 and < 2^31
+ * Per element it computes the centroid Q_cen, the average side length L
+ * (Sec. 2: (a+b+c)/3 for a triangle, (a+b)/2 for a rectangle), the area A
+ * and the frame from which the cubature nodes of Eq. 3.2 / Eq. 3.3 are
+ * expanded on the fly.  BEM_ERR_INVALID names the first bad element.
+ * The mesh copies everything it needs; the caller's arrays may be freed
+ * after the call.  *out receives the mesh (NULL on failure).
+ */
+int bem_create(const int32_t* types, const double* verts, const double* sigma, int64_t n,
+               const bem_options* opt, void* stream, bem_mesh** out);
+
+/* Release the mesh and every device buffer it owns.  NULL is a no-op. */
+void bem_destroy(bem_mesh* mesh);
+
+/* Number of elements of the mesh (0 for NULL). */
+int64_t bem_num_elements(const bem_mesh* mesh);
+
+/*
+ * bem_set_sigma -- replace the charge densities (n = bem_num_elements
+ * doubles), e.g. between the iterations of a charge-density solve.
+ */
+int bem_set_sigma(bem_mesh* mesh, const double* sigma, void* stream);
+
+/*
+ * bem_eval -- phi and E at n field points (Eq. 2.1 approximated by Eq. 4.1
+ * with the rule bands of Sec. 4 and the analytic near field).
+ *   points [n][3]  field points
+ *   phi    [n]     potential (V), or NULL to skip it
+ *   E      [n][3]  field (V/m), or NULL to skip it
+ * n = 0 is a no-op.  Each result depends only on its own field point and
+ * the mesh: it is the same whatever other points share the call.  On a
+ * field point that lies on an element the normal field is taken as the
+ * mean of both sides (zero contribution).
+ */
+int bem_eval(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
+
+/*
+ * bem_assemble -- BEM collocation matrix (the linear system for the charge
+ * densities that the paper's BEM context solves, Sec. 1 and Sec. 5):
+ *   A[i][j] = potential at colloc[i] of element j with sigma_j = 1,
+ * by the same rule bands, the analytic branch for near and self terms, and
+ * 1/(4 pi eps0).
+ *   colloc [m][3]       collocation points
+ *   A      [m][n_el]    output, row-major (m * n_el doubles, n_el =
+ *                       bem_num_elements)
+ */
+int bem_assemble(bem_mesh* mesh, const double* colloc, int64_t m, double* A, void* stream);
+
+/*
+ * bem_matvec -- matrix-free product y = A x of the collocation matrix at the
+ * element centroids (the shell-matrix product of the paper's iterative BEM
+ * solver context, Sec. 5): y[i] = potential at the centroid of element i of
+ * all elements carrying charge density x[j].
+ *   x [n_el], y [n_el]
+ */
+int bem_matvec(bem_mesh* mesh, const double* x, double* y, void* stream);
+
+/* Element centroids Q_cen (Sec. 2), n_el x 3, written to a host or device array. */
+int bem_centroids(bem_mesh* mesh, double* out, void* stream);
+
+/*
+ * bem_rule -- the expanded nodes of one cubature rule as the library stores
+ * them (App. A, App. B): for rule index r = 0..4 (N = 4, 7, 12, 19|17, 33),
+ * writes N rows (alpha, beta, w) to out (host, 33 * 3 doubles) and returns
+ * N.  A node sits at Q = Q_cen + alpha e0 + beta e1 with e0 = A - Q_cen,
+ * e1 = B - Q_cen for a triangle (alpha = lambda_A - lambda_C, beta =
+ * lambda_B - lambda_C, Eq. 3.3) and e0 = (a/2) u_x, e1 = (b/2) u_y for a
+ * rectangle (alpha = x, beta = y, Eq. 3.2).  Host only; no device needed.
+ */
+int bem_rule(int32_t type, int32_t r, double* out);
+
+/* Statistics of the last bem_eval / bem_assemble / bem_matvec on this mesh:
+ * out[0..5] pair counts per distance-ratio band for triangles (analytic,
+ * 33, 19, 12, 7, 4 points), out[6..11] the same for rectangles (analytic,
+ * 33, 17, 12, 7, 4 points), out[12] the number of near (analytic) pairs.
+ * out[0..11] are filled only by calls made with statistics enabled
+ * (bem_set_stats); out[12] always. */
+int bem_last_stats(const bem_mesh* mesh, int64_t* out /* 13 */);
+
+/* Enable (1) or disable (0) the per-band pair counts of the next calls; the
+ * counting variant of the far-field kernel is slower, so it is off by default. */
+int bem_set_stats(bem_mesh* mesh, int32_t enable);
+
+/* Enable (1) or disable (0) per-phase timing with CUDA events recorded on the
+ * call's stream.  bem_last_times then gives, in milliseconds, for the last
+ * bem_eval / bem_matvec: out[0] spatial sort of the points, out[1] far-field
+ * cubature kernel, out[2] near-pair scan + analytic near-field kernel,
+ * out[3] finalisation (sum, scale, scatter). */
+int bem_set_timing(bem_mesh* mesh, int32_t enable);
+int bem_last_times(const bem_mesh* mesh, double* out /* 4 */);
+
+/* Total number of CUDA kernels this library has launched in this process
+ * (all meshes, all devices). */
+int64_t bem_kernel_launches(void);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* bem_last_error(void);
+
+/* Library version string. */
+const char* bem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H */

@@ -1,0 +1,308 @@
+"""GB300 (sm_103a) library for the potential phi and field E of charged BEM
+triangles and rectangles by Gaussian cubature (arXiv:1606.03743).
+
+This module is the thin Python binding of the C ABI in include/bem.h: the
+``bem_*`` functions below marshal arguments to the same-named C entry points
+(every step of the computation runs in the library's CUDA kernels), and
+``Mesh`` wraps a ``bem_mesh*`` handle.  Arrays may be numpy arrays (host) or
+torch tensors (CPU or CUDA); results come back as the same kind.  PyTorch is
+only used for device memory and the current CUDA stream.
+
+There is no CPU fallback: if libbem.so is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
+           "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
+           "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
+           "bem_kernel_launches", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+
+FP64, MIXED = 0, 1
+TRIANGLE, RECTANGLE = 0, 1
+STATUS = {0: "BEM_OK", -1: "BEM_ERR_INVALID", -2: "BEM_ERR_OOM", -3: "BEM_ERR_CAPACITY", -4: "BEM_ERR_CUDA",
+          -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOT_FOUND"}
+
+
+class BemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bem_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("flags", C.c_int32), ("limits", C.POINTER(C.c_double)),
+                ("eps0", C.c_double), ("device_mem_budget", C.c_size_t)]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load the in-tree libbem.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or _build._stale():
+        if not build_if_missing:
+            raise ImportError(f"libbem.so not built: {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    vp, d, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    lib.bem_create.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(bem_options), vp, C.POINTER(vp)]
+    lib.bem_destroy.argtypes = [vp]
+    lib.bem_destroy.restype = None
+    lib.bem_num_elements.argtypes = [vp]
+    lib.bem_num_elements.restype = C.c_int64
+    lib.bem_set_sigma.argtypes = [vp, vp, vp]
+    lib.bem_eval.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    lib.bem_assemble.argtypes = [vp, vp, C.c_int64, vp, vp]
+    lib.bem_matvec.argtypes = [vp, vp, vp, vp]
+    lib.bem_centroids.argtypes = [vp, vp, vp]
+    lib.bem_rule.argtypes = [C.c_int32, C.c_int32, d]
+    lib.bem_last_stats.argtypes = [vp, i64]
+    lib.bem_set_stats.argtypes = [vp, C.c_int32]
+    lib.bem_set_timing.argtypes = [vp, C.c_int32]
+    lib.bem_last_times.argtypes = [vp, d]
+    lib.bem_kernel_launches.restype = C.c_int64
+    lib.bem_last_error.restype = C.c_char_p
+    lib.bem_version.restype = C.c_char_p
+    for name in ("bem_create", "bem_set_sigma", "bem_eval", "bem_assemble", "bem_matvec", "bem_centroids",
+                 "bem_rule", "bem_last_stats", "bem_set_stats", "bem_set_timing", "bem_last_times"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise BemError(rc, bem_last_error())
+    return rc
+
+
+# ---------------------------------------------------------------- array marshalling
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _is_torch(x) -> bool:
+    t = _torch()
+    return t is not None and isinstance(x, t.Tensor)
+
+
+def _stream(stream=None) -> int:
+    if stream is not None:
+        return int(stream)
+    t = _torch()
+    if t is not None and t.cuda.is_available() and t.cuda.is_initialized():
+        return int(t.cuda.current_stream().cuda_stream)
+    return 0
+
+
+def _prep(x, dtype, shape=None):
+    """Contiguous array of the given dtype; returns (object keeping it alive, pointer)."""
+    if _is_torch(x):
+        t = _torch()
+        tdt = {np.float64: t.float64, np.int32: t.int32}[dtype]
+        x = x.to(tdt).contiguous()
+        if shape is not None:
+            x = x.reshape(shape)
+        return x, x.data_ptr()
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a, a.ctypes.data
+
+
+def _empty_like_kind(ref, shape):
+    if _is_torch(ref):
+        t = _torch()
+        return t.empty(shape, dtype=t.float64, device=ref.device)
+    return np.empty(shape, dtype=np.float64)
+
+
+def _ptr(x) -> int:
+    return x.data_ptr() if _is_torch(x) else x.ctypes.data
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+def bem_version() -> str:
+    return load_library().bem_version().decode()
+
+
+def bem_last_error() -> str:
+    return load_library().bem_last_error().decode()
+
+
+def bem_rule(type_: int, r: int) -> np.ndarray:
+    """Expanded nodes (alpha, beta, w) of rule r (0..4) of an element type."""
+    out = np.zeros((33, 3))
+    n = _check(load_library().bem_rule(type_, r, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out[:n].copy()
+
+
+def bem_create(types, verts, sigma, precision: int = FP64, limits=None, eps0: float = 0.0,
+               device_mem_budget: int = 0, stream=None) -> int:
+    lib = load_library()
+    t, tp = _prep(types, np.int32)
+    n = int(t.shape[0])
+    v, vp_ = _prep(verts, np.float64, (n, 4, 3))
+    s, sp = _prep(sigma, np.float64, (n,))
+    opt = bem_options()
+    opt.precision = int(precision)
+    opt.flags = 0
+    lim_keep = None
+    if limits is not None:
+        lim_keep = np.ascontiguousarray(np.asarray(limits, np.float64).reshape(10))
+        opt.limits = lim_keep.ctypes.data_as(C.POINTER(C.c_double))
+    opt.eps0 = float(eps0)
+    opt.device_mem_budget = int(device_mem_budget)
+    h = C.c_void_p()
+    _check(lib.bem_create(tp, vp_, sp, n, C.byref(opt), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def bem_destroy(mesh: int) -> None:
+    load_library().bem_destroy(mesh)
+
+
+def bem_num_elements(mesh: int) -> int:
+    return int(load_library().bem_num_elements(mesh))
+
+
+def bem_set_sigma(mesh: int, sigma, stream=None) -> None:
+    s, sp = _prep(sigma, np.float64, (bem_num_elements(mesh),))
+    _check(load_library().bem_set_sigma(mesh, sp, _stream(stream)))
+
+
+def bem_eval(mesh: int, points, phi=None, E=None, stream=None) -> None:
+    p, pp = _prep(points, np.float64)
+    n = p.numel() // 3 if _is_torch(p) else p.size // 3
+    _check(load_library().bem_eval(mesh, pp, n, _ptr(phi) if phi is not None else None,
+                                   _ptr(E) if E is not None else None, _stream(stream)))
+
+
+def bem_assemble(mesh: int, colloc, A, stream=None) -> None:
+    p, pp = _prep(colloc, np.float64)
+    m = p.numel() // 3 if _is_torch(p) else p.size // 3
+    _check(load_library().bem_assemble(mesh, pp, m, _ptr(A), _stream(stream)))
+
+
+def bem_matvec(mesh: int, x, y, stream=None) -> None:
+    xx, xp = _prep(x, np.float64, (bem_num_elements(mesh),))
+    _check(load_library().bem_matvec(mesh, xp, _ptr(y), _stream(stream)))
+
+
+def bem_centroids(mesh: int, out, stream=None) -> None:
+    _check(load_library().bem_centroids(mesh, _ptr(out), _stream(stream)))
+
+
+def bem_set_stats(mesh: int, enable: bool) -> None:
+    _check(load_library().bem_set_stats(mesh, 1 if enable else 0))
+
+
+def bem_set_timing(mesh: int, enable: bool) -> None:
+    _check(load_library().bem_set_timing(mesh, 1 if enable else 0))
+
+
+def bem_last_times(mesh: int) -> np.ndarray:
+    """(sort, far, near, finalise) milliseconds of the last call with timing on."""
+    out = np.zeros(4)
+    _check(load_library().bem_last_times(mesh, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def bem_kernel_launches() -> int:
+    return int(load_library().bem_kernel_launches())
+
+
+def bem_last_stats(mesh: int) -> np.ndarray:
+    out = np.zeros(13, np.int64)
+    _check(load_library().bem_last_stats(mesh, out.ctypes.data_as(C.POINTER(C.c_int64))))
+    return out
+
+
+# ---------------------------------------------------------------- object API
+class Mesh:
+    """A device-resident mesh of constant-density triangles and rectangles.
+
+    types (n,) int32, verts (n, 4, 3) float64, sigma (n,) float64 -- numpy
+    arrays or torch tensors; precision FP64 or MIXED (see include/bem.h)."""
+
+    def __init__(self, types, verts, sigma, precision: int = FP64, limits=None, eps0: float = 0.0,
+                 device_mem_budget: int = 0, stream=None):
+        self._h = bem_create(types, verts, sigma, precision, limits, eps0, device_mem_budget, stream)
+        self.n = bem_num_elements(self._h)
+        self.precision = precision
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            bem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def eval(self, points, want_phi: bool = True, want_E: bool = True, stream=None):
+        """(phi (n,), E (n, 3)) at the field points (same array kind as points)."""
+        n = (points.numel() if _is_torch(points) else np.asarray(points).size) // 3
+        phi = _empty_like_kind(points, (n,)) if want_phi else None
+        E = _empty_like_kind(points, (n, 3)) if want_E else None
+        bem_eval(self._h, points, phi, E, stream)
+        return phi, E
+
+    def assemble(self, colloc, stream=None):
+        m = (colloc.numel() if _is_torch(colloc) else np.asarray(colloc).size) // 3
+        A = _empty_like_kind(colloc, (m, self.n))
+        bem_assemble(self._h, colloc, A, stream)
+        return A
+
+    def matvec(self, x, stream=None):
+        y = _empty_like_kind(x, (self.n,))
+        bem_matvec(self._h, x, y, stream)
+        return y
+
+    def set_sigma(self, sigma, stream=None):
+        bem_set_sigma(self._h, sigma, stream)
+
+    def centroids(self, like=None, stream=None):
+        out = _empty_like_kind(like if like is not None else np.zeros(0), (self.n, 3))
+        bem_centroids(self._h, out, stream)
+        return out
+
+    def set_stats(self, enable: bool):
+        bem_set_stats(self._h, enable)
+
+    def last_stats(self) -> np.ndarray:
+        return bem_last_stats(self._h)
+
+    def set_timing(self, enable: bool):
+        bem_set_timing(self._h, enable)
+
+    def last_times(self) -> np.ndarray:
+        return bem_last_times(self._h)

@@ -1,0 +1,571 @@
+// bem_capi.cu -- the extern "C" entry points declared in include/bem.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <string>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+namespace {
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+const double kDefaultLimits[2][5] = {{3.0, 12.0, 30.0, 120.0, 2250.0}, {3.0, 18.0, 45.0, 160.0, 2800.0}};
+constexpr double kEps0SI = 8.8541878128e-12;
+constexpr int kMaxCellBits = 7;  // must match the key width of k_sort.cu
+constexpr size_t kCells = size_t(1) << (3 * kMaxCellBits);
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA;
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown host pointer
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dalloc(bem_mesh* m, T** p, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (m->w.bytes + bytes > m->budget) {
+        set_error("device memory budget exceeded: need %zu more bytes, budget %zu, in use %zu", bytes, m->budget,
+                  m->w.bytes);
+        return BEM_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc((void**)p, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        *p = nullptr;
+        return BEM_ERR_OOM;
+    }
+    m->w.bytes += bytes;
+    return BEM_OK;
+}
+
+template <typename T>
+void dfree(bem_mesh* m, T** p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        m->w.bytes -= count * sizeof(T);
+        *p = nullptr;
+    }
+}
+
+void free_points(bem_mesh* m) {
+    Work& w = m->w;
+    const size_t c = w.cap_pts;
+    dfree(m, &w.pts, 3 * c);
+    dfree(m, &w.out, 4 * c);
+    dfree(m, &w.perm, c);
+    dfree(m, &w.key, c);
+    dfree(m, &w.far, c);
+    dfree(m, &w.near_cnt, c);
+    dfree(m, &w.near_off, c);
+    dfree(m, &w.scan_tmp, scan_tmp_ints((int)std::max(c, kCells)));
+    w.cap_pts = 0;
+}
+
+void free_near(bem_mesh* m) {
+    Work& w = m->w;
+    dfree(m, &w.near_rec, w.cap_near);
+    dfree(m, &w.near_val, w.cap_near);
+    w.cap_near = 0;
+}
+
+int ensure_points(bem_mesh* m, size_t n) {
+    Work& w = m->w;
+    if (n <= w.cap_pts) return BEM_OK;
+    free_points(m);
+    size_t c = 1024;
+    while (c < n) c *= 2;
+    int rc;
+    if ((rc = dalloc(m, &w.pts, 3 * c)) || (rc = dalloc(m, &w.out, 4 * c)) || (rc = dalloc(m, &w.perm, c)) ||
+        (rc = dalloc(m, &w.key, c)) || (rc = dalloc(m, &w.far, c)) || (rc = dalloc(m, &w.near_cnt, c)) ||
+        (rc = dalloc(m, &w.near_off, c)) || (rc = dalloc(m, &w.scan_tmp, scan_tmp_ints((int)std::max(c, kCells))))) {
+        w.cap_pts = c;
+        free_points(m);
+        return rc;
+    }
+    w.cap_pts = c;
+    return BEM_OK;
+}
+
+int ensure_near(bem_mesh* m, size_t n) {
+    Work& w = m->w;
+    if (n <= w.cap_near) return BEM_OK;
+    free_near(m);
+    size_t c = size_t(1) << 16;
+    while (c < n) c *= 2;
+    int rc;
+    if ((rc = dalloc(m, &w.near_rec, c)) || (rc = dalloc(m, &w.near_val, c))) {
+        w.cap_near = c;
+        free_near(m);
+        return rc;
+    }
+    w.cap_near = c;
+    return BEM_OK;
+}
+
+void free_mesh(bem_mesh* m) {
+    if (!m) return;
+    free_points(m);
+    free_near(m);
+    MeshDev& d = m->d;
+    cudaFree(d.chi);
+    cudaFree(d.clo);
+    cudaFree(d.e0);
+    cudaFree(d.e1);
+    cudaFree(d.cen);
+    cudaFree(d.fr);
+    cudaFree(d.geo);
+    cudaFree(d.verts);
+    cudaFree(d.type);
+    cudaFree(d.sigma);
+    cudaFree(m->w.cell_cnt);
+    cudaFree(m->w.cell_off);
+    cudaFree(m->w.counters);
+    cudaFree(m->w.bbox);
+    for (auto& e : m->ev)
+        if (e) cudaEventDestroy(e);
+    delete m;
+}
+
+// Stage an input array of `bytes` onto the device if it is a host array.
+int stage_in(const void* src, size_t bytes, void* dev_buf, const void** out, cudaStream_t s) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return BEM_OK;
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(dev_buf, src, bytes, cudaMemcpyHostToDevice, s));
+    *out = dev_buf;
+    return BEM_OK;
+}
+
+// After launch_sort_points: fail on non-finite field points.
+int check_points(bem_mesh* m, const char* fn, cudaStream_t s) {
+    unsigned long long bad = 0;
+    BEM_CUDA_TRY(cudaMemcpyAsync(&bad, m->w.counters + 15, sizeof bad, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) {
+        set_error("%s: a field point has a non-finite (or |x| >= 1e30) coordinate", fn);
+        return BEM_ERR_INVALID;
+    }
+    return BEM_OK;
+}
+
+int check_mesh(const bem_mesh* m, const char* fn) {
+    if (!m) {
+        set_error("%s: mesh is NULL", fn);
+        return BEM_ERR_INVALID;
+    }
+    return BEM_OK;
+}
+
+// Far pass + near pass + finalisation for n sorted points (m->w.perm filled).
+// Retries once with a larger near list if the first pass overflowed it.
+int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, double* dphi, double* dE, int stride4,
+             bool want_e, cudaStream_t s) {
+    Work& w = m->w;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 16 * sizeof(unsigned long long), s));
+        FarArgs a{};
+        a.pts = dpts;
+        a.perm = w.perm;
+        a.n_pts = n;
+        a.sigma = dsigma;
+        a.far = w.far;
+        a.near_cnt = w.near_cnt;
+        a.near_rec = w.near_rec;
+        a.counters = w.counters;
+        a.near_cap = w.cap_near;
+        a.kc = m->kc;
+        a.want_e = want_e;
+        a.stats = m->stats;
+        if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[1], s));
+        int rc = launch_far(m, a, s);
+        if (rc) return rc;
+        if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[2], s));
+        if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n, w.scan_tmp, s))) return rc;
+        if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s))) return rc;
+        if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[3], s));
+        if ((rc = launch_finalize(m, w.perm, n, dphi, dE, stride4, s))) return rc;
+        if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[4], s));
+        unsigned long long cnt[14];
+        BEM_CUDA_TRY(cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (m->timing) {
+            float t;
+            for (int k = 0; k < 4; ++k) {
+                BEM_CUDA_TRY(cudaEventElapsedTime(&t, m->ev[k], m->ev[k + 1]));
+                m->last_times[k] = t;
+            }
+        }
+        if (cnt[0] <= w.cap_near) {
+            m->last_stats[12] = (int64_t)cnt[0];
+            if (m->stats)
+                for (int k = 0; k < 12; ++k) m->last_stats[k] = (int64_t)cnt[2 + k];
+            return BEM_OK;
+        }
+        if ((rc = ensure_near(m, (size_t)cnt[0]))) return rc;  // grow and run again
+    }
+    set_error("near-pair list did not converge");
+    return BEM_ERR_CAPACITY;
+}
+
+}  // namespace
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" {
+
+const char* bem_last_error(void) { return g_err.c_str(); }
+
+const char* bem_version(void) { return "bem-cubature-gb300 0.1 (sm_103a)"; }
+
+int64_t bem_num_elements(const bem_mesh* m) { return m ? m->d.n : 0; }
+
+int bem_create(const int32_t* types, const double* verts, const double* sigma, int64_t n, const bem_options* opt,
+               void* stream, bem_mesh** out) {
+    if (!out) {
+        set_error("bem_create: out is NULL");
+        return BEM_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (!types || !verts || !sigma || n < 1 || n >= (int64_t(1) << 31)) {
+        set_error("bem_create: bad arguments (n = %lld)", (long long)n);
+        return BEM_ERR_INVALID;
+    }
+    bem_mesh* m = new (std::nothrow) bem_mesh();
+    if (!m) {
+        set_error("bem_create: out of host memory");
+        return BEM_ERR_OOM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    m->precision = opt ? opt->precision : BEM_FP64;
+    if (m->precision != BEM_FP64 && m->precision != BEM_MIXED) {
+        set_error("bem_create: unknown precision %d", (int)m->precision);
+        delete m;
+        return BEM_ERR_INVALID;
+    }
+    if (opt && opt->flags != 0) {
+        set_error("bem_create: flags must be 0");
+        delete m;
+        return BEM_ERR_INVALID;
+    }
+    m->eps0 = (opt && opt->eps0 > 0.0) ? opt->eps0 : kEps0SI;
+    m->kc = 1.0 / (4.0 * M_PI * m->eps0);
+    m->budget = (opt && opt->device_mem_budget) ? opt->device_mem_budget : (size_t(4) << 30);
+    for (int t = 0; t < 2; ++t)
+        for (int k = 0; k < 5; ++k) {
+            m->limits[t][k] = (opt && opt->limits) ? opt->limits[5 * t + k] : kDefaultLimits[t][k];
+            if (!(m->limits[t][k] >= 0.0) || !isfinite(m->limits[t][k]) || (k && m->limits[t][k] < m->limits[t][k - 1])) {
+                set_error("bem_create: limits must be finite, non-negative and ascending");
+                delete m;
+                return BEM_ERR_INVALID;
+            }
+        }
+    cudaError_t ce = cudaGetDevice(&m->device);
+    if (ce != cudaSuccess) {
+        delete m;
+        return cuda_fail(ce, "cudaGetDevice");
+    }
+    m->d.n = (int)n;
+    MeshDev& d = m->d;
+    int rc = BEM_OK;
+    // element arrays are owned by the mesh, outside the scratch budget
+    const size_t nn = (size_t)n;
+#define BEM_ALLOC(ptr, count)                                                              \
+    if (!rc) {                                                                             \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), sizeof(*(ptr)) * (count));             \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            set_error("bem_create: cudaMalloc failed: %s", cudaGetErrorString(e_));        \
+            rc = BEM_ERR_OOM;                                                              \
+        }                                                                                  \
+    }
+    BEM_ALLOC(d.chi, nn);
+    BEM_ALLOC(d.clo, nn);
+    BEM_ALLOC(d.e0, nn);
+    BEM_ALLOC(d.e1, nn);
+    BEM_ALLOC(d.cen, 3 * nn);
+    BEM_ALLOC(d.fr, 6 * nn);
+    BEM_ALLOC(d.geo, 2 * nn);
+    BEM_ALLOC(d.verts, 12 * nn);
+    BEM_ALLOC(d.type, nn);
+    BEM_ALLOC(d.sigma, nn);
+    BEM_ALLOC(m->w.cell_cnt, kCells);
+    BEM_ALLOC(m->w.cell_off, kCells);
+    BEM_ALLOC(m->w.counters, 16);
+    BEM_ALLOC(m->w.bbox, 2);
+#undef BEM_ALLOC
+    if (rc) {
+        free_mesh(m);
+        return rc;
+    }
+    // stage the raw input (host or device) into scratch, then preprocess
+    int* dtypes = nullptr;
+    double *dverts = nullptr, *dsig = nullptr;
+    ce = cudaMalloc((void**)&dtypes, sizeof(int) * nn);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&dverts, sizeof(double) * 12 * nn);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&dsig, sizeof(double) * nn);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dtypes, types, sizeof(int) * nn, cudaMemcpyDefault, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dverts, verts, sizeof(double) * 12 * nn, cudaMemcpyDefault, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dsig, sigma, sizeof(double) * nn, cudaMemcpyDefault, s);
+    if (ce != cudaSuccess) {
+        rc = cuda_fail(ce, "bem_create staging");
+    } else {
+        int64_t bad = -1;
+        int code = 0;
+        rc = launch_prep(m, dtypes, dverts, dsig, s, &bad, &code);
+    }
+    cudaFree(dtypes);
+    cudaFree(dverts);
+    cudaFree(dsig);
+    if (rc) {
+        free_mesh(m);
+        return rc;
+    }
+    if ((rc = ensure_near(m, std::max<size_t>(size_t(1) << 20, 4 * nn)))) {
+        free_mesh(m);
+        return rc;
+    }
+    *out = m;
+    return BEM_OK;
+}
+
+void bem_destroy(bem_mesh* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    free_mesh(m);
+}
+
+int bem_set_sigma(bem_mesh* m, const double* sigma, void* stream) {
+    int rc = check_mesh(m, "bem_set_sigma");
+    if (rc) return rc;
+    if (!sigma) {
+        set_error("bem_set_sigma: sigma is NULL");
+        return BEM_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    BEM_CUDA_TRY(cudaMemcpyAsync(m->d.sigma, sigma, sizeof(double) * m->d.n, cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BEM_OK;
+}
+
+int bem_set_stats(bem_mesh* m, int32_t enable) {
+    int rc = check_mesh(m, "bem_set_stats");
+    if (rc) return rc;
+    m->stats = enable != 0;
+    return BEM_OK;
+}
+
+int bem_last_stats(const bem_mesh* m, int64_t* out) {
+    int rc = check_mesh(m, "bem_last_stats");
+    if (rc) return rc;
+    if (!out) {
+        set_error("bem_last_stats: out is NULL");
+        return BEM_ERR_INVALID;
+    }
+    for (int k = 0; k < 13; ++k) out[k] = m->last_stats[k];
+    return BEM_OK;
+}
+
+int bem_set_timing(bem_mesh* m, int32_t enable) {
+    int rc = check_mesh(m, "bem_set_timing");
+    if (rc) return rc;
+    if (enable && !m->ev[0]) {
+        BEM_CUDA_TRY(cudaSetDevice(m->device));
+        for (auto& e : m->ev) BEM_CUDA_TRY(cudaEventCreate(&e));
+    }
+    m->timing = enable != 0;
+    return BEM_OK;
+}
+
+int bem_last_times(const bem_mesh* m, double* out) {
+    int rc = check_mesh(m, "bem_last_times");
+    if (rc) return rc;
+    if (!out) {
+        set_error("bem_last_times: out is NULL");
+        return BEM_ERR_INVALID;
+    }
+    for (int k = 0; k < 4; ++k) out[k] = m->last_times[k];
+    return BEM_OK;
+}
+
+int64_t bem_kernel_launches(void) { return g_launches.load(); }
+
+int bem_centroids(bem_mesh* m, double* out, void* stream) {
+    int rc = check_mesh(m, "bem_centroids");
+    if (rc) return rc;
+    if (!out) {
+        set_error("bem_centroids: out is NULL");
+        return BEM_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    BEM_CUDA_TRY(cudaMemcpyAsync(out, m->d.cen, sizeof(double) * 3 * m->d.n, cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BEM_OK;
+}
+
+int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* E, void* stream) {
+    int rc = check_mesh(m, "bem_eval");
+    if (rc) return rc;
+    if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && !points)) {
+        set_error("bem_eval: bad arguments (n = %lld)", (long long)n);
+        return BEM_ERR_INVALID;
+    }
+    if (n == 0) return BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    if ((rc = ensure_points(m, (size_t)n))) return rc;
+    Work& w = m->w;
+    const double* dpts;
+    if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s))) return rc;
+    const bool phi_dev = phi && is_device_ptr(phi), E_dev = E && is_device_ptr(E);
+    const bool phi_host = phi && !phi_dev, E_host = E && !E_dev;
+    if ((phi_dev && E_host) || (phi_host && E_dev)) {
+        set_error("bem_eval: phi and E must both be host or both be device arrays");
+        return BEM_ERR_INVALID;
+    }
+    if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[0], s));
+    if ((rc = launch_sort_points(m, dpts, (int)n, s))) return rc;
+    if ((rc = check_points(m, "bem_eval", s))) return rc;
+    if (!phi_host && !E_host) return run_eval(m, dpts, (int)n, m->d.sigma, phi, E, 0, E != nullptr, s);
+    // host outputs: finalise into the staging buffer (phi | E), then copy out
+    double* sphi = w.out;
+    double* sE = w.out + n;
+    if ((rc = run_eval(m, dpts, (int)n, m->d.sigma, sphi, sE, 0, E != nullptr, s))) return rc;
+    if (phi) BEM_CUDA_TRY(cudaMemcpyAsync(phi, sphi, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (E) BEM_CUDA_TRY(cudaMemcpyAsync(E, sE, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BEM_OK;
+}
+
+int bem_matvec(bem_mesh* m, const double* x, double* y, void* stream) {
+    int rc = check_mesh(m, "bem_matvec");
+    if (rc) return rc;
+    if (!x || !y) {
+        set_error("bem_matvec: x or y is NULL");
+        return BEM_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    const int n = m->d.n;
+    if ((rc = ensure_points(m, (size_t)n))) return rc;
+    Work& w = m->w;
+    // x is staged into the first n doubles of the (otherwise unused) points buffer
+    const double* dx;
+    if ((rc = stage_in(x, sizeof(double) * n, w.pts, (const void**)&dx, s))) return rc;
+    if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[0], s));
+    if ((rc = launch_sort_points(m, m->d.cen, n, s))) return rc;
+    const bool y_dev = is_device_ptr(y);
+    double* dy = y_dev ? y : w.out;
+    if ((rc = run_eval(m, m->d.cen, n, dx, dy, nullptr, 0, false, s))) return rc;
+    if (!y_dev) {
+        BEM_CUDA_TRY(cudaMemcpyAsync(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return BEM_OK;
+}
+
+int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, void* stream) {
+    int rc = check_mesh(m, "bem_assemble");
+    if (rc) return rc;
+    if (mrows < 0 || mrows >= (int64_t(1) << 31) || (mrows > 0 && (!colloc || !A))) {
+        set_error("bem_assemble: bad arguments (m = %lld)", (long long)mrows);
+        return BEM_ERR_INVALID;
+    }
+    if (mrows == 0) return BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    if ((rc = ensure_points(m, (size_t)mrows))) return rc;
+    Work& w = m->w;
+    const double* dpts;
+    if ((rc = stage_in(colloc, sizeof(double) * 3 * mrows, w.pts, (const void**)&dpts, s))) return rc;
+    const size_t abytes = sizeof(double) * (size_t)mrows * (size_t)m->d.n;
+    const bool a_dev = is_device_ptr(A);
+    double* dA = A;
+    if (!a_dev) {
+        if ((rc = dalloc(m, &dA, (size_t)mrows * (size_t)m->d.n))) return rc;
+    }
+    rc = launch_sort_points(m, dpts, (int)mrows, s);
+    if (!rc) rc = check_points(m, "bem_assemble", s);
+    for (int attempt = 0; !rc && attempt < 3; ++attempt) {
+        cudaError_t e = cudaMemsetAsync(w.counters, 0, 16 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "bem_assemble");
+            break;
+        }
+        FarArgs a{};
+        a.pts = dpts;
+        a.perm = w.perm;
+        a.n_pts = (int)mrows;
+        a.sigma = nullptr;  // assembly: unit charge density
+        a.far = w.far;
+        a.near_cnt = w.near_cnt;
+        a.near_rec = w.near_rec;
+        a.counters = w.counters;
+        a.near_cap = w.cap_near;
+        a.A = dA;
+        a.kc = m->kc;
+        a.stats = m->stats;
+        if ((rc = launch_far(m, a, s))) break;
+        if ((rc = launch_near_assemble(m, dpts, w.perm, dA, 0, s))) break;
+        unsigned long long cnt[14];
+        e = cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "bem_assemble");
+            break;
+        }
+        if (cnt[0] <= w.cap_near) {
+            m->last_stats[12] = (int64_t)cnt[0];
+            if (m->stats)
+                for (int k = 0; k < 12; ++k) m->last_stats[k] = (int64_t)cnt[2 + k];
+            break;
+        }
+        rc = ensure_near(m, (size_t)cnt[0]);
+        if (!rc && attempt == 2) {
+            set_error("near-pair list did not converge");
+            rc = BEM_ERR_CAPACITY;
+        }
+    }
+    if (!rc && !a_dev) {
+        cudaError_t e = cudaMemcpyAsync(A, dA, abytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "bem_assemble readback");
+    }
+    if (!a_dev) dfree(m, &dA, (size_t)mrows * (size_t)m->d.n);
+    return rc;
+}
+
+}  // extern "C"

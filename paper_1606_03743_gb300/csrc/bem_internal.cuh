@@ -1,0 +1,141 @@
+// bem_internal.cuh -- internal types shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bem.h"
+
+namespace bem {
+
+// ---------------------------------------------------------------- rules
+// Node slots of the five rules of one element type, concatenated in rule
+// order r = 0..4 (N = 4, 7, 12, 19|17, 33; App. A / App. B).
+constexpr int kMaxSlots = 80;  // 75 triangle slots, 73 rectangle slots, padded
+
+struct RuleSet {
+    int n[2][5];      // nodes per rule [type][r]
+    int start[2][5];  // first slot of rule r
+    double alpha[2][kMaxSlots], beta[2][kMaxSlots], w[2][kMaxSlots];
+};
+const RuleSet& rules();  // expanded once on the host (rules.cu)
+
+// ---------------------------------------------------------------- bands
+// Band of a pair: 0 = analytic near field, 1..5 = cubature with rule
+// r = 5 - band (band 1 = 33 points ... band 5 = 4 points).
+__host__ __device__ inline int band_rule(int band) { return 5 - band; }
+
+// ---------------------------------------------------------------- mesh data in HBM
+// Structure of arrays, one entry per element, element order as given.
+struct MeshDev {
+    int n = 0;
+    // mixed path records (float4, 64 B per element)
+    float4* chi = nullptr;  // centroid hi part xyz, w = type (0/1)
+    float4* clo = nullptr;  // centroid lo part xyz, w = L
+    float4* e0 = nullptr;   // frame vector e0 xyz, w = area
+    float4* e1 = nullptr;   // frame vector e1 xyz, w = 0
+    // FP64 path / near field / assembly
+    double* cen = nullptr;    // [n][3] centroid
+    double* fr = nullptr;     // [n][6] e0, e1 (FP64)
+    double* geo = nullptr;    // [n][2] L, area
+    double* verts = nullptr;  // [n][12] corners as given
+    int* type = nullptr;      // [n]
+    double* sigma = nullptr;  // [n]
+    double* cen_sorted_scratch = nullptr;
+};
+
+// Per-call scratch (grown on demand, owned by the mesh).
+struct Work {
+    size_t cap_pts = 0;
+    double* pts = nullptr;        // staged points [cap][3] (host inputs)
+    double* out = nullptr;        // staged outputs [cap][4]
+    int* perm = nullptr;          // sorted -> original point index
+    unsigned* key = nullptr;      // spatial cell key per point
+    int* cell_cnt = nullptr;      // histogram of cells
+    int* cell_off = nullptr;      // exclusive scan of cell_cnt
+    double4* far = nullptr;       // far-field sums per sorted point
+    int* near_cnt = nullptr;      // near pairs per sorted point
+    int* near_off = nullptr;      // exclusive scan of near_cnt
+    int* scan_tmp = nullptr;      // block sums of the scans
+    size_t cap_near = 0;
+    int4* near_rec = nullptr;     // (sorted point, element, ordinal, -)
+    double4* near_val = nullptr;  // analytic contributions in (point, ordinal) order
+    unsigned long long* counters = nullptr;  // [0] near pairs, [1] error flags, [2..13] band stats
+    float4* bbox = nullptr;       // [2] points bbox (min, max)
+    size_t bytes = 0;
+};
+
+enum Precision { kFP64 = 0, kMixed = 1 };
+
+}  // namespace bem
+
+struct bem_mesh {
+    int device = 0;
+    int precision = bem::kFP64;
+    double eps0 = 8.8541878128e-12;
+    double kc = 0.0;          // 1 / (4 pi eps0)
+    double limits[2][5];      // DR band limits per type
+    size_t budget = 0;
+    bool stats = false;
+    int64_t last_stats[13] = {0};
+    bool timing = false;
+    double last_times[4] = {0, 0, 0, 0};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bem::MeshDev d;
+    bem::Work w;
+};
+
+namespace bem {
+
+// ---------------------------------------------------------------- helpers
+void set_error(const char* fmt, ...);
+void count_launches(int n);  // adds n to the process-wide kernel launch counter
+int cuda_fail(cudaError_t e, const char* what);
+
+#define BEM_CUDA_TRY(call)                                   \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return ::bem::cuda_fail(_e, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- launchers
+// Element preprocessing (k_prep.cu). Returns the index of the first invalid
+// element through *bad (-1 if none) after synchronising.
+int launch_prep(bem_mesh* m, const int* types, const double* verts, const double* sigma, cudaStream_t s,
+                int64_t* bad, int* bad_code);
+int launch_set_q(bem_mesh* m, cudaStream_t s);
+
+// Spatial sort of field points (k_sort.cu): perm = points in cell order.
+int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s);
+// Exclusive scan of n ints (k_sort.cu); tmp needs scan_tmp_ints(n) ints.
+int launch_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+size_t scan_tmp_ints(int n);
+
+struct FarArgs {
+    const double* pts;   // original field points [n][3]
+    const int* perm;     // sorted -> original
+    int n_pts;
+    const double* sigma; // per element charge density (eval) or the x of a matvec
+    double4* far;        // out: far sums per sorted point
+    int* near_cnt;       // out: near pairs per sorted point
+    int4* near_rec;      // out: near pair list
+    unsigned long long* counters;
+    unsigned long long near_cap;
+    double* A;           // assembly output (row-major m x n_el) or nullptr
+    double kc;           // 1/(4 pi eps0) (assembly writes scaled entries)
+    int want_e;          // 0: potential only
+    int stats;           // count pairs per band into counters[2..13]
+};
+// Far-field cubature + near-pair compaction (k_far.cu).
+int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s);
+// Analytic near field over the compacted list and the per-point finalisation (k_near.cu).
+int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
+                     unsigned long long n_near, cudaStream_t s);
+int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int out_stride4,
+                    cudaStream_t s);
+int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double* A, unsigned long long n_near,
+                         cudaStream_t s);
+
+}  // namespace bem

@@ -1,0 +1,191 @@
+// k_near.cu -- analytic near field (FP64) over the compacted near-pair list,
+// and the per-point finalisation.
+//
+// Below the near limit (DR < 3 by default, Sec. 4) the paper integrates the
+// element analytically; it cites the formulas without printing them.  For a
+// uniformly charged planar polygon with unit normal n (corners counter-
+// clockwise about n) and field point P at signed height h = (P - V)·n:
+//   int dA / R         = sum_e d_e l_e - h Omega
+//   int (P - Q)/R^3 dA = sum_e m_e l_e + n Omega
+// where for edge e: t_e its unit direction, m_e = t_e x n the outward
+// in-plane normal, d_e = (V1 - P)·m_e, l_e = int_e ds / R = ln((s2 + R2) /
+// (s1 + R1)) with s_k = (V_k - P)·t_e, R_k = |V_k - P|, and Omega the solid
+// angle of the polygon seen from P with the sign of h (Van Oosterom and
+// Strackee's formula on each triangle).  The edge logarithm is evaluated in
+// whichever of its three equivalent forms has no cancellation.
+#include "bem_internal.cuh"
+
+namespace bem {
+
+namespace {
+
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 sub(D3 a, D3 b) { return D3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double dot(D3 a, D3 b) { return fma(a.x, b.x, fma(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ D3 cross(D3 a, D3 b) {
+    return D3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ D3 scale(D3 a, double s) { return D3{a.x * s, a.y * s, a.z * s}; }
+
+// Signed solid angle of triangle (a, b, c) (relative positions from P), with
+// the sign of h for a triangle counter-clockwise about the normal.
+__device__ double solid_angle(D3 a, D3 b, D3 c) {
+    const double la = sqrt(dot(a, a)), lb = sqrt(dot(b, b)), lc = sqrt(dot(c, c));
+    const double trip = dot(a, cross(b, c));  // = -2 area h
+    const double den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
+    return -2.0 * atan2(trip, den);
+}
+
+// phi and E (unit sigma, without 1/(4 pi eps0)) of element with corners V
+// (3 for a triangle, 4 for a rectangle) at P.
+__device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double out[4]) {
+    D3 c[4];
+    for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);  // corners relative to P
+    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
+    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    const double h = -dot(c[0], nrm);  // (P - V0)·n
+    double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    double r[4];
+    for (int k = 0; k < nv; ++k) r[k] = sqrt(dot(c[k], c[k]));
+    for (int k = 0; k < nv; ++k) {
+        const int k2 = (k + 1 == nv) ? 0 : k + 1;
+        D3 t = sub(c[k2], c[k]);
+        t = scale(t, 1.0 / sqrt(dot(t, t)));
+        const D3 m = cross(t, nrm);
+        const double s1 = dot(c[k], t), s2 = dot(c[k2], t);
+        const double d = dot(c[k], m);
+        double num, den;
+        if (s1 >= 0.0) {
+            num = r[k2] + s2;
+            den = r[k] + s1;
+        } else if (s2 <= 0.0) {
+            num = r[k] - s1;
+            den = r[k2] - s2;
+        } else {  // the foot of the perpendicular lies inside the edge
+            num = (r[k2] + s2) * (r[k] - s1);
+            den = fma(d, d, h * h);
+        }
+        // a point on the closed edge: the edge adds d l -> 0 to the potential
+        // and its (log-singular) in-plane field is left out
+        const double l = den == 0.0 ? 0.0 : log(num / den);
+        phi = fma(d, l, phi);
+        ex = fma(m.x, l, ex);
+        ey = fma(m.y, l, ey);
+        ez = fma(m.z, l, ez);
+    }
+    double om = 0.0;
+    if (h != 0.0) {
+        if (nv == 3) om = solid_angle(c[0], c[1], c[2]);
+        else om = solid_angle(c[0], c[1], c[3]) + solid_angle(c[1], c[2], c[3]);
+    }
+    out[0] = phi - h * om;
+    out[1] = fma(nrm.x, om, ex);
+    out[2] = fma(nrm.y, om, ey);
+    out[3] = fma(nrm.z, om, ez);
+}
+
+__global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
+                            const double* __restrict__ pts, const int* __restrict__ perm,
+                            const int* __restrict__ near_off, const int* __restrict__ type,
+                            const double* __restrict__ verts, const double* __restrict__ sigma,
+                            double4* __restrict__ val) {
+    const unsigned long long n = min(counters[0], cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int4 r = rec[i];
+        const int src = perm[r.x];
+        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
+        double f[4];
+        polygon_field(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
+        const double sg = sigma[r.y];
+        const unsigned long long slot = (unsigned long long)near_off[r.x] + (unsigned long long)r.z;
+        if (slot < cap) val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
+    }
+}
+
+// far sums + near contributions in element order, times 1/(4 pi eps0),
+// written at the point's original position.
+__global__ void k_finalize(int n, const int* __restrict__ perm, const double4* __restrict__ far,
+                           const int* __restrict__ near_cnt, const int* __restrict__ near_off,
+                           const double4* __restrict__ val, unsigned long long cap, double kc, double* phi, double* E,
+                           int stride4) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 s = far[i];
+    const int cnt = near_cnt[i];
+    const unsigned long long off = (unsigned long long)near_off[i];
+    for (int k = 0; k < cnt; ++k) {
+        if (off + k >= cap) break;
+        const double4 v = val[off + k];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+    }
+    const int o = perm[i];
+    if (stride4) {  // packed (phi, Ex, Ey, Ez) per point
+        phi[4 * (size_t)o] = kc * s.x;
+        phi[4 * (size_t)o + 1] = kc * s.y;
+        phi[4 * (size_t)o + 2] = kc * s.z;
+        phi[4 * (size_t)o + 3] = kc * s.w;
+        return;
+    }
+    if (phi) phi[o] = kc * s.x;
+    if (E) {
+        E[3 * (size_t)o] = kc * s.y;
+        E[3 * (size_t)o + 1] = kc * s.z;
+        E[3 * (size_t)o + 2] = kc * s.w;
+    }
+}
+
+__global__ void k_near_assemble(const int4* __restrict__ rec, const unsigned long long* counters,
+                                unsigned long long cap, const double* __restrict__ pts, const int* __restrict__ perm,
+                                const int* __restrict__ type, const double* __restrict__ verts, int n_el, double kc,
+                                double* __restrict__ A) {
+    const unsigned long long n = min(counters[0], cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int4 r = rec[i];
+        const int src = perm[r.x];
+        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
+        double f[4];
+        polygon_field(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
+        A[(size_t)src * n_el + r.y] = kc * f[0];
+    }
+}
+
+}  // namespace
+
+int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
+                     unsigned long long /*n_near_hint*/, cudaStream_t s) {
+    (void)n_pts;
+    Work& w = m->w;
+    k_near_eval<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
+                                        m->d.type, m->d.verts, sigma, w.near_val);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
+
+int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int stride4, cudaStream_t s) {
+    Work& w = m->w;
+    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, perm, w.far, w.near_cnt, w.near_off, w.near_val,
+                                                   (unsigned long long)w.cap_near, m->kc, phi, E, stride4);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
+
+int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double* A, unsigned long long,
+                         cudaStream_t s) {
+    Work& w = m->w;
+    k_near_assemble<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm,
+                                            m->d.type, m->d.verts, m->d.n, m->kc, A);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
+
+}  // namespace bem

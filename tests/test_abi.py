@@ -1,0 +1,106 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/bem.h declares; host-only queries (rule tables, error strings)
+work without a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1606_03743_gb300 as bem
+from paper_1606_03743_gb300 import build as bem_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                txt = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+            names |= set(re.findall(r"\b(bem_\w+)\s*\(", txt))
+    return names
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("bem_create", "bem_destroy", "bem_eval", "bem_assemble", "bem_matvec", "bem_set_sigma",
+                 "bem_last_error"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol():
+    lib_path = bem_build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    missing = _declared() - exported
+    assert not missing, missing
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name)
+
+
+def test_version_and_error_strings():
+    assert "sm_103a" in bem.bem_version()
+    assert isinstance(bem.bem_last_error(), str)
+
+
+def test_bad_rule_query_sets_error():
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_rule(2, 0)
+    assert e.value.code == -1
+    assert "bem_rule" in bem.bem_last_error()
+
+
+@pytest.mark.parametrize("type_,sizes,degrees", [(0, (4, 7, 12, 19, 33), (3, 5, 7, 9, 12)),
+                                                 (1, (4, 7, 12, 17, 33), (3, 5, 7, 9, 13))])
+def test_library_rules_exact_to_degree(type_, sizes, degrees):
+    """The library's own node tables (alpha, beta, w): right node counts,
+    weights summing to one and exactness on monomials up to the degree
+    (App. A, App. B), checked in the library's coordinates: for a triangle
+    with corners e0 = (1, 0), e1 = (0, 1), e2 = (-1, -1) about its centroid,
+    and for the square [-1, 1]^2 (e0 = (1, 0), e1 = (0, 1))."""
+    for r in range(5):
+        nodes = bem.bem_rule(type_, r)
+        assert nodes.shape[0] == sizes[r]
+        assert abs(nodes[:, 2].sum() - 1.0) < 1e-15
+        x, y, w = nodes[:, 0], nodes[:, 1], nodes[:, 2]
+        # exact moments by a high-order product rule on the same region
+        if type_ == 1:
+            g, gw = np.polynomial.legendre.leggauss(20)
+            X, Y = np.meshgrid(g, g, indexing="ij")
+            W = np.outer(gw, gw) / 4.0
+        else:
+            # collapsed map of the triangle (1,0), (0,1), (-1,-1), Jacobian u
+            g, gw = np.polynomial.legendre.leggauss(20)
+            u, v = (g + 1) / 2, (g + 1) / 2
+            U, V = np.meshgrid(u, v, indexing="ij")
+            A, B, Cc = np.array([1.0, 0.0]), np.array([0.0, 1.0]), np.array([-1.0, -1.0])
+            X = A[0] + U * (B[0] - A[0]) + U * V * (Cc[0] - B[0])
+            Y = A[1] + U * (B[1] - A[1]) + U * V * (Cc[1] - B[1])
+            W = np.outer(gw, gw) / 4.0 * U * 2.0  # normalised to unit mass
+        tol = 5e-14 if (type_ == 0 and sizes[r] == 12) else 5e-15
+        for n in range(degrees[r] + 1):
+            for m in range(degrees[r] + 1 - n):
+                ex = np.sum(W * X ** n * Y ** m)
+                val = np.sum(w * x ** n * y ** m)
+                assert abs(val - ex) <= tol * max(1.0, abs(ex)), (r, n, m, val, ex)
+
+
+def test_library_rules_match_oracle_tables():
+    """Both sides typed the appendix tables independently: the same nodes
+    (up to order) after mapping the oracle's barycentric rows to (alpha, beta)."""
+    for type_ in (0, 1):
+        for r in range(5):
+            lib = bem.bem_rule(type_, r)
+            orc = oracle.rule(type_, r)
+            if type_ == 0:
+                o = np.stack([orc[:, 0] - orc[:, 2], orc[:, 1] - orc[:, 2], orc[:, 3]], 1)
+            else:
+                o = np.stack([orc[:, 0], orc[:, 1], orc[:, 3]], 1)
+            key = lambda a: a[np.lexsort((a[:, 1], a[:, 0]))]
+            assert np.allclose(key(lib), key(o), rtol=0, atol=1e-15)
