@@ -181,6 +181,37 @@ int bem_last_times(const bem_mesh* mesh, double* out /* 4 */);
  * (all meshes, all devices). */
 int64_t bem_kernel_launches(void);
 
+/*
+ * bem_eval_noalloc -- bem_eval that allocates no device memory.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * let the library call cudaMalloc -- an application that hands all device
+ * memory to its own pool up front, or a latency-critical loop (a particle
+ * tracker asking for fields at every step) that must never wait on the
+ * allocator.  bem_eval grows the mesh's scratch buffers on demand; this call
+ * instead takes all of its scratch from one fixed array of
+ * BEM_NOALLOC_BYTES bytes in device memory, which every GPU that loads the
+ * library holds until the process exits.  It runs the same kernels, so its
+ * results equal bem_eval's.
+ *   points [n][3], phi [n] (or NULL), E [n][3] (or NULL): device arrays of
+ *   the mesh's device; host arrays are rejected (BEM_ERR_INVALID).
+ *   n <= BEM_NOALLOC_MAX_POINTS, else BEM_ERR_INVALID.
+ * If the points have more than BEM_NOALLOC_MAX_NEAR near-field (analytic)
+ * pairs the call returns BEM_ERR_CAPACITY and phi / E hold incomplete
+ * values: split the points, or use bem_eval.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the one array, which keeps the previous
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU -- from two host threads or on two streams -- race.
+ * The call returns after its results are complete (it synchronises the
+ * stream).
+ */
+#define BEM_NOALLOC_MAX_POINTS 32768
+#define BEM_NOALLOC_MAX_NEAR 262144
+#define BEM_NOALLOC_BYTES (14u << 20)
+int bem_eval_noalloc(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bem_last_error(void);
 

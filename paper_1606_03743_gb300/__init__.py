@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
@@ -73,6 +73,8 @@ def load_library(build_if_missing: bool = True):
     lib.bem_set_timing.argtypes = [vp, C.c_int32]
     lib.bem_last_times.argtypes = [vp, d]
     lib.bem_kernel_launches.restype = C.c_int64
+    lib.bem_eval_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    lib.bem_eval_noalloc.restype = C.c_int
     lib.bem_last_error.restype = C.c_char_p
     lib.bem_version.restype = C.c_char_p
     for name in ("bem_create", "bem_set_sigma", "bem_eval", "bem_assemble", "bem_matvec", "bem_centroids",
@@ -192,6 +194,20 @@ def bem_eval(mesh: int, points, phi=None, E=None, stream=None) -> None:
     n = p.numel() // 3 if _is_torch(p) else p.size // 3
     _check(load_library().bem_eval(mesh, pp, n, _ptr(phi) if phi is not None else None,
                                    _ptr(E) if E is not None else None, _stream(stream)))
+
+
+# limits of bem_eval_noalloc (include/bem.h)
+NOALLOC_MAX_POINTS = 32768
+NOALLOC_MAX_NEAR = 262144
+
+
+def bem_eval_noalloc(mesh: int, points, phi=None, E=None, stream=None) -> None:
+    """bem_eval with all scratch in a fixed device array (no allocation);
+    points, phi and E must be CUDA tensors, at most NOALLOC_MAX_POINTS points."""
+    p, pp = _prep(points, np.float64)
+    n = p.numel() // 3 if _is_torch(p) else p.size // 3
+    _check(load_library().bem_eval_noalloc(mesh, pp, n, _ptr(phi) if phi is not None else None,
+                                           _ptr(E) if E is not None else None, _stream(stream)))
 
 
 def bem_assemble(mesh: int, colloc, A, stream=None) -> None:
