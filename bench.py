@@ -264,6 +264,10 @@ def main():
                          "mufu_frac": mufu_frac},
             "band_pairs": {"triangle": [int(x) for x in stats[0:6]], "rectangle": [int(x) for x in stats[6:12]],
                            "order": "analytic, 33, 19|17, 12, 7, 4 points"},
+            "far_kernel_work": {"warp_element_uniform": int(stats[13]), "warp_element_mixed": int(stats[14]),
+                                "node_evals_executed": int(stats[15]),
+                                "node_evals_algorithmic": int(rsq),
+                                "executed_over_algorithmic": float(stats[15]) / rsq if rsq else None},
             "clocks": ck}
 
     if rank == 0 and world == 1 and not a.no_extras:
@@ -331,8 +335,9 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     ns = min(a.cpu_sample, a.points)
     nt = oracle.max_threads()
     t0c = time.perf_counter()
-    rphi, rE, mdr = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[:ns], nthreads=nt,
-                                      return_min_dr=True)
+    rphi, rE, mdr, esum = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[:ns], nthreads=nt,
+                                            return_min_dr=True, return_esum=True)
+    kappa = esum / np.linalg.norm(rE, axis=1)
     cpu_s = time.perf_counter() - t0c
     out["cpu_baseline"] = {"value": ns * mesh.n / cpu_s, "unit": UNIT, "cores": nt, "kind": "oracle",
                            "sample": f"first {ns} of the {a.points} points x all {mesh.n} elements ({cpu_s:.1f} s)"}
@@ -343,17 +348,25 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     k = min(ns, n64)
 
     def errs(p, e, rp, re, sel):
-        ep = np.abs(p - rp) / np.abs(rp)
-        eE = np.linalg.norm(e - re, axis=1) / np.linalg.norm(re, axis=1)
+        n = len(p)
+        sel = sel[:n]
+        ep = np.abs(p - rp[:n]) / np.abs(rp[:n])
+        dE = np.linalg.norm(e - re[:n], axis=1)
+        eE = dE / np.linalg.norm(re[:n], axis=1)
+        eEc = dE / esum[:n]  # |dE| / sum_j |E_j|: error relative to the size of the terms
         return {"max_rel_phi": float(ep[sel].max(initial=0)), "max_rel_E": float(eE[sel].max(initial=0)),
                 "mean_rel_phi": float(ep[sel].mean()) if sel.any() else 0.0,
-                "mean_rel_E": float(eE[sel].mean()) if sel.any() else 0.0, "n": int(sel.sum())}
+                "mean_rel_E": float(eE[sel].mean()) if sel.any() else 0.0,
+                "max_E_over_sum_abs_Ej": float(eEc[sel].max(initial=0)), "n": int(sel.sum())}
 
-    bands = {"min_DR>=3": mdr >= 3, "min_DR<3": mdr < 3}
+    bands = {"min_DR>=3,kappa<=100": (mdr >= 3) & (kappa <= 100), "min_DR>=3": mdr >= 3, "min_DR<3": mdr < 3}
     out["accuracy_vs_oracle"] = {
         "run_precision": a.precision,
         "bands": {b: errs(gphi, gE, rphi, rE, s) for b, s in bands.items()},
-        "fp64_path": {b: errs(g64phi[:k], g64E[:k], rphi[:k], rE[:k], s[:k]) for b, s in bands.items()},
+        "fp64_path": {b: errs(g64phi[:k], g64E[:k], rphi, rE, s) for b, s in bands.items()},
+        "kappa": {"definition": "sum_j |E_j| / |E| (oracle)", "median": float(np.median(kappa)),
+                  "p99": float(np.percentile(kappa, 99)), "max": float(kappa.max()),
+                  "frac_above_100": float((kappa > 100).mean())},
         "points": ns}
     m64.close()
     return out

@@ -160,10 +160,14 @@ int bem_rule(int32_t type, int32_t r, double* out);
 /* Statistics of the last bem_eval / bem_assemble / bem_matvec on this mesh:
  * out[0..5] pair counts per distance-ratio band for triangles (analytic,
  * 33, 19, 12, 7, 4 points), out[6..11] the same for rectangles (analytic,
- * 33, 17, 12, 7, 4 points), out[12] the number of near (analytic) pairs.
- * out[0..11] are filled only by calls made with statistics enabled
- * (bem_set_stats); out[12] always. */
-int bem_last_stats(const bem_mesh* mesh, int64_t* out /* 13 */);
+ * 33, 17, 12, 7, 4 points), out[12] the number of near (analytic) pairs,
+ * out[13] (warp, element) pairs where one band served all 32 x PT points
+ * of the warp, out[14] those that fell back to per-point bands, out[15]
+ * node evaluations executed by the far-field kernel (masked ones
+ * included; compare with the pairs x nodes of out[0..11]).
+ * out[0..11] and out[13..15] are filled only by calls made with statistics
+ * enabled (bem_set_stats); out[12] always. */
+int bem_last_stats(const bem_mesh* mesh, int64_t* out /* 16 */);
 
 /* Enable (1) or disable (0) the per-band pair counts of the next calls; the
  * counting variant of the far-field kernel is slower, so it is off by default. */
@@ -207,9 +211,9 @@ int64_t bem_kernel_launches(void);
  * The call returns after its results are complete (it synchronises the
  * stream).
  */
-#define BEM_NOALLOC_MAX_POINTS 32768
+#define BEM_NOALLOC_MAX_POINTS 16384
 #define BEM_NOALLOC_MAX_NEAR 262144
-#define BEM_NOALLOC_BYTES (14u << 20)
+#define BEM_NOALLOC_BYTES (24u << 20)
 int bem_eval_noalloc(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
 
 /* Message of the last failure on the calling thread ("" if none). */

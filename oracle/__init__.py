@@ -61,7 +61,7 @@ def _load():
         lib.oracle_element.argtypes = [C.c_int, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
         lib.oracle_element.restype = C.c_int
         lib.oracle_eval.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d,
-                                    C.c_int, C.c_int, C.c_int, i64, d]
+                                    C.c_int, C.c_int, C.c_int, i64, d, d]
         lib.oracle_eval.restype = C.c_int
         lib.oracle_assemble.argtypes = [C.c_int64, i32, d, d, C.c_double, C.c_int64, C.c_int64, d, d, C.c_int]
         lib.oracle_assemble.restype = C.c_int
@@ -153,9 +153,11 @@ def element_batch(types, verts, P, method: int = METHOD_PAPER, param: int = 0, l
 
 def eval_field(types, verts, sigma, pts, method: int = METHOD_PAPER, param: int = 16, limits=None,
                eps0: float = 0.0, nthreads: int | None = None, return_hist: bool = False,
-               return_min_dr: bool = False):
+               return_min_dr: bool = False, return_esum: bool = False):
     """phi (n,) and E (n, 3) at the field points, summed over all elements in
-    index order, including 1/(4 pi eps0) (eps0 <= 0 selects the SI value)."""
+    index order, including 1/(4 pi eps0) (eps0 <= 0 selects the SI value).
+    Optional extras, in this order: the (2, 6) band histogram, the per-point
+    minimum distance ratio, the per-point sum of |E_j| over elements."""
     types = np.ascontiguousarray(types, dtype=np.int32)
     verts = _f64(verts, (types.shape[0], 4, 3))
     sigma = _f64(sigma, (types.shape[0],))
@@ -165,11 +167,12 @@ def eval_field(types, verts, sigma, pts, method: int = METHOD_PAPER, param: int 
     E = np.zeros((n, 3))
     hist = np.zeros(12, np.int64)
     mdr = np.zeros(n) if return_min_dr else None
+    esum = np.zeros(n) if return_esum else None
     lim = None if limits is None else _f64(limits, (10,))
     nt = nthreads or max_threads()
     rc = _load().oracle_eval(types.shape[0], types.ctypes.data_as(C.POINTER(C.c_int32)), _dp(verts), _dp(sigma),
                              _dp(lim), eps0, n, _dp(pts), _dp(phi), _dp(E), method, param, nt,
-                             hist.ctypes.data_as(C.POINTER(C.c_int64)), _dp(mdr))
+                             hist.ctypes.data_as(C.POINTER(C.c_int64)), _dp(mdr), _dp(esum))
     if rc != 0:
         raise ValueError("oracle_eval: bad arguments")
     out = [phi, E]
@@ -177,6 +180,8 @@ def eval_field(types, verts, sigma, pts, method: int = METHOD_PAPER, param: int 
         out.append(hist.reshape(2, 6))
     if return_min_dr:
         out.append(mdr)
+    if return_esum:
+        out.append(esum)
     return tuple(out)
 
 

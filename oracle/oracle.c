@@ -681,11 +681,14 @@ int oracle_element(int type, const double* verts, const double* P, int method, i
  *   hist:   optional 2 x 6 pair counts per (type, band) -- band 0 is the
  *           analytic branch, band 1 + r is cubature rule r
  *   min_dr: optional per-point minimum distance ratio over all elements
+ *   esum:   optional per-point sum over elements of |E_j| (times
+ *           1/(4 pi eps0)); esum / |E| is the condition number of the field
+ *           sum, the factor by which cancellation magnifies rounding
  */
 int oracle_eval(int64_t n_el, const int32_t* type, const double* verts, const double* sigma,
                 const double* limits, double eps0, int64_t n_pts, const double* pts,
                 double* phi, double* E, int method, int param, int nthreads,
-                int64_t* hist, double* min_dr)
+                int64_t* hist, double* min_dr, double* esum)
 {
     const double kc = coulomb_k(eps0);
     int64_t p, j;
@@ -704,7 +707,7 @@ int oracle_eval(int64_t n_el, const int32_t* type, const double* verts, const do
 #pragma omp for schedule(dynamic, 4)
         for (p = 0; p < n_pts; ++p) {
             const double* P = pts + 3 * p;
-            double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0}, mdr = INFINITY;
+            double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0}, mdr = INFINITY, eabs = 0.0;
             int64_t jj;
             int k;
             for (jj = 0; jj < n_el; ++jj) {
@@ -726,10 +729,12 @@ int oracle_eval(int64_t n_el, const int32_t* type, const double* verts, const do
                 }
                 if (dr < mdr) mdr = dr;
                 for (k = 0; k < 4; ++k) nsum_add(&s[k], &c[k], sigma[jj] * f[k]);
+                eabs += fabs(sigma[jj]) * sqrt(f[1] * f[1] + f[2] * f[2] + f[3] * f[3]);
             }
             phi[p] = kc * (s[0] + c[0]);
             for (k = 0; k < 3; ++k) E[3 * p + k] = kc * (s[k + 1] + c[k + 1]);
             if (min_dr) min_dr[p] = mdr;
+            if (esum) esum[p] = kc * eabs;
         }
 #pragma omp critical
         for (j = 0; j < 12; ++j) hist_local[j] += h_thr[j];

@@ -197,7 +197,7 @@ def bem_eval(mesh: int, points, phi=None, E=None, stream=None) -> None:
 
 
 # limits of bem_eval_noalloc (include/bem.h)
-NOALLOC_MAX_POINTS = 32768
+NOALLOC_MAX_POINTS = 16384
 NOALLOC_MAX_NEAR = 262144
 
 
@@ -245,7 +245,7 @@ def bem_kernel_launches() -> int:
 
 
 def bem_last_stats(mesh: int) -> np.ndarray:
-    out = np.zeros(13, np.int64)
+    out = np.zeros(16, np.int64)
     _check(load_library().bem_last_stats(mesh, out.ctypes.data_as(C.POINTER(C.c_int64))))
     return out
 

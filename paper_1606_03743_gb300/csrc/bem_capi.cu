@@ -19,6 +19,7 @@ const double kDefaultLimits[2][5] = {{3.0, 12.0, 30.0, 120.0, 2250.0}, {3.0, 18.
 constexpr double kEps0SI = 8.8541878128e-12;
 constexpr int kMaxCellBits = 7;  // must match the key width of k_sort.cu
 constexpr size_t kCells = size_t(1) << (3 * kMaxCellBits);
+constexpr size_t kCounters = 24;
 }  // namespace
 
 void set_error(const char* fmt, ...) {
@@ -79,15 +80,15 @@ void dfree(bem_mesh* m, T** p, size_t count) {
 
 void free_points(bem_mesh* m) {
     Work& w = m->w;
-    const size_t c = w.cap_pts;
+    const size_t c = w.cap_pts, cs = c * (size_t)m->n_chunks;
     dfree(m, &w.pts, 3 * c);
     dfree(m, &w.out, 4 * c);
     dfree(m, &w.perm, c);
     dfree(m, &w.key, c);
-    dfree(m, &w.far, c);
-    dfree(m, &w.near_cnt, c);
-    dfree(m, &w.near_off, c);
-    dfree(m, &w.scan_tmp, scan_tmp_ints((int)std::max(c, kCells)));
+    dfree(m, &w.part, cs);
+    dfree(m, &w.near_cnt, cs);
+    dfree(m, &w.near_off, cs);
+    dfree(m, &w.scan_tmp, scan_tmp_ints((int)std::max(cs, kCells)));
     w.cap_pts = 0;
 }
 
@@ -104,10 +105,15 @@ int ensure_points(bem_mesh* m, size_t n) {
     free_points(m);
     size_t c = 1024;
     while (c < n) c *= 2;
+    const size_t cs = c * (size_t)m->n_chunks;
+    if (cs >= (size_t(1) << 31)) {
+        set_error("too many field points for one call (%zu x %d element chunks)", n, m->n_chunks);
+        return BEM_ERR_INVALID;
+    }
     int rc;
     if ((rc = dalloc(m, &w.pts, 3 * c)) || (rc = dalloc(m, &w.out, 4 * c)) || (rc = dalloc(m, &w.perm, c)) ||
-        (rc = dalloc(m, &w.key, c)) || (rc = dalloc(m, &w.far, c)) || (rc = dalloc(m, &w.near_cnt, c)) ||
-        (rc = dalloc(m, &w.near_off, c)) || (rc = dalloc(m, &w.scan_tmp, scan_tmp_ints((int)std::max(c, kCells))))) {
+        (rc = dalloc(m, &w.key, c)) || (rc = dalloc(m, &w.part, cs)) || (rc = dalloc(m, &w.near_cnt, cs)) ||
+        (rc = dalloc(m, &w.near_off, cs)) || (rc = dalloc(m, &w.scan_tmp, scan_tmp_ints((int)std::max(cs, kCells))))) {
         w.cap_pts = c;
         free_points(m);
         return rc;
@@ -193,14 +199,15 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
              bool want_e, cudaStream_t s) {
     Work& w = m->w;
     for (int attempt = 0; attempt < 3; ++attempt) {
-        BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 16 * sizeof(unsigned long long), s));
+        BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, kCounters * sizeof(unsigned long long), s));
         FarArgs a{};
         a.pts = dpts;
         a.perm = w.perm;
         a.n_pts = n;
         a.sigma = dsigma;
-        a.far = w.far;
+        a.part = w.part;
         a.near_cnt = w.near_cnt;
+        a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;
         a.near_cap = w.cap_near;
@@ -211,12 +218,12 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         int rc = launch_far(m, a, s);
         if (rc) return rc;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[2], s));
-        if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n, w.scan_tmp, s))) return rc;
+        if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n * m->n_chunks, w.scan_tmp, s))) return rc;
         if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s))) return rc;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[3], s));
         if ((rc = launch_finalize(m, w.perm, n, dphi, dE, stride4, s))) return rc;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[4], s));
-        unsigned long long cnt[14];
+        unsigned long long cnt[kCounters];
         BEM_CUDA_TRY(cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
         if (m->timing) {
@@ -228,8 +235,10 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         }
         if (cnt[0] <= w.cap_near) {
             m->last_stats[12] = (int64_t)cnt[0];
-            if (m->stats)
+            if (m->stats) {
                 for (int k = 0; k < 12; ++k) m->last_stats[k] = (int64_t)cnt[2 + k];
+                for (int k = 0; k < 3; ++k) m->last_stats[13 + k] = (int64_t)cnt[16 + k];
+            }
             return BEM_OK;
         }
         if ((rc = ensure_near(m, (size_t)cnt[0]))) return rc;  // grow and run again
@@ -297,6 +306,11 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
         return cuda_fail(ce, "cudaGetDevice");
     }
     m->d.n = (int)n;
+    // the far-field pass splits the elements into chunks fixed by the mesh
+    // (so a point's sum is always split the same way), about 32k elements each
+    m->n_chunks = (int)std::min<int64_t>(16, std::max<int64_t>(1, (n + 32767) / 32768));
+    m->chunk_len = (int)(((n + m->n_chunks - 1) / m->n_chunks + 31) / 32 * 32);
+    m->n_chunks = (int)((n + m->chunk_len - 1) / m->chunk_len);
     MeshDev& d = m->d;
     int rc = BEM_OK;
     // element arrays are owned by the mesh, outside the scratch budget
@@ -322,7 +336,7 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     BEM_ALLOC(d.sigma, nn);
     BEM_ALLOC(m->w.cell_cnt, kCells);
     BEM_ALLOC(m->w.cell_off, kCells);
-    BEM_ALLOC(m->w.counters, 16);
+    BEM_ALLOC(m->w.counters, kCounters);
     BEM_ALLOC(m->w.bbox, 2);
 #undef BEM_ALLOC
     if (rc) {
@@ -394,7 +408,7 @@ int bem_last_stats(const bem_mesh* m, int64_t* out) {
         set_error("bem_last_stats: out is NULL");
         return BEM_ERR_INVALID;
     }
-    for (int k = 0; k < 13; ++k) out[k] = m->last_stats[k];
+    for (int k = 0; k < 16; ++k) out[k] = m->last_stats[k];
     return BEM_OK;
 }
 
@@ -520,7 +534,7 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
     rc = launch_sort_points(m, dpts, (int)mrows, s);
     if (!rc) rc = check_points(m, "bem_assemble", s);
     for (int attempt = 0; !rc && attempt < 3; ++attempt) {
-        cudaError_t e = cudaMemsetAsync(w.counters, 0, 16 * sizeof(unsigned long long), s);
+        cudaError_t e = cudaMemsetAsync(w.counters, 0, kCounters * sizeof(unsigned long long), s);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "bem_assemble");
             break;
@@ -530,8 +544,8 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
         a.perm = w.perm;
         a.n_pts = (int)mrows;
         a.sigma = nullptr;  // assembly: unit charge density
-        a.far = w.far;
         a.near_cnt = w.near_cnt;
+        a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;
         a.near_cap = w.cap_near;
@@ -540,7 +554,7 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
         a.stats = m->stats;
         if ((rc = launch_far(m, a, s))) break;
         if ((rc = launch_near_assemble(m, dpts, w.perm, dA, 0, s))) break;
-        unsigned long long cnt[14];
+        unsigned long long cnt[kCounters];
         e = cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
@@ -549,8 +563,10 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
         }
         if (cnt[0] <= w.cap_near) {
             m->last_stats[12] = (int64_t)cnt[0];
-            if (m->stats)
+            if (m->stats) {
                 for (int k = 0; k < 12; ++k) m->last_stats[k] = (int64_t)cnt[2 + k];
+                for (int k = 0; k < 3; ++k) m->last_stats[13 + k] = (int64_t)cnt[16 + k];
+            }
             break;
         }
         rc = ensure_near(m, (size_t)cnt[0]);

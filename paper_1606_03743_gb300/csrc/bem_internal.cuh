@@ -43,7 +43,6 @@ struct MeshDev {
     double* verts = nullptr;  // [n][12] corners as given
     int* type = nullptr;      // [n]
     double* sigma = nullptr;  // [n]
-    double* cen_sorted_scratch = nullptr;
 };
 
 // Per-call scratch (grown on demand, owned by the mesh).
@@ -55,14 +54,16 @@ struct Work {
     unsigned* key = nullptr;      // spatial cell key per point
     int* cell_cnt = nullptr;      // histogram of cells
     int* cell_off = nullptr;      // exclusive scan of cell_cnt
-    double4* far = nullptr;       // far-field sums per sorted point
-    int* near_cnt = nullptr;      // near pairs per sorted point
+    double4* part = nullptr;      // far-field sums per (sorted point, element chunk)
+    int* near_cnt = nullptr;      // near pairs per (sorted point, element chunk)
     int* near_off = nullptr;      // exclusive scan of near_cnt
     int* scan_tmp = nullptr;      // block sums of the scans
     size_t cap_near = 0;
-    int4* near_rec = nullptr;     // (sorted point, element, ordinal, -)
+    int4* near_rec = nullptr;     // (sorted point, element, ordinal, chunk)
     double4* near_val = nullptr;  // analytic contributions in (point, ordinal) order
-    unsigned long long* counters = nullptr;  // [0] near pairs, [1] error flags, [2..13] band stats
+    unsigned long long* counters = nullptr;  // [0] near pairs, [1] bad element, [2..13] band stats,
+                                             // [14] far work-item counter, [15] bad field point,
+                                             // [16..18] far-kernel efficiency counts (statistics runs)
     float4* bbox = nullptr;       // [2] points bbox (min, max)
     size_t bytes = 0;
 };
@@ -77,9 +78,11 @@ struct bem_mesh {
     double eps0 = 8.8541878128e-12;
     double kc = 0.0;          // 1 / (4 pi eps0)
     double limits[2][5];      // DR band limits per type
+    int n_chunks = 1;         // element chunks of the far-field pass (fixed by the mesh)
+    int chunk_len = 0;        // elements per chunk (a multiple of 32)
     size_t budget = 0;
     bool stats = false;
-    int64_t last_stats[13] = {0};
+    int64_t last_stats[16] = {0};
     bool timing = false;
     double last_times[4] = {0, 0, 0, 0};
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -105,7 +108,6 @@ int cuda_fail(cudaError_t e, const char* what);
 // element through *bad (-1 if none) after synchronising.
 int launch_prep(bem_mesh* m, const int* types, const double* verts, const double* sigma, cudaStream_t s,
                 int64_t* bad, int* bad_code);
-int launch_set_q(bem_mesh* m, cudaStream_t s);
 
 // Spatial sort of field points (k_sort.cu): perm = points in cell order.
 int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s);
@@ -118,8 +120,9 @@ struct FarArgs {
     const int* perm;     // sorted -> original
     int n_pts;
     const double* sigma; // per element charge density (eval) or the x of a matvec
-    double4* far;        // out: far sums per sorted point
-    int* near_cnt;       // out: near pairs per sorted point
+    double4* part;       // out: far sums per (sorted point, chunk)
+    int* near_cnt;       // out: near pairs per (sorted point, chunk)
+    int* work;           // work-item counter, zero at launch
     int4* near_rec;      // out: near pair list
     unsigned long long* counters;
     unsigned long long near_cap;
@@ -130,6 +133,7 @@ struct FarArgs {
 };
 // Far-field cubature + near-pair compaction (k_far.cu).
 int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s);
+int far_points_per_tile(int precision);
 // Analytic near field over the compacted list and the per-point finalisation (k_near.cu).
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
                      unsigned long long n_near, cudaStream_t s);

@@ -88,7 +88,7 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double
 
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
-                            const int* __restrict__ near_off, const int* __restrict__ type,
+                            const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
                             const double* __restrict__ verts, const double* __restrict__ sigma,
                             double4* __restrict__ val) {
     const unsigned long long n = min(counters[0], cap);
@@ -100,22 +100,32 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
         double f[4];
         polygon_field(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
         const double sg = sigma[r.y];
-        const unsigned long long slot = (unsigned long long)near_off[r.x] + (unsigned long long)r.z;
+        const unsigned long long slot =
+            (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
         if (slot < cap) val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
     }
 }
 
-// far sums + near contributions in element order, times 1/(4 pi eps0),
-// written at the point's original position.
-__global__ void k_finalize(int n, const int* __restrict__ perm, const double4* __restrict__ far,
+// far sums of the element chunks in chunk order + near contributions in
+// element order, times 1/(4 pi eps0), written at the point's original position.
+__global__ void k_finalize(int n, int n_chunks, const int* __restrict__ perm, const double4* __restrict__ part,
                            const int* __restrict__ near_cnt, const int* __restrict__ near_off,
                            const double4* __restrict__ val, unsigned long long cap, double kc, double* phi, double* E,
                            int stride4) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double4 s = far[i];
-    const int cnt = near_cnt[i];
-    const unsigned long long off = (unsigned long long)near_off[i];
+    const size_t p0 = (size_t)i * n_chunks;
+    double4 s = part[p0];
+    int cnt = near_cnt[p0];
+    for (int c = 1; c < n_chunks; ++c) {
+        const double4 v = part[p0 + c];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+        cnt += near_cnt[p0 + c];
+    }
+    const unsigned long long off = (unsigned long long)near_off[p0];
     for (int k = 0; k < cnt; ++k) {
         if (off + k >= cap) break;
         const double4 v = val[off + k];
@@ -163,7 +173,7 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
     (void)n_pts;
     Work& w = m->w;
     k_near_eval<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
-                                        m->d.type, m->d.verts, sigma, w.near_val);
+                                        m->n_chunks, m->d.type, m->d.verts, sigma, w.near_val);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
@@ -171,7 +181,7 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
 
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int stride4, cudaStream_t s) {
     Work& w = m->w;
-    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, perm, w.far, w.near_cnt, w.near_off, w.near_val,
+    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, m->n_chunks, perm, w.part, w.near_cnt, w.near_off, w.near_val,
                                                    (unsigned long long)w.cap_near, m->kc, phi, E, stride4);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);

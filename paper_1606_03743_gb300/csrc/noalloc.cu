@@ -25,7 +25,8 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 
 constexpr size_t kMaxPts = BEM_NOALLOC_MAX_POINTS;
 constexpr size_t kMaxNear = BEM_NOALLOC_MAX_NEAR;
-constexpr size_t kCellsMax = 4096;     // the sort uses at most 2^(3*4) cells for <= 2^15 points
+constexpr size_t kMaxChunks = 16;      // element chunks of the far-field pass (at most 16 per mesh)
+constexpr size_t kCellsMax = 4096;     // the sort uses at most 2^(3*3) cells for <= 2^14 points
 constexpr size_t kScanInts = 16384;    // block sums of every scan level, with room to spare
 
 // byte offsets of the scratch areas inside the array
@@ -33,14 +34,14 @@ constexpr size_t kOffPerm = 0;
 constexpr size_t kOffKey = kOffPerm + align_up(4 * kMaxPts);
 constexpr size_t kOffCellCnt = kOffKey + align_up(4 * kMaxPts);
 constexpr size_t kOffCellOff = kOffCellCnt + align_up(4 * kCellsMax);
-constexpr size_t kOffFar = kOffCellOff + align_up(4 * kCellsMax);
-constexpr size_t kOffNearCnt = kOffFar + align_up(32 * kMaxPts);
-constexpr size_t kOffNearOff = kOffNearCnt + align_up(4 * kMaxPts);
-constexpr size_t kOffScan = kOffNearOff + align_up(4 * kMaxPts);
+constexpr size_t kOffPart = kOffCellOff + align_up(4 * kCellsMax);
+constexpr size_t kOffNearCnt = kOffPart + align_up(32 * kMaxPts * kMaxChunks);
+constexpr size_t kOffNearOff = kOffNearCnt + align_up(4 * kMaxPts * kMaxChunks);
+constexpr size_t kOffScan = kOffNearOff + align_up(4 * kMaxPts * kMaxChunks);
 constexpr size_t kOffRec = kOffScan + align_up(4 * kScanInts);
 constexpr size_t kOffVal = kOffRec + align_up(16 * kMaxNear);
 constexpr size_t kOffCounters = kOffVal + align_up(32 * kMaxNear);
-constexpr size_t kOffBbox = kOffCounters + align_up(16 * 8);
+constexpr size_t kOffBbox = kOffCounters + align_up(24 * 8);
 constexpr size_t kBytes = kOffBbox + align_up(32);
 static_assert(kBytes <= BEM_NOALLOC_BYTES, "scratch layout outgrew the stated size");
 
@@ -116,7 +117,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     w.key = reinterpret_cast<unsigned*>(base + kOffKey);
     w.cell_cnt = reinterpret_cast<int*>(base + kOffCellCnt);
     w.cell_off = reinterpret_cast<int*>(base + kOffCellOff);
-    w.far = reinterpret_cast<double4*>(base + kOffFar);
+    w.part = reinterpret_cast<double4*>(base + kOffPart);
     w.near_cnt = reinterpret_cast<int*>(base + kOffNearCnt);
     w.near_off = reinterpret_cast<int*>(base + kOffNearOff);
     w.scan_tmp = reinterpret_cast<int*>(base + kOffScan);
@@ -127,7 +128,8 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     w.bbox = reinterpret_cast<float4*>(base + kOffBbox);
     view.stats = false;
     view.timing = false;
-    if (scan_tmp_ints((int)kMaxPts) > kScanInts || scan_tmp_ints((int)kCellsMax) > kScanInts) {
+    if (m->n_chunks > (int)kMaxChunks || scan_tmp_ints((int)(kMaxPts * kMaxChunks)) > kScanInts ||
+        scan_tmp_ints((int)kCellsMax) > kScanInts) {
         set_error("bem_eval_noalloc: internal scan scratch too small");
         return BEM_ERR_CAPACITY;
     }
@@ -148,8 +150,9 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.perm = w.perm;
     a.n_pts = (int)n;
     a.sigma = m->d.sigma;
-    a.far = w.far;
+    a.part = w.part;
     a.near_cnt = w.near_cnt;
+    a.work = reinterpret_cast<int*>(w.counters + 14);
     a.near_rec = w.near_rec;
     a.counters = w.counters;
     a.near_cap = w.cap_near;
@@ -157,7 +160,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.want_e = E != nullptr;
     a.stats = 0;
     if ((rc = launch_far(&view, a, s))) return rc;
-    if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)n, w.scan_tmp, s))) return rc;
+    if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)n * m->n_chunks, w.scan_tmp, s))) return rc;
     if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s))) return rc;
     if ((rc = launch_finalize(&view, w.perm, (int)n, phi, E, 0, s))) return rc;
     unsigned long long n_near = 0;

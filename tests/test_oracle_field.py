@@ -339,3 +339,15 @@ def test_potential_continuous_onto_an_edge(type_):
         for eps in (1e-9, 1e-11):
             near, _ = oracle.element(type_, verts, P + eps * (cen - P), oracle.METHOD_ANALYTIC)
             assert abs(near[0] - on[0]) < 1e-7 * abs(on[0])
+
+
+def test_esum_is_sum_of_element_field_norms():
+    mesh = synth.plate_mesh(seed=1, n=2)
+    pts = synth.plate_points(seed=2, n=4)
+    _, E, es = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts, return_esum=True)
+    k = oracle.coulomb_k()
+    for p in range(4):
+        ref = sum(abs(mesh.sigma[j]) * np.linalg.norm(oracle.element(int(mesh.types[j]), mesh.verts[j], pts[p])[0][1:])
+                  for j in range(mesh.n))
+        assert es[p] == pytest.approx(k * ref, rel=1e-13)
+        assert es[p] >= np.linalg.norm(E[p]) * (1 - 1e-12)  # triangle inequality
