@@ -118,19 +118,23 @@ def far_traffic_from_profile():
     return float(m_b.group(1))
 
 
-def algorithmic_flops(stats: np.ndarray) -> tuple[float, float]:
-    """FP32 flops and rsqrt count the method needs for the far pairs of one
-    step: per pair 8 flops to form P - Q_cen and |P - Q_cen|^2, per Gaussian
-    node 18 flops (r = d - o_i: 3; r^2: 5; q_i / r: 1; phi sum: 1;
-    q_i / r^3: 2; E sum: 6, FMA = 2 flops) and one rsqrt (Eq. 4.1)."""
+def algorithmic_work(stats: np.ndarray) -> tuple[float, float, float]:
+    """Work the method needs for the far pairs of one step, from the pair
+    counts per distance-ratio band.  FP32-pipe operations (an FMA is one
+    operation): per pair 8 to classify it (P - Q_cen: 3, its square: 3,
+    compare: 2), per Gaussian node 13 (r_i = P - Q_i: 3, r^2: 3, q_i / r: 1,
+    phi sum: 1, 1 / r^2: 1, q_i / r^3: 1, E sum: 3) plus one rsqrt (Eq. 4.1).
+    Also the same work in flops (FMA = 2): 8 + 18 per node.
+    Returns (ops, rsqrts, flops)."""
     nodes = {0: [0, 33, 19, 12, 7, 4], 1: [0, 33, 17, 12, 7, 4]}
-    flops = rsq = 0.0
+    ops = rsq = flops = 0.0
     for t in (0, 1):
         for b in range(1, 6):
             pairs = float(stats[6 * t + b])
+            ops += pairs * (8 + 13 * nodes[t][b])
             flops += pairs * (8 + 18 * nodes[t][b])
             rsq += pairs * nodes[t][b]
-    return flops, rsq
+    return ops, rsq, flops
 
 
 def cores_used(n_threads: int) -> int:
@@ -242,12 +246,15 @@ def main():
     pairs_step = float(a.points) * mesh.n
     value = world * pairs_step * a.steps / (ms * 1e-3)
 
-    # roofline of the dominant kernel (far-field cubature), from its own events
-    flops, rsq = algorithmic_flops(stats)
+    # roofline of the dominant kernel (far-field cubature), from its own events:
+    # the FP32 pipe's issue rate bounds it (152 SMs x 128 lanes x 2070 MHz
+    # operations per second), the MUFU pipe's rsqrt rate second
+    ops, rsq, flops = algorithmic_work(stats)
     far_avg = statistics.mean(far_ms)
-    peak_fp32 = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12  # TFLOP/s at the maximum SM clock
-    achieved = flops / (far_avg * 1e-3) / 1e12
+    peak_ops = SM_COUNT * FP32_LANES * 2070e6 / 1e12  # T FP32-pipe ops/s at the maximum SM clock
+    achieved = ops / (far_avg * 1e-3) / 1e12
     mufu_frac = rsq / (far_avg * 1e-3) / (SM_COUNT * MUFU_LANES * 2070e6)
+    flop_frac = flops / (far_avg * 1e-3) / (2 * peak_ops * 1e12)
     traffic = far_traffic_from_profile()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -257,14 +264,19 @@ def main():
                        "precision": a.precision, "parallelism": f"points sharded, {world} GPU(s)",
                        "l2": "256 MiB buffer written between steps (inside the timed region)"},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                         "frac": achieved / peak_ops, "traffic": traffic,
                          "kernel": "k_far (far-field cubature)", "kernel_ms": far_avg,
-                         "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)",
-                         "mufu_frac": mufu_frac},
+                         "peak_note": ("FP32 pipe issue rate: 152 SMs x 128 lanes x 2070 MHz, one op per lane "
+                                       "per clock (an FMA is one op); derived from unit counts and the maximum "
+                                       "SM clock"),
+                         "work_note": "algorithmic FP32 ops per far pair: 8 + 13 x nodes of its rule",
+                         "mufu_frac": mufu_frac, "mufu_peak_note": "MUFU rsqrt: 152 SMs x MUFU_LANES x 2070 MHz",
+                         "flop_frac_fma2": flop_frac},
             "band_pairs": {"triangle": [int(x) for x in stats[0:6]], "rectangle": [int(x) for x in stats[6:12]],
                            "order": "analytic, 33, 19|17, 12, 7, 4 points"},
             "far_kernel_work": {"warp_element_uniform": int(stats[13]), "warp_element_mixed": int(stats[14]),
+                                "algorithmic_ops": ops,
                                 "node_evals_executed": int(stats[15]),
                                 "node_evals_algorithmic": int(rsq),
                                 "executed_over_algorithmic": float(stats[15]) / rsq if rsq else None},

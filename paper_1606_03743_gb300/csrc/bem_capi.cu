@@ -213,6 +213,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         a.near_cap = w.cap_near;
         a.kc = m->kc;
         a.want_e = want_e;
+        a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
         a.stats = m->stats;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[1], s));
         int rc = launch_far(m, a, s);
@@ -357,7 +358,7 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     } else {
         int64_t bad = -1;
         int code = 0;
-        rc = launch_prep(m, dtypes, dverts, dsig, s, &bad, &code);
+        rc = launch_prep(m, dtypes, dverts, dsig, s, &bad, &code, &m->coord_max);
     }
     cudaFree(dtypes);
     cudaFree(dverts);
@@ -549,6 +550,7 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
         a.near_rec = w.near_rec;
         a.counters = w.counters;
         a.near_cap = w.cap_near;
+        a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
         a.A = dA;
         a.kc = m->kc;
         a.stats = m->stats;

@@ -32,7 +32,7 @@ __host__ __device__ inline int band_rule(int band) { return 5 - band; }
 struct MeshDev {
     int n = 0;
     // mixed path records (float4, 64 B per element)
-    float4* chi = nullptr;  // centroid hi part xyz, w = type (0/1)
+    float4* chi = nullptr;  // centroid hi part xyz, w = type (0/1) as int bits
     float4* clo = nullptr;  // centroid lo part xyz, w = L
     float4* e0 = nullptr;   // frame vector e0 xyz, w = area
     float4* e1 = nullptr;   // frame vector e1 xyz, w = 0
@@ -78,6 +78,7 @@ struct bem_mesh {
     double eps0 = 8.8541878128e-12;
     double kc = 0.0;          // 1 / (4 pi eps0)
     double limits[2][5];      // DR band limits per type
+    double coord_max = 0.0;   // largest |coordinate| of any element corner
     int n_chunks = 1;         // element chunks of the far-field pass (fixed by the mesh)
     int chunk_len = 0;        // elements per chunk (a multiple of 32)
     size_t budget = 0;
@@ -107,7 +108,7 @@ int cuda_fail(cudaError_t e, const char* what);
 // Element preprocessing (k_prep.cu). Returns the index of the first invalid
 // element through *bad (-1 if none) after synchronising.
 int launch_prep(bem_mesh* m, const int* types, const double* verts, const double* sigma, cudaStream_t s,
-                int64_t* bad, int* bad_code);
+                int64_t* bad, int* bad_code, double* coord_max);
 
 // Spatial sort of field points (k_sort.cu): perm = points in cell order.
 int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s);
@@ -129,6 +130,7 @@ struct FarArgs {
     double* A;           // assembly output (row-major m x n_el) or nullptr
     double kc;           // 1/(4 pi eps0) (assembly writes scaled entries)
     int want_e;          // 0: potential only
+    const unsigned* bbox;  // field-point bounding box written by launch_sort_points
     int stats;           // count pairs per band into counters[2..13]
 };
 // Far-field cubature + near-pair compaction (k_far.cu).

@@ -29,13 +29,15 @@
 //
 // Arithmetic:
 //  * FP64 path: everything in double precision.
-//  * Mixed path: the point-to-centroid difference is formed from FP32 hi/lo
-//    splits of both, (P_hi - C_hi) + (P_lo - C_lo), so it keeps FP32
-//    relative accuracy anywhere in space; node offsets, rsqrt and the sums
-//    are FP32: each element's node terms (at most 33) are summed on their
-//    own, eight such element sums are added up, and that sum is flushed into
-//    FP64 accumulators in shared memory.  No FP32 sum runs over more than 33
-//    terms; the FP64 pipe sees two adds per element and point.
+//  * Mixed path: points and centroids are split into FP32 hi + lo parts, and
+//    P - Q_i is formed as ((P_hi - C_hi) + P_lo) - (o_i + C_lo): the small
+//    lo part of the centroid rides with the node offset o_i (both are small),
+//    so the difference keeps FP32 relative accuracy anywhere in space.  Node
+//    offsets, rsqrt and the sums are FP32: each element's node terms (at
+//    most 33) are summed on their own, eight such element sums are added up,
+//    and that sum is flushed into FP64 accumulators in shared memory.  No
+//    FP32 sum runs over more than 33 terms; the FP64 pipe sees two adds per
+//    element and point.
 #include <stdio.h>
 
 #include <type_traits>
@@ -43,6 +45,20 @@
 #include "bem_internal.cuh"
 
 namespace bem {
+
+// field points per lane of the mixed and FP64 paths (a warp's tile is 32 x PT points)
+#ifndef BEM_MIXED_PT
+#define BEM_MIXED_PT 3
+#endif
+#ifndef BEM_FP64_PT
+#define BEM_FP64_PT 2
+#endif
+constexpr int kPtMixed = BEM_MIXED_PT, kPtFp64 = BEM_FP64_PT;
+// node-loop unroll depth
+#ifndef BEM_NODE_UNROLL
+#define BEM_NODE_UNROLL 4
+#endif
+constexpr int kNodeUnroll = BEM_NODE_UNROLL;
 
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
 constexpr int kWarps = 4;     // warps per CTA
@@ -71,7 +87,13 @@ struct FarK {
     double kc;
     float tau2f[2][5];
     double tau2d[2][5];
+    const unsigned* bbox;  // field-point bounding box (order-preserving float bits: min xyz, max xyz)
+    float coord_max;       // largest |coordinate| of the mesh
 };
+
+__device__ __forceinline__ float ord_to_float(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
 
 // ------------------------------------------------------------ helpers
 __device__ __forceinline__ float warp_min(float v) {
@@ -95,8 +117,6 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float tiny_floor(float x) { return fmaxf(x, 1e-30f); }
-__device__ __forceinline__ double tiny_floor(double x) { return fmax(x, 1e-300); }
 
 // Warp-cooperative append of near pairs; want[q] marks point q of this lane.
 template <int PT>
@@ -119,22 +139,22 @@ __device__ __forceinline__ void append_near(const FarK& p, const bool (&want)[PT
 }
 
 // One point charge (offset o, charge o.w) at the PT points of a lane.
-// INIT: the sums start from this term (instead of adding to them).
+// MASKED: point q's charge is scaled by mq[q] (1 or 0); masked-off points
+// have been moved far away by the caller, so r^2 > 0 and their terms are
+// exact zeros, while an active point's arithmetic is bit-for-bit that of
+// the unmasked path.  INIT: the sums start from this term.
 template <typename R, typename R4, int PT, bool WANT_E, bool MASKED, bool INIT>
 __device__ __forceinline__ void node(const R4 o, const R (&dx)[PT], const R (&dy)[PT], const R (&dz)[PT],
-                                     R (&acc)[PT][4], const int (&bq)[PT], int band) {
+                                     R (&acc)[PT][4], const R (&mq)[PT]) {
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
         const R rx = dx[q] - o.x, ry = dy[q] - o.y, rz = dz[q] - o.z;
-        R r2 = fmad(rx, rx, fmad(ry, ry, rz * rz));
+        const R r2 = fmad(rx, rx, fmad(ry, ry, rz * rz));
         R wq = o.w;
-        if (MASKED) {
-            wq = (bq[q] == band) ? wq : R(0);
-            r2 = tiny_floor(r2);  // a masked-off point may sit on a node
-        }
+        if (MASKED) wq *= mq[q];
         const R inv = rsq(r2);
-        const R a = wq * inv;  // q_i / r_i
-        const R b = a * inv * inv;  // q_i / r_i^3
+        const R a = wq * inv;          // q_i / r_i
+        const R b = a * (inv * inv);   // q_i / r_i^3
         if (INIT) {
             acc[q][0] = a;
             if (WANT_E) { acc[q][1] = b * rx; acc[q][2] = b * ry; acc[q][3] = b * rz; }
@@ -151,18 +171,18 @@ __device__ __forceinline__ void node(const R4 o, const R (&dx)[PT], const R (&dy
 
 // Accumulate the point charges of one rule of one element into
 // acc[q] = (phi, Ex, Ey, Ez) sums.  nd: the rule's (offset, w_i q) records in
-// shared memory (warp-uniform addresses: broadcast).  MASKED: only points q
-// with bq[q] == band contribute.  INIT: the first node starts the sums.
+// shared memory (warp-uniform addresses: broadcast).  MASKED: point q counts
+// with weight mq[q].  INIT: the first node starts the sums.
 template <typename R, typename R4, int PT, bool WANT_E, bool MASKED, bool INIT>
 __device__ __forceinline__ void nodes(const R4* __restrict__ nd, int n, const R (&dx)[PT], const R (&dy)[PT],
-                                      const R (&dz)[PT], R (&acc)[PT][4], const int (&bq)[PT], int band) {
+                                      const R (&dz)[PT], R (&acc)[PT][4], const R (&mq)[PT]) {
     int i = 0;
     if (INIT) {  // every rule has at least four nodes
-        node<R, R4, PT, WANT_E, MASKED, true>(nd[0], dx, dy, dz, acc, bq, band);
+        node<R, R4, PT, WANT_E, MASKED, true>(nd[0], dx, dy, dz, acc, mq);
         i = 1;
     }
-#pragma unroll 4
-    for (; i < n; ++i) node<R, R4, PT, WANT_E, MASKED, false>(nd[i], dx, dy, dz, acc, bq, band);
+#pragma unroll kNodeUnroll
+    for (; i < n; ++i) node<R, R4, PT, WANT_E, MASKED, false>(nd[i], dx, dy, dz, acc, mq);
 }
 
 // Shared memory of one warp.
@@ -223,9 +243,21 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
         rs.start[tid] = c_rule_start[tid];
     }
     if (STATS && tid < 15) rs.stat[tid] = 0ull;
+    // absolute margin of the warp band test: coordinates enter it rounded to
+    // FP32 (relative 6e-8); 1e-6 of the largest magnitude in play bounds that
+    // rounding with a wide margin
+    float slack_abs;
+    {
+        float pm = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pm = fmaxf(pm, fabsf(ord_to_float(p.bbox[k])));
+        slack_abs = 1e-6f * (3.0f * p.coord_max + pm);
+    }
     __syncthreads();
 
-    const int dummy_b[PT] = {};
+    R ones[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) ones[q] = (R)1;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(p.work, 1);
@@ -307,6 +339,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
                     const double sg = p.sigma ? p.sigma[j] : 1.0;
                     const double area = p.geo[2 * j + 1];
                     R4 c, cl;
+                    float th[5];
                     if constexpr (F64) {
                         const double L = p.geo[2 * j];
                         c = R4{p.cen[3 * j], p.cen[3 * j + 1], p.cen[3 * j + 2], (double)ty};
@@ -314,16 +347,23 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
                         ws.e0[lane] = R4{p.fr[6 * j], p.fr[6 * j + 1], p.fr[6 * j + 2], sg * area};
                         ws.e1[lane] = R4{p.fr[6 * j + 3], p.fr[6 * j + 4], p.fr[6 * j + 5], 0.0};
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) ws.thr[lane * 5 + k] = p.tau2d[ty][k] * L * L;
+                        for (int k = 0; k < 5; ++k) {
+                            const double t = p.tau2d[ty][k] * L * L;
+                            ws.thr[lane * 5 + k] = t;
+                            th[k] = (float)t;
+                        }
                     } else {
-                        c = p.chi[j];
+                        c = p.chi[j];  // w: the element type as int bits
                         cl = p.clo[j];
                         const float4 a = p.e0f[j], b = p.e1f[j];
                         ws.e0[lane] = R4{a.x, a.y, a.z, (float)(sg * area)};
                         ws.e1[lane] = R4{b.x, b.y, b.z, 0.0f};
                         const float L = cl.w;
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) ws.thr[lane * 5 + k] = p.tau2f[ty][k] * L * L;
+                        for (int k = 0; k < 5; ++k) {
+                            th[k] = p.tau2f[ty][k] * L * L;
+                            ws.thr[lane * 5 + k] = th[k];
+                        }
                     }
                     ws.c[lane] = c;
                     ws.cl[lane] = cl;
@@ -332,12 +372,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
                     const float dy = ((float)(wcy - (float)c.y)) - (float)cl.y;
                     const float dz = ((float)(wcz - (float)c.z)) - (float)cl.z;
                     const float Dc = sqrtf(dx * dx + dy * dy + dz * dz);
-                    const float cmag = fabsf((float)c.x) + fabsf((float)c.y) + fabsf((float)c.z);
-                    const float slack = 1e-5f * (Dc + wrad) + 1e-6f * (wmag + cmag);
+                    const float slack = fmaf(1e-5f, Dc + wrad, slack_abs);
                     const float dmin = fmaxf(Dc - wrad - slack, 0.0f), dmax = Dc + wrad + slack;
-                    float th[5];
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) th[k] = (float)ws.thr[lane * 5 + k];
                     const int blo = band_of<float>(dmin * dmin, th), bhi = band_of<float>(dmax * dmax, th);
                     code = blo == bhi ? blo : kMixedCode;
                 }
@@ -347,17 +383,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
             const int nb = min(32, el1 - b0);
             for (int e = 0; e < nb; ++e) {
                 const int cd = __shfl_sync(0xffffffffu, code, e);
-                const R4 c = ws.c[e], cl = ws.cl[e];
-                const int ty = (int)c.w;
+                const R4 c = ws.c[e];
+                int ty;
+                if constexpr (F64) ty = (int)c.w;
+                else ty = __float_as_int(c.w);
+                // (P_hi - C_hi) + P_lo; the centroid's lo part is in the node offsets
                 R dx[PT], dy[PT], dz[PT];
 #pragma unroll
                 for (int q = 0; q < PT; ++q) {
                     if constexpr (F64) {
                         dx[q] = px[q] - c.x; dy[q] = py[q] - c.y; dz[q] = pz[q] - c.z;
                     } else {
-                        dx[q] = (px[q] - c.x) + (lx[q] - cl.x);
-                        dy[q] = (py[q] - c.y) + (ly[q] - cl.y);
-                        dz[q] = (pz[q] - c.z) + (lz[q] - cl.z);
+                        dx[q] = (px[q] - c.x) + lx[q];
+                        dy[q] = (py[q] - c.y) + ly[q];
+                        dz[q] = (pz[q] - c.z) + lz[q];
                     }
                 }
                 // per-element sums (mixed path, assembly; started by the element's
@@ -370,10 +409,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
                 auto expand = [&](int r) -> int {
                     const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
                     const R4 a = ws.e0[e], b = ws.e1[e];
+                    R ox = 0, oy = 0, oz = 0;  // mixed path: the centroid's lo part
+                    if constexpr (!F64) {
+                        const R4 cl = ws.cl[e];
+                        ox = cl.x; oy = cl.y; oz = cl.z;
+                    }
                     for (int i = lane; i < n; i += 32) {
                         const R al = rs.al[st + i], be = rs.be[st + i];
-                        ws.nd[par][i] = R4{fmad(al, a.x, be * b.x), fmad(al, a.y, be * b.y),
-                                           fmad(al, a.z, be * b.z), rs.w[st + i] * a.w};
+                        ws.nd[par][i] = R4{fmad(al, a.x, fmad(be, b.x, ox)), fmad(al, a.y, fmad(be, b.y, oy)),
+                                           fmad(al, a.z, fmad(be, b.z, oz)), rs.w[st + i] * a.w};
                     }
                     __syncwarp();
                     return n;
@@ -381,7 +425,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
 
                 if (cd >= 1 && cd <= 5) {
                     const int n = expand(band_rule(cd));
-                    nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, dummy_b, 0);
+                    nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, ones);
                     par ^= 1;
                     if (STATS && lane == 0) {
                         atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -415,8 +459,30 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
 #pragma unroll 1
                     for (int band = 1; band <= 5; ++band) {
                         if (!(mask & (1u << band))) continue;
+                        // points of other bands: zero charge, parked far from every node
+                        // (the active points' differences are formed afresh, exactly as above)
+                        R mq[PT];
+                        {
+                            const R4 cc = ws.c[e];
+#pragma unroll
+                            for (int q = 0; q < PT; ++q) {
+                                const bool on = bq[q] == band;
+                                mq[q] = on ? (R)1 : (R)0;
+                                R ax, ay, az;
+                                if constexpr (F64) {
+                                    ax = px[q] - cc.x; ay = py[q] - cc.y; az = pz[q] - cc.z;
+                                } else {
+                                    ax = (px[q] - cc.x) + lx[q];
+                                    ay = (py[q] - cc.y) + ly[q];
+                                    az = (pz[q] - cc.z) + lz[q];
+                                }
+                                dx[q] = on ? ax : (R)1e3;
+                                dy[q] = on ? ay : (R)1e3;
+                                dz[q] = on ? az : (R)1e3;
+                            }
+                        }
                         const int n = expand(band_rule(band));
-                        nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, dx, dy, dz, dst, bq, band);
+                        nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, dx, dy, dz, dst, mq);
                         par ^= 1;
                         if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                     }
@@ -537,7 +603,7 @@ int launch_stats(const FarK& k, cudaStream_t s, bool stats) {
 }
 }  // namespace
 
-int far_points_per_tile(int precision) { return 32 * (precision == kFP64 ? 2 : 4); }
+int far_points_per_tile(int precision) { return 32 * (precision == kFP64 ? kPtFp64 : kPtMixed); }
 
 int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     int rc = upload_rules(m->device);
@@ -559,6 +625,8 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.near_cap = a.near_cap;
     k.A = a.A;
     k.kc = a.kc;
+    k.bbox = a.bbox;
+    k.coord_max = (float)m->coord_max;
     for (int t = 0; t < 2; ++t)
         for (int i = 0; i < 5; ++i) {
             k.tau2d[t][i] = m->limits[t][i] * m->limits[t][i];
@@ -581,15 +649,15 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.n_items = n_tiles * k.n_chunks;
     const bool st = a.stats != 0;
     if (a.A) {
-        if (f64) return launch_stats<true, 2, false, 1>(k, s, st);
-        return launch_stats<false, 4, false, 1>(k, s, st);
+        if (f64) return launch_stats<true, kPtFp64, false, 1>(k, s, st);
+        return launch_stats<false, kPtMixed, false, 1>(k, s, st);
     }
     if (f64) {
-        if (a.want_e) return launch_stats<true, 2, true, 0>(k, s, st);
-        return launch_stats<true, 2, false, 0>(k, s, st);
+        if (a.want_e) return launch_stats<true, kPtFp64, true, 0>(k, s, st);
+        return launch_stats<true, kPtFp64, false, 0>(k, s, st);
     }
-    if (a.want_e) return launch_stats<false, 4, true, 0>(k, s, st);
-    return launch_stats<false, 4, false, 0>(k, s, st);
+    if (a.want_e) return launch_stats<false, kPtMixed, true, 0>(k, s, st);
+    return launch_stats<false, kPtMixed, false, 0>(k, s, st);
 }
 
 }  // namespace bem

@@ -8,6 +8,8 @@
 //                       e1 = (P3 - P0) / 2 = (b/2) u_y
 // and writes the FP64 arrays (centroid, frame, L, area) plus the FP32
 // records of the mixed path with the centroid split into hi + lo floats.
+#include <string.h>
+
 #include "bem_internal.cuh"
 
 namespace bem {
@@ -31,9 +33,15 @@ __device__ __forceinline__ double len(V3 a) { return sqrt(dot(a, a)); }
 enum { kBadType = 1, kNotFinite = 2, kDegenerate = 3, kNotRectangle = 4 };
 
 __global__ void k_prep(int n, const int* __restrict__ type, const double* __restrict__ verts,
-                       const double* __restrict__ sigma, MeshDev d, unsigned long long* bad) {
+                       const double* __restrict__ sigma, MeshDev d, unsigned long long* bad, unsigned* cmax) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    {
+        // largest |coordinate| (float bits of a non-negative float order like unsigned ints)
+        float m = 0.0f;
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, (float)fabs(verts[12 * (size_t)j + k]));
+        if (isfinite(m)) atomicMax(cmax, __float_as_uint(m));
+    }
     const int ty = type[j];
     const double* v = verts + 12 * (size_t)j;
     int code = 0;
@@ -84,7 +92,7 @@ __global__ void k_prep(int n, const int* __restrict__ type, const double* __rest
     d.geo[2 * j] = L;
     d.geo[2 * j + 1] = area;
     const float hx = (float)cen.x, hy = (float)cen.y, hz = (float)cen.z;
-    d.chi[j] = make_float4(hx, hy, hz, (float)ty);
+    d.chi[j] = make_float4(hx, hy, hz, __int_as_float(ty));  // w: type as int bits
     d.clo[j] = make_float4((float)(cen.x - hx), (float)(cen.y - hy), (float)(cen.z - hz), (float)L);
     d.e0[j] = make_float4((float)e0.x, (float)e0.y, (float)e0.z, (float)area);
     d.e1[j] = make_float4((float)e1.x, (float)e1.y, (float)e1.z, 0.0f);
@@ -104,17 +112,23 @@ const char* code_name(int c) {
 
 // types/verts/sigma are device arrays (staged by the caller).
 int launch_prep(bem_mesh* m, const int* types, const double* verts, const double* sigma, cudaStream_t s,
-                int64_t* bad_index, int* bad_code) {
+                int64_t* bad_index, int* bad_code, double* coord_max) {
     unsigned long long* dbad = m->w.counters + 1;
-    const unsigned long long init = ~0ull;
-    BEM_CUDA_TRY(cudaMemcpyAsync(dbad, &init, sizeof init, cudaMemcpyHostToDevice, s));
+    unsigned* dmax = reinterpret_cast<unsigned*>(m->w.counters + 2);
+    const unsigned long long init[2] = {~0ull, 0ull};
+    BEM_CUDA_TRY(cudaMemcpyAsync(dbad, init, sizeof init, cudaMemcpyHostToDevice, s));
     const int n = m->d.n;
-    k_prep<<<(n + 255) / 256, 256, 0, s>>>(n, types, verts, sigma, m->d, dbad);
+    k_prep<<<(n + 255) / 256, 256, 0, s>>>(n, types, verts, sigma, m->d, dbad, dmax);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     unsigned long long hbad = 0;
+    unsigned hmax = 0;
     BEM_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(&hmax, dmax, sizeof hmax, cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    float fm;
+    memcpy(&fm, &hmax, sizeof fm);
+    *coord_max = fm;
     if (hbad != ~0ull) {
         *bad_index = (int64_t)(hbad >> 8);
         *bad_code = (int)(hbad & 0xff);

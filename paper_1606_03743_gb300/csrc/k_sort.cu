@@ -1,7 +1,8 @@
 // k_sort.cu -- spatial ordering of field points and an exclusive scan.
 //
 // Field points are ordered by a Morton (Z-order) cell key over their bounding
-// box so that the 32 * PT points of a warp are neighbours: the far-field
+// box (about one point per cell) so that the 32 * PT points of a warp are
+// neighbours: the far-field
 // kernel then usually finds every point of a warp in the same distance-ratio
 // band of an element and runs one rule for the whole warp.  The order within
 // a cell is whatever the atomics give; results do not depend on it because
@@ -139,9 +140,10 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
 }
 
 int bits_for(int n) {
-    // about 16 points per cell, 1..7 bits per axis
+    // about one point per cell (1..7 bits per axis): the Z-order curve then
+    // orders the points finely, so 32 x PT consecutive points are compact
     int b = 1;
-    while (b < 7 && (1 << (3 * (b + 1))) * 16 <= n) ++b;
+    while (b < 7 && (1 << (3 * b)) < n) ++b;
     return b;
 }
 

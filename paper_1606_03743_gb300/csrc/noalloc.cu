@@ -26,7 +26,7 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 constexpr size_t kMaxPts = BEM_NOALLOC_MAX_POINTS;
 constexpr size_t kMaxNear = BEM_NOALLOC_MAX_NEAR;
 constexpr size_t kMaxChunks = 16;      // element chunks of the far-field pass (at most 16 per mesh)
-constexpr size_t kCellsMax = 4096;     // the sort uses at most 2^(3*3) cells for <= 2^14 points
+constexpr size_t kCellsMax = 32768;    // the sort uses at most 2^(3*5) cells for <= 2^14 points
 constexpr size_t kScanInts = 16384;    // block sums of every scan level, with room to spare
 
 // byte offsets of the scratch areas inside the array
@@ -159,6 +159,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.kc = m->kc;
     a.want_e = E != nullptr;
     a.stats = 0;
+    a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
     if ((rc = launch_far(&view, a, s))) return rc;
     if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)n * m->n_chunks, w.scan_tmp, s))) return rc;
     if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s))) return rc;
