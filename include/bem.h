@@ -216,6 +216,71 @@ int64_t bem_kernel_launches(void);
 #define BEM_NOALLOC_BYTES (24u << 20)
 int bem_eval_noalloc(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of field-point queries on a device-resident
+ * mesh (a particle tracker's stream of uneven requests).  A server thread
+ * forms ticks: it admits queued requests in arrival order while their
+ * points fit one tick's device buffers, copies them in, replays one CUDA
+ * graph of the whole evaluation (captured at creation; the persistent
+ * far-field kernel walks (point tile x element chunk) work items), and
+ * copies the results back.  Two ticks can be in flight, so requests that
+ * arrive while one tick runs are admitted into the next and overlap it.
+ * Each result equals bem_eval's for the same points bit for bit, whatever
+ * other requests shared its tick.  While a server exists it owns the mesh:
+ * make no other call on that mesh until bem_server_destroy.
+ * ------------------------------------------------------------------------ */
+typedef struct bem_server bem_server;
+
+typedef struct {
+    int64_t max_points_per_tick;     /* points one tick can take (0: 131072); a
+                                        request may not exceed it */
+    int64_t max_near_pairs_per_tick; /* near-field pairs one tick can take (0: 2^21);
+                                        a tick that has more evaluates its
+                                        requests one by one with bem_eval */
+    size_t device_mem_budget;        /* bound on the server's device memory
+                                        (0: 2 GiB); max_points_per_tick is halved
+                                        until two ticks' buffers fit */
+    int32_t flags;                   /* reserved, must be 0 */
+} bem_server_options;
+
+/* Create a server on mesh (opt may be NULL).  Builds both ticks' device
+ * buffers and CUDA graphs and starts the server thread. */
+int bem_server_create(bem_mesh* mesh, const bem_server_options* opt, bem_server** out);
+
+/* Finish every queued request, stop the thread, release everything. */
+void bem_server_destroy(bem_server* server);
+
+/* Queue n field points (host array [n][3], copied) for evaluation; *ticket
+ * names the request.  Thread-safe.  BEM_ERR_INVALID for n < 1, n above the
+ * tick capacity or a non-finite coordinate. */
+int bem_submit(bem_server* server, const double* points, int64_t n, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and the results copied to phi [n] / E [n][3]
+ * (host arrays, either may be NULL) once the request has finished; the
+ * ticket is then spent.  *done = 0 otherwise.  BEM_ERR_NOT_FOUND for an
+ * unknown or spent ticket. */
+int bem_poll(bem_server* server, uint64_t ticket, double* phi, double* E, int32_t* done);
+
+/* Blocking with a bound: wait at most timeout_s seconds for the request,
+ * then copy its results as bem_poll.  BEM_ERR_TIMEOUT if it is still
+ * unfinished (the ticket stays valid). */
+int bem_wait(bem_server* server, uint64_t ticket, double timeout_s, double* phi, double* E);
+
+/* Drop a request: a queued one is removed, a running one's results are
+ * discarded when its tick ends. */
+int bem_cancel(bem_server* server, uint64_t ticket);
+
+/* Stop (1) or resume (0) forming new ticks; queued requests wait meanwhile. */
+int bem_server_pause(bem_server* server, int32_t paused);
+
+/* Service statistics since creation or the last reset (reset = 1 clears them
+ * after reading): out[0] requests completed, out[1] p50 and out[2] p99
+ * latency (ms, submission to results on the host), out[3] mean latency
+ * (ms), out[4] ticks, out[5] points evaluated, out[6] ticks that fell back
+ * to per-request evaluation, out[7] points per tick (capacity), out[8]
+ * device bytes held, out[9] graph launches. */
+int bem_server_stats(bem_server* server, int32_t reset, double* out /* 10 */);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bem_last_error(void);
 

@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
@@ -40,6 +40,11 @@ class BemError(RuntimeError):
 class bem_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("flags", C.c_int32), ("limits", C.POINTER(C.c_double)),
                 ("eps0", C.c_double), ("device_mem_budget", C.c_size_t)]
+
+
+class bem_server_options(C.Structure):
+    _fields_ = [("max_points_per_tick", C.c_int64), ("max_near_pairs_per_tick", C.c_int64),
+                ("device_mem_budget", C.c_size_t), ("flags", C.c_int32)]
 
 
 _lib = None
@@ -75,6 +80,18 @@ def load_library(build_if_missing: bool = True):
     lib.bem_kernel_launches.restype = C.c_int64
     lib.bem_eval_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     lib.bem_eval_noalloc.restype = C.c_int
+    lib.bem_server_create.argtypes = [vp, C.POINTER(bem_server_options), C.POINTER(vp)]
+    lib.bem_server_destroy.argtypes = [vp]
+    lib.bem_server_destroy.restype = None
+    lib.bem_submit.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_uint64)]
+    lib.bem_poll.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(C.c_int32)]
+    lib.bem_wait.argtypes = [vp, C.c_uint64, C.c_double, vp, vp]
+    lib.bem_cancel.argtypes = [vp, C.c_uint64]
+    lib.bem_server_pause.argtypes = [vp, C.c_int32]
+    lib.bem_server_stats.argtypes = [vp, C.c_int32, d]
+    for name in ("bem_server_create", "bem_submit", "bem_poll", "bem_wait", "bem_cancel", "bem_server_pause",
+                 "bem_server_stats"):
+        getattr(lib, name).restype = C.c_int
     lib.bem_last_error.restype = C.c_char_p
     lib.bem_version.restype = C.c_char_p
     for name in ("bem_create", "bem_set_sigma", "bem_eval", "bem_assemble", "bem_matvec", "bem_centroids",
@@ -322,3 +339,80 @@ class Mesh:
 
     def last_times(self) -> np.ndarray:
         return bem_last_times(self._h)
+
+
+# ---------------------------------------------------------------- serving
+SERVER_STAT_NAMES = ("completed", "p50_ms", "p99_ms", "mean_ms", "ticks", "points", "fallback_ticks",
+                     "points_per_tick", "device_bytes", "graph_launches")
+
+
+class Server:
+    """Continuous-batching server of field-point queries on a mesh (see
+    bem_server_* in include/bem.h).  Requests are host arrays of points;
+    results come back as numpy arrays.  While the server lives it owns the
+    mesh."""
+
+    def __init__(self, mesh: "Mesh", max_points_per_tick: int = 0, max_near_pairs_per_tick: int = 0,
+                 device_mem_budget: int = 0):
+        lib = load_library()
+        opt = bem_server_options(int(max_points_per_tick), int(max_near_pairs_per_tick), int(device_mem_budget), 0)
+        h = C.c_void_p()
+        _check(lib.bem_server_create(mesh.handle, C.byref(opt), C.byref(h)))
+        self._h = h.value
+        self._mesh = mesh  # keep the mesh alive
+        self._sizes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().bem_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, points) -> int:
+        p = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+        t = C.c_uint64()
+        _check(load_library().bem_submit(self._h, p.ctypes.data, p.shape[0], C.byref(t)))
+        self._sizes[t.value] = p.shape[0]
+        return t.value
+
+    def poll(self, ticket: int):
+        """(done, phi, E): phi and E are None until the request has finished."""
+        n = self._sizes.get(ticket, 0)  # unknown tickets: the library reports BEM_ERR_NOT_FOUND
+        phi, E = np.empty(n), np.empty((n, 3))
+        done = C.c_int32()
+        _check(load_library().bem_poll(self._h, ticket, phi.ctypes.data, E.ctypes.data, C.byref(done)))
+        if not done.value:
+            return False, None, None
+        self._sizes.pop(ticket, None)
+        return True, phi, E
+
+    def wait(self, ticket: int, timeout: float = 60.0):
+        n = self._sizes.get(ticket, 0)
+        phi, E = np.empty(n), np.empty((n, 3))
+        _check(load_library().bem_wait(self._h, ticket, float(timeout), phi.ctypes.data, E.ctypes.data))
+        self._sizes.pop(ticket, None)
+        return phi, E
+
+    def cancel(self, ticket: int):
+        _check(load_library().bem_cancel(self._h, ticket))
+        self._sizes.pop(ticket, None)
+
+    def pause(self, paused: bool = True):
+        _check(load_library().bem_server_pause(self._h, 1 if paused else 0))
+
+    def stats(self, reset: bool = False) -> dict:
+        out = np.zeros(10)
+        _check(load_library().bem_server_stats(self._h, 1 if reset else 0,
+                                               out.ctypes.data_as(C.POINTER(C.c_double))))
+        return dict(zip(SERVER_STAT_NAMES, out.tolist()))

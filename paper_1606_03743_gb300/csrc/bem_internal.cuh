@@ -111,7 +111,7 @@ int launch_prep(bem_mesh* m, const int* types, const double* verts, const double
                 int64_t* bad, int* bad_code, double* coord_max);
 
 // Spatial sort of field points (k_sort.cu): perm = points in cell order.
-int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s);
+int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s, const int* n_dev = nullptr);
 // Exclusive scan of n ints (k_sort.cu); tmp needs scan_tmp_ints(n) ints.
 int launch_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 size_t scan_tmp_ints(int n);
@@ -132,6 +132,7 @@ struct FarArgs {
     int want_e;          // 0: potential only
     const unsigned* bbox;  // field-point bounding box written by launch_sort_points
     int stats;           // count pairs per band into counters[2..13]
+    const int* n_dev;    // if set: the point count is read on the device (n_pts is the capacity)
 };
 // Far-field cubature + near-pair compaction (k_far.cu).
 int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s);
@@ -140,7 +141,7 @@ int far_points_per_tile(int precision);
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
                      unsigned long long n_near, cudaStream_t s);
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int out_stride4,
-                    cudaStream_t s);
+                    cudaStream_t s, const int* n_dev = nullptr);
 int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double* A, unsigned long long n_near,
                          cudaStream_t s);
 

@@ -89,6 +89,8 @@ struct FarK {
     double tau2d[2][5];
     const unsigned* bbox;  // field-point bounding box (order-preserving float bits: min xyz, max xyz)
     float coord_max;       // largest |coordinate| of the mesh
+    const int* n_dev;      // if set: the point count is read here (n_pts is then the capacity)
+    int tile_pts;          // points per work-item tile (32 x PT)
 };
 
 __device__ __forceinline__ float ord_to_float(unsigned u) {
@@ -230,6 +232,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
     RuleSmem<R>& rs = *reinterpret_cast<RuleSmem<R>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WS& ws = reinterpret_cast<WS*>(smem_raw + ((sizeof(RuleSmem<R>) + 15) / 16) * 16)[warp];
+    int n_pts = p.n_pts, n_items = p.n_items;
+    if (p.n_dev) {
+        n_pts = min(n_pts, *p.n_dev);
+        n_items = (n_pts + p.tile_pts - 1) / p.tile_pts * p.n_chunks;
+    }
 
     for (int i = tid; i < 2 * kSlots; i += blockDim.x) {
         if constexpr (F64) {
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
         int item = 0;
         if (lane == 0) item = atomicAdd(p.work, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= p.n_items) break;
+        if (item >= n_items) break;
         const int tile = item / p.n_chunks, chunk = item - tile * p.n_chunks;
         const int base = tile * (32 * PT);
 
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
             int i = base + q * 32 + lane;
-            valid[q] = i < p.n_pts;
+            valid[q] = i < n_pts;
             if (!valid[q]) i = base;  // duplicate a live point of the tile
             sidx[q] = i;
             const int src = p.perm[i];
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
             wmag = sqrtf(wcx * wcx + wcy * wcy + wcz * wcz) + wrad;
         }
         int nvalid = 0;  // valid points of the tile (for the statistics)
-        if (STATS) nvalid = min(32 * PT, p.n_pts - base);
+        if (STATS) nvalid = min(32 * PT, n_pts - base);
 
         // ---- accumulators
         R acc[PT][4];  // FP64 path: the sums; mixed: FP32 sum of up to 8 element sums
@@ -627,6 +634,7 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.kc = a.kc;
     k.bbox = a.bbox;
     k.coord_max = (float)m->coord_max;
+    k.n_dev = a.n_dev;
     for (int t = 0; t < 2; ++t)
         for (int i = 0; i < 5; ++i) {
             k.tau2d[t][i] = m->limits[t][i] * m->limits[t][i];
@@ -647,6 +655,7 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
         k.n_chunks = m->n_chunks;
     }
     k.n_items = n_tiles * k.n_chunks;
+    k.tile_pts = tile;
     const bool st = a.stats != 0;
     if (a.A) {
         if (f64) return launch_stats<true, kPtFp64, false, 1>(k, s, st);

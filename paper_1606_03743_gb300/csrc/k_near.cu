@@ -108,10 +108,11 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
 
 // far sums of the element chunks in chunk order + near contributions in
 // element order, times 1/(4 pi eps0), written at the point's original position.
-__global__ void k_finalize(int n, int n_chunks, const int* __restrict__ perm, const double4* __restrict__ part,
-                           const int* __restrict__ near_cnt, const int* __restrict__ near_off,
-                           const double4* __restrict__ val, unsigned long long cap, double kc, double* phi, double* E,
-                           int stride4) {
+__global__ void k_finalize(int n, const int* n_dev, int n_chunks, const int* __restrict__ perm,
+                           const double4* __restrict__ part, const int* __restrict__ near_cnt,
+                           const int* __restrict__ near_off, const double4* __restrict__ val, unsigned long long cap,
+                           double kc, double* phi, double* E, int stride4) {
+    if (n_dev) n = min(n, *n_dev);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const size_t p0 = (size_t)i * n_chunks;
@@ -179,9 +180,11 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
     return BEM_OK;
 }
 
-int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int stride4, cudaStream_t s) {
+int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int stride4, cudaStream_t s,
+                    const int* n_dev) {
     Work& w = m->w;
-    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, m->n_chunks, perm, w.part, w.near_cnt, w.near_off, w.near_val,
+    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, n_dev, m->n_chunks, perm, w.part, w.near_cnt, w.near_off,
+                                                   w.near_val,
                                                    (unsigned long long)w.cap_near, m->kc, phi, E, stride4);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);

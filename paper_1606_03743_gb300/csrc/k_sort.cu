@@ -27,7 +27,9 @@ __global__ void k_bbox_init(unsigned* bb) {
     else if (threadIdx.x < 6) bb[threadIdx.x] = 0u;          // max
 }
 
-__global__ void k_bbox(const double* __restrict__ pts, int n, unsigned* bb, unsigned long long* bad) {
+__global__ void k_bbox(const double* __restrict__ pts, int n, const int* n_dev, unsigned* bb,
+                       unsigned long long* bad) {
+    if (n_dev) n = min(n, *n_dev);
     float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
     bool finite = true;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -66,8 +68,9 @@ __device__ __forceinline__ unsigned spread3(unsigned x) {  // 10 bits -> every t
     return x;
 }
 
-__global__ void k_keys(const double* __restrict__ pts, int n, const unsigned* bb, int bits, unsigned* key,
-                       int* cell_cnt) {
+__global__ void k_keys(const double* __restrict__ pts, int n, const int* n_dev, const unsigned* bb, int bits,
+                       unsigned* key, int* cell_cnt) {
+    if (n_dev) n = min(n, *n_dev);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float lim = (float)((1 << bits) - 1);
@@ -84,7 +87,8 @@ __global__ void k_keys(const double* __restrict__ pts, int n, const unsigned* bb
     atomicAdd(cell_cnt + kk, 1);
 }
 
-__global__ void k_scatter(const unsigned* __restrict__ key, int n, int* cursor, int* perm) {
+__global__ void k_scatter(const unsigned* __restrict__ key, int n, const int* n_dev, int* cursor, int* perm) {
+    if (n_dev) n = min(n, *n_dev);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int pos = atomicAdd(cursor + key[i], 1);
@@ -178,8 +182,10 @@ int launch_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t
 }
 
 // Sort the first n points of pts into m->w.perm (cell order).  Non-finite
-// (or absurdly large) coordinates set counters[15].
-int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s) {
+// (or absurdly large) coordinates set counters[15].  With n_dev the actual
+// count is read on the device (n is then the capacity; the launch sequence
+// can be captured once in a CUDA graph).
+int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s, const int* n_dev) {
     Work& w = m->w;
     BEM_CUDA_TRY(cudaMemsetAsync(w.counters + 15, 0, sizeof(unsigned long long), s));
     const int bits = bits_for(n);
@@ -188,14 +194,14 @@ int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s) {
     k_bbox_init<<<1, 32, 0, s>>>(bb);
     BEM_CUDA_TRY(cudaGetLastError());
     const int grid = min((n + 255) / 256, 152 * 4);
-    k_bbox<<<grid, 256, 0, s>>>(pts, n, bb, w.counters + 15);
+    k_bbox<<<grid, 256, 0, s>>>(pts, n, n_dev, bb, w.counters + 15);
     BEM_CUDA_TRY(cudaGetLastError());
     BEM_CUDA_TRY(cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * ncell, s));
-    k_keys<<<(n + 255) / 256, 256, 0, s>>>(pts, n, bb, bits, w.key, w.cell_cnt);
+    k_keys<<<(n + 255) / 256, 256, 0, s>>>(pts, n, n_dev, bb, bits, w.key, w.cell_cnt);
     BEM_CUDA_TRY(cudaGetLastError());
     int rc = launch_exclusive_scan(w.cell_cnt, w.cell_off, ncell, w.scan_tmp, s);
     if (rc) return rc;
-    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(w.key, n, w.cell_off, w.perm);
+    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(w.key, n, n_dev, w.cell_off, w.perm);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(4);  // bbox_init, bbox, keys, scatter
     return BEM_OK;
