@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--fp64-points", type=int, default=16384, help="batch for the FP64-path comparison line")
     ap.add_argument("--cpu-sample", type=int, default=8192, help="points of the oracle CPU baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 comparison and CPU baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (latency) measurement")
+    ap.add_argument("--no-assembly", action="store_true", help="skip the collocation-assembly measurement")
+    ap.add_argument("--serve-requests", type=int, default=200)
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -284,6 +287,12 @@ def main():
 
     if rank == 0 and world == 1 and not a.no_extras:
         line.update(extras(a, bem, torch, m, mesh, pts, prec, stream, phi, E))
+    if rank == 0 and world == 1 and not a.no_serving:
+        line["serving"] = serving(a, bem, torch)
+        lat = line["serving"]["mixed"]
+        line["latency"] = {"p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "workload": line["serving"]["workload"]}
+    if rank == 0 and world == 1 and not a.no_assembly:
+        line["assembly"] = assembly(a, bem, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()
@@ -381,6 +390,107 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
                   "frac_above_100": float((kappa > 100).mean())},
         "points": ns}
     m64.close()
+    return out
+
+
+def run_server(bem, m, reqs, rate, n_el):
+    """Poisson arrivals at `rate` requests/s into a server on mesh m; returns
+    latency statistics (measured by the library, submission to results on
+    the host) and throughput."""
+    srv = bem.Server(m)
+    rng = np.random.default_rng(55)
+    gaps = rng.exponential(1.0 / rate, len(reqs))
+    tickets = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for r, g in zip(reqs, gaps):
+        now = time.perf_counter()
+        if t_next > now:
+            time.sleep(t_next - now)
+        tickets.append(srv.submit(r))
+        t_next += g
+    for t in tickets:
+        srv.wait(t, timeout=600)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    pts = sum(len(r) for r in reqs)
+    return {"requests": len(reqs), "points": int(pts), "rate_req_per_s": rate, "p50_ms": st["p50_ms"],
+            "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "ticks": int(st["ticks"]),
+            "fallback_ticks": int(st["fallback_ticks"]), "graph_launches": int(st["graph_launches"]),
+            "throughput_pairs_per_s": pts * n_el / wall, "wall_s": wall}
+
+
+def serving(a, bem, torch):
+    """Serving workload: the 500k-element coaxial mesh resident on the GPU,
+    query batches of floor(10^U[0,5]) points (clipped to [1, 1e5]) along
+    helical tracks, Poisson arrivals at 70 % of the measured capacity."""
+    mesh = synth.coax_mesh_large(seed=4)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"workload": (f"{mesh.n} elements (coaxial, 400x500 rectangles per cylinder + 100000 cap triangles); "
+                        f"{a.serve_requests} requests of 10^U[0,5] points on helices, Poisson arrivals at 70% "
+                        "of measured capacity")}
+    reqs = synth.helix_requests(seed=5, n_req=a.serve_requests)
+    for prec, name in ((bem.MIXED, "mixed"), (bem.FP64, "fp64")):
+        m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                     torch.from_numpy(mesh.sigma).to(dev), precision=prec)
+        # capacity in points/s from one evaluation of a representative batch
+        probe = synth.coax_points(seed=6, n=65536 if prec == bem.MIXED else 2048)
+        m.eval(probe[:1024])
+        t0 = time.perf_counter()
+        m.eval(probe)
+        cap_pts = len(probe) / (time.perf_counter() - t0)
+        if prec == bem.MIXED:
+            sel = reqs
+        else:  # the FP64 kernel is ~30x slower: a capped subset (sizes <= 2000), compared like for like below
+            sel = [r for r in reqs if len(r) <= 2000][:20]
+        mean_size = float(np.mean([len(r) for r in sel]))
+        rate = 0.7 * cap_pts / mean_size
+        out[name] = run_server(bem, m, sel, rate, mesh.n)
+        out[name]["capacity_points_per_s"] = cap_pts
+        if prec == bem.FP64:
+            # the same capped subset on the mixed path, at the same arrival rate
+            m.close()
+            m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                         torch.from_numpy(mesh.sigma).to(dev), precision=bem.MIXED)
+            out["mixed_same_subset_as_fp64"] = run_server(bem, m, sel, rate, mesh.n)
+        m.close()
+    return out
+
+
+def assembly(a, bem, torch):
+    """Collocation assembly: 20000 elements (geodesic sphere + inner
+    cylinder), the dense 20000 x 20000 FP64 matrix on the device, plus the
+    matrix-free product."""
+    mesh = synth.sphere_cylinder_mesh(seed=3)
+    col = synth.collocation_points(mesh)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"workload": f"{mesh.n} elements (18000-triangle geodesic sphere + 2000-rectangle cylinder), "
+                       f"{mesh.n} x {mesh.n} FP64 matrix"}
+    c_d = torch.from_numpy(col).to(dev)
+    A = torch.empty((mesh.n, mesh.n), dtype=torch.float64, device=dev)
+    x = torch.from_numpy(mesh.sigma).to(dev)
+    y = torch.empty(mesh.n, dtype=torch.float64, device=dev)
+    for prec, name in ((bem.FP64, "fp64"), (bem.MIXED, "mixed")):
+        m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                     torch.from_numpy(mesh.sigma).to(dev), precision=prec)
+        bem.bem_assemble(m.handle, c_d, A)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bem.bem_assemble(m.handle, c_d, A)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        bem.bem_matvec(m.handle, x, y)
+        t0 = time.perf_counter()
+        bem.bem_matvec(m.handle, x, y)
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        nbytes = 8.0 * mesh.n * mesh.n
+        out[name] = {"assemble_ms": ta * 1e3, "matrix_write_GBps": nbytes / ta / 1e9,
+                     "entries_per_s": mesh.n * mesh.n / ta, "matvec_ms": tm * 1e3,
+                     "matvec_pairs_per_s": mesh.n * mesh.n / tm}
+        m.close()
+    del A
     return out
 
 

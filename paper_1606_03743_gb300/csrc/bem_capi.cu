@@ -308,8 +308,10 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     }
     m->d.n = (int)n;
     // the far-field pass splits the elements into chunks fixed by the mesh
-    // (so a point's sum is always split the same way), about 32k elements each
-    m->n_chunks = (int)std::min<int64_t>(16, std::max<int64_t>(1, (n + 32767) / 32768));
+    // (so a point's sum is always split the same way): at least ~2500
+    // elements each, at most 16 chunks, enough work items to fill the GPU
+    // even for a few thousand points
+    m->n_chunks = (int)std::min<int64_t>(16, std::max<int64_t>(1, (n + 2499) / 2500));
     m->chunk_len = (int)(((n + m->n_chunks - 1) / m->n_chunks + 31) / 32 * 32);
     m->n_chunks = (int)((n + m->chunk_len - 1) / m->chunk_len);
     MeshDev& d = m->d;
@@ -451,16 +453,10 @@ int bem_centroids(bem_mesh* m, double* out, void* stream) {
     return BEM_OK;
 }
 
-int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* E, void* stream) {
-    int rc = check_mesh(m, "bem_eval");
-    if (rc) return rc;
-    if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && !points)) {
-        set_error("bem_eval: bad arguments (n = %lld)", (long long)n);
-        return BEM_ERR_INVALID;
-    }
-    if (n == 0) return BEM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    BEM_CUDA_TRY(cudaSetDevice(m->device));
+namespace {
+// One slice of bem_eval (at most kEvalSlice points).
+int eval_slice(bem_mesh* m, const double* points, int64_t n, double* phi, double* E, cudaStream_t s) {
+    int rc;
     if ((rc = ensure_points(m, (size_t)n))) return rc;
     Work& w = m->w;
     const double* dpts;
@@ -482,6 +478,28 @@ int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* 
     if (phi) BEM_CUDA_TRY(cudaMemcpyAsync(phi, sphi, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     if (E) BEM_CUDA_TRY(cudaMemcpyAsync(E, sE, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BEM_OK;
+}
+// Large calls run in slices: the scratch grows with the points of one
+// slice, and results do not depend on how the points are grouped.
+constexpr int64_t kEvalSlice = int64_t(1) << 21;
+}  // namespace
+
+int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* E, void* stream) {
+    int rc = check_mesh(m, "bem_eval");
+    if (rc) return rc;
+    if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && !points)) {
+        set_error("bem_eval: bad arguments (n = %lld)", (long long)n);
+        return BEM_ERR_INVALID;
+    }
+    if (n == 0) return BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    for (int64_t off = 0; off < n; off += kEvalSlice) {
+        const int64_t k = std::min(kEvalSlice, n - off);
+        rc = eval_slice(m, points + 3 * off, k, phi ? phi + off : nullptr, E ? E + 3 * off : nullptr, s);
+        if (rc) return rc;
+    }
     return BEM_OK;
 }
 

@@ -48,7 +48,7 @@ namespace bem {
 
 // field points per lane of the mixed and FP64 paths (a warp's tile is 32 x PT points)
 #ifndef BEM_MIXED_PT
-#define BEM_MIXED_PT 3
+#define BEM_MIXED_PT 4
 #endif
 #ifndef BEM_FP64_PT
 #define BEM_FP64_PT 2
@@ -221,8 +221,12 @@ constexpr size_t far_smem_bytes() {
 // into counters[16..18] the (warp, element) pairs that ran one band for the
 // whole warp, those that fell back to per-point bands, and the node
 // evaluations executed (lanes x points x nodes, masked ones included).
+// CTAs per SM the register allocation must allow (4 x 4 warps)
+#ifndef BEM_MIN_BLOCKS
+#define BEM_MIN_BLOCKS 4
+#endif
 template <bool F64, int PT, bool WANT_E, int MODE, bool STATS>
-__global__ void __launch_bounds__(kWarps * 32) k_far(const FarK p) {
+__global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK p) {
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
     constexpr bool ACC64 = !F64 && MODE == 0;  // FP64 accumulators in shared memory
