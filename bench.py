@@ -188,6 +188,7 @@ def main():
 
     import torch
     import paper_1606_03743_gb300 as bem
+    from paper_1606_03743_gb300 import shard
 
     torch.cuda.set_device(local)
     dist = None
@@ -202,7 +203,7 @@ def main():
 
     prec = bem.MIXED if a.precision == "mixed" else bem.FP64
     mesh = synth.coax_mesh(seed=2)
-    pts = synth.coax_points(seed=2 + 1000 * rank, n=a.points)  # each rank its own batch
+    pts = synth.coax_points(seed=shard.rank_seed(2, rank), n=a.points)  # each rank its own batch
     dev = torch.device("cuda", local)
     m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
                  torch.from_numpy(mesh.sigma).to(dev), precision=prec)
@@ -242,12 +243,9 @@ def main():
     ck = clocks.stop()
     m.set_timing(False)
     ms = t_start.elapsed_time(t_end)
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = shard.slowest_rank_ms(ms, dist, dev)
     pairs_step = float(a.points) * mesh.n
-    value = world * pairs_step * a.steps / (ms * 1e-3)
+    value = shard.job_rate(world * pairs_step * a.steps, ms)
 
     # roofline of the dominant kernel (far-field cubature), from its own events:
     # the FP32 pipe's issue rate bounds it (152 SMs x 128 lanes x 2070 MHz
