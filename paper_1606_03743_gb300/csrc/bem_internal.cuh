@@ -79,6 +79,7 @@ struct bem_mesh {
     double kc = 0.0;          // 1 / (4 pi eps0)
     double limits[2][5];      // DR band limits per type
     double coord_max = 0.0;   // largest |coordinate| of any element corner
+    double grid = 1.0;        // mixed path: spacing (a power of two) of the hi parts of points and centroids
     int n_chunks = 1;         // element chunks of the far-field pass (fixed by the mesh)
     int chunk_len = 0;        // elements per chunk (a multiple of 32)
     size_t budget = 0;

@@ -29,15 +29,27 @@
 //
 // Arithmetic:
 //  * FP64 path: everything in double precision.
-//  * Mixed path: points and centroids are split into FP32 hi + lo parts, and
-//    P - Q_i is formed as ((P_hi - C_hi) + P_lo) - (o_i + C_lo): the small
-//    lo part of the centroid rides with the node offset o_i (both are small),
-//    so the difference keeps FP32 relative accuracy anywhere in space.  Node
-//    offsets, rsqrt and the sums are FP32: each element's node terms (at
-//    most 33) are summed on their own, eight such element sums are added up,
-//    and that sum is flushed into FP64 accumulators in shared memory.  No
-//    FP32 sum runs over more than 33 terms; the FP64 pipe sees two adds per
-//    element and point.
+//  * Mixed path: points and centroids are split into FP32 hi + lo parts with
+//    the hi parts on one power-of-two grid fixed by the mesh, so that in
+//    d = P - C = (P_hi - C_hi) + (P_lo - C_lo) the first difference is exact
+//    and d is rounded once: FP32 relative accuracy anywhere in space, with
+//    rounding errors that differ from element to element instead of one
+//    common shift of the point.  The node offsets lie in the
+//    element plane, o_i = alpha_i e0 + beta_i e1, so with u = d.e0, v = d.e1
+//    and s = |d|^2 (once per point and element) each node needs only
+//      r_i^2 = s + |o_i|^2 - 2 (alpha_i u + beta_i v),
+//    and the field sum_i b_i (d - o_i) (b_i = w_i q / r_i^3) is rebuilt per
+//    element from B = sum b_i, sum b_i alpha_i, sum b_i beta_i:
+//      d B - e0 sum b_i alpha_i - e1 sum b_i beta_i.
+//    That is 10 FP32 operations and one rsqrt per node and point instead of
+//    13; two points of a lane go through packed f32x2 instructions together.
+//    At DR >= 3 the terms of r_i^2 cancel by at most a factor of about 4, so
+//    the split costs about two bits of an FP32 result.  rsqrt and the sums
+//    are FP32: each element's node terms (at most 33) are summed on their
+//    own, eight such element sums are added up, and that sum is flushed into
+//    FP64 accumulators in shared memory.  No FP32 sum runs over more than 33
+//    terms; the FP64 pipe sees two adds per element and point.
+#include <math.h>
 #include <stdio.h>
 
 #include <type_traits>
@@ -59,6 +71,17 @@ constexpr int kPtMixed = BEM_MIXED_PT, kPtFp64 = BEM_FP64_PT;
 #define BEM_NODE_UNROLL 4
 #endif
 constexpr int kNodeUnroll = BEM_NODE_UNROLL;
+// mixed path: elements per FP32 running sum before it moves into FP64 (a power of two)
+#ifndef BEM_FLUSH
+#define BEM_FLUSH 8
+#endif
+constexpr int kFlush = BEM_FLUSH;
+static_assert((kFlush & (kFlush - 1)) == 0 && kFlush <= 32, "flush interval: a power of two up to 32");
+// mixed path: bands 1..kRefineBands (the nearest, 33-point first) refine rsqrt by a Newton step
+#ifndef BEM_REFINE_BANDS
+#define BEM_REFINE_BANDS 0
+#endif
+constexpr int kRefineBands = BEM_REFINE_BANDS;
 
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
 constexpr int kWarps = 4;     // warps per CTA
@@ -89,6 +112,7 @@ struct FarK {
     double tau2d[2][5];
     const unsigned* bbox;  // field-point bounding box (order-preserving float bits: min xyz, max xyz)
     float coord_max;       // largest |coordinate| of the mesh
+    double grid, inv_grid; // mixed path: grid of the hi parts (a power of two) and its inverse
     const int* n_dev;      // if set: the point count is read here (n_pts is then the capacity)
     int tile_pts;          // points per work-item tile (32 x PT)
 };
@@ -187,6 +211,66 @@ __device__ __forceinline__ void nodes(const R4* __restrict__ nd, int n, const R 
     for (; i < n; ++i) node<R, R4, PT, WANT_E, MASKED, false>(nd[i], dx, dy, dz, acc, mq);
 }
 
+// ---- mixed path: two field points per packed f32x2 operation
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One node of an element at the NP point pairs of a lane, in the frame form:
+// ab = (-2 alpha, -2 alpha, -2 beta, -2 beta), ow = (|o|^2, |o|^2, w q, w q);
+// s, u, v = |d|^2, d.e0, d.e1 per point.  acc[k] = (sum a, sum b,
+// sum b (-2 alpha), sum b (-2 beta)) with a = w q / r, b = a / r^2 (phi only:
+// sum a).  A point that must not take part carries s = +inf: then r^2 = +inf,
+// rsqrt gives +0 and its terms are exact zeros, while the other points'
+// arithmetic is bit-for-bit that of a pass without it.  INIT: the sums start
+// from this term.
+template <int NP, bool WANT_E, bool INIT, bool REFINE>
+__device__ __forceinline__ void node2(const float4 ab, const float4 ow, const float2 (&s)[NP],
+                                      const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
+    const float2 al = make_float2(ab.x, ab.y), be = make_float2(ab.z, ab.w);
+    const float2 oo = make_float2(ow.x, ow.y), w = make_float2(ow.z, ow.w);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const float2 r2 = fma2(al, u[k], fma2(be, v[k], add2(s[k], oo)));
+        float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        if (REFINE) {  // one Newton step: y <- y + (y/2) (1 - x y^2)
+            const float2 m = mul2(r2, inv);
+            const float2 t = fma2(make_float2(-m.x, -m.y), inv, make_float2(1.0f, 1.0f));
+            inv = fma2(mul2(inv, make_float2(0.5f, 0.5f)), t, inv);
+        }
+        const float2 a = mul2(w, inv);  // q_i / r_i
+        if (INIT) {
+            acc[k][0] = a;
+        } else {
+            acc[k][0] = add2(acc[k][0], a);
+        }
+        if (WANT_E) {
+            const float2 b = mul2(a, mul2(inv, inv));  // q_i / r_i^3
+            if (INIT) {
+                acc[k][1] = b; acc[k][2] = mul2(b, al); acc[k][3] = mul2(b, be);
+            } else {
+                acc[k][1] = add2(acc[k][1], b);
+                acc[k][2] = fma2(b, al, acc[k][2]);
+                acc[k][3] = fma2(b, be, acc[k][3]);
+            }
+        }
+    }
+}
+
+// All n nodes of one rule (two records per node in nd, broadcast reads).
+template <int NP, bool WANT_E, bool INIT, bool REFINE>
+__device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
+                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
+    int i = 0;
+    if (INIT) {  // every rule has at least four nodes
+        node2<NP, WANT_E, true, REFINE>(nd[0], nd[1], s, u, v, acc);
+        i = 1;
+    }
+#pragma unroll kNodeUnroll
+    for (; i < n; ++i) node2<NP, WANT_E, false, REFINE>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+}
+
 // Shared memory of one warp.
 template <typename R, typename R4, int PT, bool ACC64>
 struct WarpSmem {
@@ -195,7 +279,7 @@ struct WarpSmem {
     R4 e0[32];   // frame e0, w = q (element charge)
     R4 e1[32];   // frame e1
     R thr[32 * 5];
-    R4 nd[2][kNodeBuf];
+    R4 nd[2][sizeof(R) == 8 ? kNodeBuf : 2 * kNodeBuf];  // node records (FP64: one per node; mixed: two)
     double acc64[ACC64 ? PT * 4 * 32 : 1];
 };
 
@@ -266,6 +350,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
     }
     __syncthreads();
 
+    static_assert(F64 || PT % 2 == 0, "the mixed path works on point pairs");
+    constexpr int NP = F64 ? 1 : PT / 2;  // point pairs of a lane (mixed path)
     R ones[PT];
 #pragma unroll
     for (int q = 0; q < PT; ++q) ones[q] = (R)1;
@@ -294,9 +380,12 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 px[q] = X; py[q] = Y; pz[q] = Z;
                 lx[q] = ly[q] = lz[q] = 0.0f;
             } else {
-                const float hx = (float)X, hy = (float)Y, hz = (float)Z;
-                px[q] = hx; py[q] = hy; pz[q] = hz;
-                lx[q] = (float)(X - (double)hx); ly[q] = (float)(Y - (double)hy); lz[q] = (float)(Z - (double)hz);
+                // hi part on the centroids' grid (exact differences P_hi - C_hi), lo part the rest
+                const double hX = rint(X * p.inv_grid) * p.grid, hY = rint(Y * p.inv_grid) * p.grid,
+                             hZ = rint(Z * p.inv_grid) * p.grid;
+                px[q] = (float)hX; py[q] = (float)hY; pz[q] = (float)hZ;
+                lx[q] = (float)(X - (double)px[q]); ly[q] = (float)(Y - (double)py[q]);
+                lz[q] = (float)(Z - (double)pz[q]);
             }
         }
         // ---- bounding sphere of the tile (FP32, only for the band test)
@@ -305,7 +394,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
-                const float v[3] = {(float)px[q], (float)py[q], (float)pz[q]};
+                const float v[3] = {(float)px[q] + lx[q], (float)py[q] + ly[q], (float)pz[q] + lz[q]};
 #pragma unroll
                 for (int k = 0; k < 3; ++k) { mn[k] = fminf(mn[k], v[k]); mx[k] = fmaxf(mx[k], v[k]); }
             }
@@ -315,7 +404,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             float r2 = 0.0f;
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
-                const float ax = (float)px[q] - wcx, ay = (float)py[q] - wcy, az = (float)pz[q] - wcz;
+                const float ax = ((float)px[q] + lx[q]) - wcx, ay = ((float)py[q] + ly[q]) - wcy,
+                            az = ((float)pz[q] + lz[q]) - wcz;
                 r2 = fmaxf(r2, ax * ax + ay * ay + az * az);
             }
             wrad = sqrtf(warp_max(r2));
@@ -323,19 +413,37 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         }
         int nvalid = 0;  // valid points of the tile (for the statistics)
         if (STATS) nvalid = min(32 * PT, n_pts - base);
+        // mixed path: points 2k and 2k+1 of the lane as packed pairs (hi, lo parts)
+        float2 P2[3][NP], L2[3][NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            if constexpr (!F64) {
+                P2[0][k] = make_float2(px[2 * k], px[2 * k + 1]);
+                P2[1][k] = make_float2(py[2 * k], py[2 * k + 1]);
+                P2[2][k] = make_float2(pz[2 * k], pz[2 * k + 1]);
+                L2[0][k] = make_float2(lx[2 * k], lx[2 * k + 1]);
+                L2[1][k] = make_float2(ly[2 * k], ly[2 * k + 1]);
+                L2[2][k] = make_float2(lz[2 * k], lz[2 * k + 1]);
+            }
+        }
 
         // ---- accumulators
-        R acc[PT][4];  // FP64 path: the sums; mixed: FP32 sum of up to 8 element sums
+        R acc[F64 ? PT : 1][4];  // FP64 evaluation: the running sums
+        float2 acc8[NP][4];      // mixed: FP32 sum of up to 8 element sums (point pairs)
         int ncnt[PT];
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
             ncnt[q] = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                acc[q][c] = (R)0;
+                if constexpr (F64) acc[q][c] = (R)0;
                 if constexpr (ACC64) ws.acc64[(q * 4 + c) * 32 + lane] = 0.0;
             }
         }
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc8[k][c] = make_float2(0.0f, 0.0f);
 
         const int el0 = chunk * p.chunk_len, el1 = min(p.n_el, el0 + p.chunk_len);
         int par = 0;  // node buffer parity
@@ -398,138 +506,242 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 int ty;
                 if constexpr (F64) ty = (int)c.w;
                 else ty = __float_as_int(c.w);
-                // (P_hi - C_hi) + P_lo; the centroid's lo part is in the node offsets
-                R dx[PT], dy[PT], dz[PT];
-#pragma unroll
-                for (int q = 0; q < PT; ++q) {
-                    if constexpr (F64) {
-                        dx[q] = px[q] - c.x; dy[q] = py[q] - c.y; dz[q] = pz[q] - c.z;
-                    } else {
-                        dx[q] = (px[q] - c.x) + lx[q];
-                        dy[q] = (py[q] - c.y) + ly[q];
-                        dz[q] = (pz[q] - c.z) + lz[q];
-                    }
-                }
-                // per-element sums (mixed path, assembly; started by the element's
-                // first rule pass) or the running sums (FP64 evaluation)
-                constexpr bool kElemSum = MODE == 1 || !F64;
-                R eacc[PT][4];
-                R(&dst)[PT][4] = kElemSum ? eacc : acc;
 
-                // expand rule r of element e into the free node buffer (lane i: node i)
-                auto expand = [&](int r) -> int {
-                    const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
-                    const R4 a = ws.e0[e], b = ws.e1[e];
-                    R ox = 0, oy = 0, oz = 0;  // mixed path: the centroid's lo part
-                    if constexpr (!F64) {
-                        const R4 cl = ws.cl[e];
-                        ox = cl.x; oy = cl.y; oz = cl.z;
-                    }
-                    for (int i = lane; i < n; i += 32) {
-                        const R al = rs.al[st + i], be = rs.be[st + i];
-                        ws.nd[par][i] = R4{fmad(al, a.x, fmad(be, b.x, ox)), fmad(al, a.y, fmad(be, b.y, oy)),
-                                           fmad(al, a.z, fmad(be, b.z, oz)), rs.w[st + i] * a.w};
-                    }
-                    __syncwarp();
-                    return n;
-                };
-
-                if (cd >= 1 && cd <= 5) {
-                    const int n = expand(band_rule(cd));
-                    nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, ones);
-                    par ^= 1;
-                    if (STATS && lane == 0) {
-                        atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
-                        atomicAdd(&rs.stat[12], 1ull);
-                        atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
-                    }
-                } else {
-                    // per-point bands
-                    int bq[PT];
-                    const R* th = ws.thr + e * 5;
-                    unsigned mask = 0;
+                if constexpr (F64) {
+                    // ---------------- FP64 path: P - Q_i = (P - C) - o_i
+                    R dx[PT], dy[PT], dz[PT];
 #pragma unroll
                     for (int q = 0; q < PT; ++q) {
-                        const R d2 = dx[q] * dx[q] + dy[q] * dy[q] + dz[q] * dz[q];
-                        bq[q] = band_of<R>(d2, th);
-                        if (valid[q]) mask |= 1u << bq[q];
+                        dx[q] = px[q] - c.x; dy[q] = py[q] - c.y; dz[q] = pz[q] - c.z;
                     }
-                    mask = __reduce_or_sync(0xffffffffu, mask);
-                    if (mask & 1u) {
-                        bool want[PT];
+                    // assembly: per-element sums; evaluation: the running sums
+                    constexpr bool kElemSum = MODE == 1;
+                    R eacc[PT][4];
+                    R(&dst)[PT][4] = kElemSum ? eacc : acc;
+
+                    // expand rule r of element e into the free node buffer (lane i: node i)
+                    auto expand = [&](int r) -> int {
+                        const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
+                        const R4 a = ws.e0[e], b = ws.e1[e];
+                        for (int i = lane; i < n; i += 32) {
+                            const R al = rs.al[st + i], be = rs.be[st + i];
+                            ws.nd[par][i] = R4{fmad(al, a.x, be * b.x), fmad(al, a.y, be * b.y),
+                                               fmad(al, a.z, be * b.z), rs.w[st + i] * a.w};
+                        }
+                        __syncwarp();
+                        return n;
+                    };
+
+                    if (cd >= 1 && cd <= 5) {
+                        const int n = expand(band_rule(cd));
+                        nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, ones);
+                        par ^= 1;
+                        if (STATS && lane == 0) {
+                            atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
+                            atomicAdd(&rs.stat[12], 1ull);
+                            atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
+                        }
+                    } else {
+                        // per-point bands
+                        int bq[PT];
+                        const R* th = ws.thr + e * 5;
+                        unsigned mask = 0;
 #pragma unroll
-                        for (int q = 0; q < PT; ++q) want[q] = valid[q] && bq[q] == 0;
-                        append_near<PT>(p, want, sidx, b0 + e, chunk, ncnt, lane);
-                    }
-                    if (kElemSum) {  // near-only points get zero far sums
+                        for (int q = 0; q < PT; ++q) {
+                            const R d2 = dx[q] * dx[q] + dy[q] * dy[q] + dz[q] * dz[q];
+                            bq[q] = band_of<R>(d2, th);
+                            if (valid[q]) mask |= 1u << bq[q];
+                        }
+                        mask = __reduce_or_sync(0xffffffffu, mask);
+                        if (mask & 1u) {
+                            bool want[PT];
 #pragma unroll
-                        for (int q = 0; q < PT; ++q)
+                            for (int q = 0; q < PT; ++q) want[q] = valid[q] && bq[q] == 0;
+                            append_near<PT>(p, want, sidx, b0 + e, chunk, ncnt, lane);
+                        }
+                        if (kElemSum) {  // near-only points get zero far sums
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) eacc[q][k] = (R)0;
-                    }
+                            for (int q = 0; q < PT; ++q)
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) eacc[q][k] = (R)0;
+                        }
 #pragma unroll 1
-                    for (int band = 1; band <= 5; ++band) {
-                        if (!(mask & (1u << band))) continue;
-                        // points of other bands: zero charge, parked far from every node
-                        // (the active points' differences are formed afresh, exactly as above)
-                        R mq[PT];
-                        {
-                            const R4 cc = ws.c[e];
+                        for (int band = 1; band <= 5; ++band) {
+                            if (!(mask & (1u << band))) continue;
+                            // points of other bands: zero charge, parked far from every node
+                            R mq[PT], mx[PT], my[PT], mz[PT];
 #pragma unroll
                             for (int q = 0; q < PT; ++q) {
                                 const bool on = bq[q] == band;
                                 mq[q] = on ? (R)1 : (R)0;
-                                R ax, ay, az;
-                                if constexpr (F64) {
-                                    ax = px[q] - cc.x; ay = py[q] - cc.y; az = pz[q] - cc.z;
-                                } else {
-                                    ax = (px[q] - cc.x) + lx[q];
-                                    ay = (py[q] - cc.y) + ly[q];
-                                    az = (pz[q] - cc.z) + lz[q];
+                                mx[q] = on ? dx[q] : (R)1e3;
+                                my[q] = on ? dy[q] : (R)1e3;
+                                mz[q] = on ? dz[q] : (R)1e3;
+                            }
+                            const int n = expand(band_rule(band));
+                            nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, mx, my, mz, dst, mq);
+                            par ^= 1;
+                            if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
+                        }
+                        if (STATS) {
+                            if (lane == 0) atomicAdd(&rs.stat[13], 1ull);
+#pragma unroll
+                            for (int q = 0; q < PT; ++q) {
+                                for (int band = 0; band <= 5; ++band) {
+                                    const unsigned m = __ballot_sync(0xffffffffu, valid[q] && bq[q] == band);
+                                    if (lane == 0 && m) atomicAdd(&rs.stat[6 * ty + band], (unsigned long long)__popc(m));
                                 }
-                                dx[q] = on ? ax : (R)1e3;
-                                dy[q] = on ? ay : (R)1e3;
-                                dz[q] = on ? az : (R)1e3;
-                            }
-                        }
-                        const int n = expand(band_rule(band));
-                        nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, dx, dy, dz, dst, mq);
-                        par ^= 1;
-                        if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
-                    }
-                    if (STATS) {
-                        if (lane == 0) atomicAdd(&rs.stat[13], 1ull);
-#pragma unroll
-                        for (int q = 0; q < PT; ++q) {
-                            for (int band = 0; band <= 5; ++band) {
-                                const unsigned m = __ballot_sync(0xffffffffu, valid[q] && bq[q] == band);
-                                if (lane == 0 && m) atomicAdd(&rs.stat[6 * ty + band], (unsigned long long)__popc(m));
                             }
                         }
                     }
-                }
-
-                if constexpr (MODE == 0 && !F64) {
-                    // add the element sums; every 8 elements move the FP32 sum into FP64
-#pragma unroll
-                    for (int q = 0; q < PT; ++q)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[q][k] += eacc[q][k];
-                    if (((b0 + e) & 7) == 7 || e == nb - 1) {
+                    if constexpr (MODE == 1) {
+                        // assembly: one potential per pair, times 1/(4 pi eps0); near pairs are filled later
 #pragma unroll
                         for (int q = 0; q < PT; ++q)
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                ws.acc64[(q * 4 + k) * 32 + lane] += (double)acc[q][k];
-                                acc[q][k] = (R)0;
-                            }
+                            if (valid[q]) p.A[(size_t)p.perm[sidx[q]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
                     }
-                }
-                if constexpr (MODE == 1) {
-                    // assembly: one potential per pair, times 1/(4 pi eps0); near pairs are filled later
+                } else {
+                    // ---------------- mixed path (frame form, point pairs)
+                    // d = (P_hi - C_hi) + (P_lo - C_lo) of pair k, the first difference exact
+                    // (formed again where needed rather than held through the node loop)
+                    auto diff = [&](int k, float2& dx, float2& dy, float2& dz) {
+                        const float4 ch = ws.c[e], cl = ws.cl[e];
+                        dx = add2(add2(P2[0][k], dup(-ch.x)), add2(L2[0][k], dup(-cl.x)));
+                        dy = add2(add2(P2[1][k], dup(-ch.y)), add2(L2[1][k], dup(-cl.y)));
+                        dz = add2(add2(P2[2][k], dup(-ch.z)), add2(L2[2][k], dup(-cl.z)));
+                    };
+                    // s = |d|^2, u = d.e0, v = d.e1 of every pair
+                    float2 sv[NP], uv[NP], vv[NP];
+                    {
+                        const float4 f0 = ws.e0[e], f1 = ws.e1[e];
 #pragma unroll
-                    for (int q = 0; q < PT; ++q)
-                        if (valid[q]) p.A[(size_t)p.perm[sidx[q]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
+                        for (int k = 0; k < NP; ++k) {
+                            float2 dx, dy, dz;
+                            diff(k, dx, dy, dz);
+                            sv[k] = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                            uv[k] = fma2(dx, dup(f0.x), fma2(dy, dup(f0.y), mul2(dz, dup(f0.z))));
+                            vv[k] = fma2(dx, dup(f1.x), fma2(dy, dup(f1.y), mul2(dz, dup(f1.z))));
+                        }
+                    }
+                    float2 eacc[NP][4];  // this element's sums (started by its first rule pass)
+                    // expand rule r of element e into the free node buffer (lane i: node i)
+                    auto expand = [&](int r) -> int {
+                        const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
+                        const float4 f0 = ws.e0[e], f1 = ws.e1[e];
+                        for (int i = lane; i < n; i += 32) {
+                            const float al = rs.al[st + i], be = rs.be[st + i];
+                            const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y),
+                                        oz = fmaf(al, f0.z, be * f1.z);
+                            const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
+                            const float am = -2.0f * al, bm = -2.0f * be, wq = rs.w[st + i] * f0.w;
+                            ws.nd[par][2 * i] = make_float4(am, am, bm, bm);
+                            ws.nd[par][2 * i + 1] = make_float4(oo, oo, wq, wq);
+                        }
+                        __syncwarp();
+                        return n;
+                    };
+
+                    if (cd >= 1 && cd <= 5) {
+                        const int n = expand(band_rule(cd));
+                        if (cd <= kRefineBands) nodes2<NP, WANT_E, true, kRefineBands != 0>(ws.nd[par], n, sv, uv, vv, eacc);
+                        else nodes2<NP, WANT_E, true, false>(ws.nd[par], n, sv, uv, vv, eacc);
+                        par ^= 1;
+                        if (STATS && lane == 0) {
+                            atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
+                            atomicAdd(&rs.stat[12], 1ull);
+                            atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
+                        }
+                    } else {
+                        // per-point bands
+                        int bq[PT];
+                        const float* th = ws.thr + e * 5;
+                        unsigned mask = 0;
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) {
+                            bq[2 * k] = band_of<float>(sv[k].x, th);
+                            bq[2 * k + 1] = band_of<float>(sv[k].y, th);
+                        }
+#pragma unroll
+                        for (int q = 0; q < PT; ++q)
+                            if (valid[q]) mask |= 1u << bq[q];
+                        mask = __reduce_or_sync(0xffffffffu, mask);
+                        if (mask & 1u) {
+                            bool want[PT];
+#pragma unroll
+                            for (int q = 0; q < PT; ++q) want[q] = valid[q] && bq[q] == 0;
+                            append_near<PT>(p, want, sidx, b0 + e, chunk, ncnt, lane);
+                        }
+#pragma unroll
+                        for (int k = 0; k < NP; ++k)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) eacc[k][j] = make_float2(0.0f, 0.0f);  // near-only points
+#pragma unroll 1
+                        for (int band = 1; band <= 5; ++band) {
+                            if (!(mask & (1u << band))) continue;
+                            // points of other bands sit at infinite distance in this pass
+                            constexpr float kInf = kRefineBands ? 3.0e38f : __builtin_huge_valf();
+                            float2 sm[NP];
+#pragma unroll
+                            for (int k = 0; k < NP; ++k)
+                                sm[k] = make_float2(bq[2 * k] == band ? sv[k].x : kInf,
+                                                    bq[2 * k + 1] == band ? sv[k].y : kInf);
+                            const int n = expand(band_rule(band));
+                            if (band <= kRefineBands) nodes2<NP, WANT_E, false, kRefineBands != 0>(ws.nd[par], n, sm, uv, vv, eacc);
+                            else nodes2<NP, WANT_E, false, false>(ws.nd[par], n, sm, uv, vv, eacc);
+                            par ^= 1;
+                            if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
+                        }
+                        if (STATS) {
+                            if (lane == 0) atomicAdd(&rs.stat[13], 1ull);
+#pragma unroll
+                            for (int q = 0; q < PT; ++q) {
+                                for (int band = 0; band <= 5; ++band) {
+                                    const unsigned m = __ballot_sync(0xffffffffu, valid[q] && bq[q] == band);
+                                    if (lane == 0 && m) atomicAdd(&rs.stat[6 * ty + band], (unsigned long long)__popc(m));
+                                }
+                            }
+                        }
+                    }
+
+                    if constexpr (MODE == 0) {
+                        // the element's phi and E = d B + (e0/2) B_alpha' + (e1/2) B_beta'
+                        // into the FP32 sums; every kFlush elements move those into FP64
+                        const float4 f0 = ws.e0[e], f1 = ws.e1[e];
+                        const float2 h0x = dup(0.5f * f0.x), h0y = dup(0.5f * f0.y), h0z = dup(0.5f * f0.z);
+                        const float2 h1x = dup(0.5f * f1.x), h1y = dup(0.5f * f1.y), h1z = dup(0.5f * f1.z);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) {
+                            acc8[k][0] = add2(acc8[k][0], eacc[k][0]);
+                            if (WANT_E) {
+                                float2 dx, dy, dz;
+                                diff(k, dx, dy, dz);
+                                // the element's field first, then one rounding of the running sum
+                                acc8[k][1] = add2(acc8[k][1], fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], mul2(h1x, eacc[k][3]))));
+                                acc8[k][2] = add2(acc8[k][2], fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], mul2(h1y, eacc[k][3]))));
+                                acc8[k][3] = add2(acc8[k][3], fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], mul2(h1z, eacc[k][3]))));
+                            }
+                        }
+                        if (((b0 + e) & (kFlush - 1)) == kFlush - 1 || e == nb - 1) {
+#pragma unroll
+                            for (int k = 0; k < NP; ++k)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    ws.acc64[((2 * k) * 4 + j) * 32 + lane] += (double)acc8[k][j].x;
+                                    ws.acc64[((2 * k + 1) * 4 + j) * 32 + lane] += (double)acc8[k][j].y;
+                                    acc8[k][j] = make_float2(0.0f, 0.0f);
+                                }
+                        }
+                    }
+                    if constexpr (MODE == 1) {
+                        // assembly: one potential per pair, times 1/(4 pi eps0); near pairs are filled later
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) {
+                            if (valid[2 * k])
+                                p.A[(size_t)p.perm[sidx[2 * k]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[k][0].x;
+                            if (valid[2 * k + 1])
+                                p.A[(size_t)p.perm[sidx[2 * k + 1]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[k][0].y;
+                        }
+                    }
                 }
             }
         }
@@ -560,6 +772,36 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 namespace {
 int uploaded_mask = 0;  // devices whose constant rule tables are loaded
 
+// FP32 copies of one rule's n weights whose exact sum is one as closely as
+// one-ulp nudges of single weights get it (within one ulp of the smallest
+// weight).  Rounding each weight on its own leaves the sum off by up to a few
+// 1e-8, which scales the charge of every element that uses the rule by the
+// same factor: a systematic error that, unlike independent rounding errors,
+// does not average out over many elements.
+void round_weights(const double* w, int n, float* out) {
+    for (int i = 0; i < n; ++i) out[i] = (float)w[i];
+    for (int it = 0; it < 4 * n; ++it) {
+        double sum = 0.0;  // exact: at most 33 floats within a few binades
+        for (int i = 0; i < n; ++i) sum += (double)out[i];
+        const double res = 1.0 - sum;
+        if (res == 0.0) break;
+        int best = -1;
+        double best_err = fabs(res);
+        float best_val = 0.0f;
+        for (int i = 0; i < n; ++i) {
+            const float c = nextafterf(out[i], res > 0.0 ? INFINITY : -INFINITY);
+            const double err = fabs(res - ((double)c - (double)out[i]));
+            if (err < best_err) {
+                best_err = err;
+                best = i;
+                best_val = c;
+            }
+        }
+        if (best < 0) break;
+        out[best] = best_val;
+    }
+}
+
 int upload_rules(int dev) {
     if (dev < 32 && (uploaded_mask >> dev) & 1) return BEM_OK;
     const RuleSet& rs = rules();
@@ -574,6 +816,9 @@ int upload_rules(int dev) {
             bf[t * kSlots + s] = (float)rs.beta[t][s];
             wf[t * kSlots + s] = (float)rs.w[t][s];
         }
+    for (int t = 0; t < 2; ++t)
+        for (int r = 0; r < 5; ++r)
+            round_weights(&rs.w[t][rs.start[t][r]], rs.n[t][r], &wf[t * kSlots + rs.start[t][r]]);
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_alpha_f, af, sizeof af));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_beta_f, bf, sizeof bf));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_w_f, wf, sizeof wf));
@@ -638,6 +883,8 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.kc = a.kc;
     k.bbox = a.bbox;
     k.coord_max = (float)m->coord_max;
+    k.grid = m->grid;
+    k.inv_grid = 1.0 / m->grid;
     k.n_dev = a.n_dev;
     for (int t = 0; t < 2; ++t)
         for (int i = 0; i < 5; ++i) {

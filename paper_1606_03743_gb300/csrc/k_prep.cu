@@ -7,7 +7,13 @@
 //                       L = (a + b) / 2, area = a b, e0 = (P1 - P0) / 2 = (a/2) u_x,
 //                       e1 = (P3 - P0) / 2 = (b/2) u_y
 // and writes the FP64 arrays (centroid, frame, L, area) plus the FP32
-// records of the mixed path with the centroid split into hi + lo floats.
+// records of the mixed path.  The centroid is split as C = C_hi + C_lo with
+// C_hi a multiple of a power-of-two grid g = 2^(e - 12), 2^e >= the largest
+// corner coordinate; the far-field kernel splits field points on the same
+// grid, so P_hi - C_hi is exact in FP32 and d = (P_hi - C_hi) + (P_lo - C_lo)
+// takes a single rounding.  (Rounding both to the nearest float instead
+// would round every P - C of a point on one common grid, a shift of the
+// point that is the same for all elements and is not averaged away.)
 #include <string.h>
 
 #include "bem_internal.cuh"
@@ -91,11 +97,28 @@ __global__ void k_prep(int n, const int* __restrict__ type, const double* __rest
     d.fr[6 * j + 3] = e1.x; d.fr[6 * j + 4] = e1.y; d.fr[6 * j + 5] = e1.z;
     d.geo[2 * j] = L;
     d.geo[2 * j + 1] = area;
-    const float hx = (float)cen.x, hy = (float)cen.y, hz = (float)cen.z;
-    d.chi[j] = make_float4(hx, hy, hz, __int_as_float(ty));  // w: type as int bits
-    d.clo[j] = make_float4((float)(cen.x - hx), (float)(cen.y - hy), (float)(cen.z - hz), (float)L);
+    // xyz of chi / clo: written by k_split once the grid is known
+    d.chi[j] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(ty));  // w: type as int bits
+    d.clo[j] = make_float4(0.0f, 0.0f, 0.0f, (float)L);
     d.e0[j] = make_float4((float)e0.x, (float)e0.y, (float)e0.z, (float)area);
     d.e1[j] = make_float4((float)e1.x, (float)e1.y, (float)e1.z, 0.0f);
+}
+
+// Centroid hi / lo parts on the grid g (a power of two, so c / g and the
+// products are exact): hi = rint(c / g) g, lo = c - hi.
+__global__ void k_split(int n, const double* __restrict__ cen, double g, double inv_g, float4* chi, float4* clo) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double h[3];
+    float lo[3];
+    for (int k = 0; k < 3; ++k) {
+        const double c = cen[3 * j + k];
+        h[k] = rint(c * inv_g) * g;
+        lo[k] = (float)(c - h[k]);
+    }
+    const float4 a = chi[j], b = clo[j];
+    chi[j] = make_float4((float)h[0], (float)h[1], (float)h[2], a.w);
+    clo[j] = make_float4(lo[0], lo[1], lo[2], b.w);
 }
 
 const char* code_name(int c) {
@@ -137,6 +160,12 @@ int launch_prep(bem_mesh* m, const int* types, const double* verts, const double
     }
     *bad_index = -1;
     *bad_code = 0;
+    int e = 0;
+    if (fm > 0.0f) frexp((double)fm, &e);  // 2^e > the largest coordinate
+    m->grid = ldexp(1.0, e - 12);
+    k_split<<<(n + 255) / 256, 256, 0, s>>>(n, m->d.cen, m->grid, 1.0 / m->grid, m->d.chi, m->d.clo);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
     return BEM_OK;
 }
 
