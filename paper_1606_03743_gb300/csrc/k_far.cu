@@ -77,11 +77,10 @@ constexpr int kNodeUnroll = BEM_NODE_UNROLL;
 #endif
 constexpr int kFlush = BEM_FLUSH;
 static_assert((kFlush & (kFlush - 1)) == 0 && kFlush <= 32, "flush interval: a power of two up to 32");
-// mixed path: bands 1..kRefineBands (the nearest, 33-point first) refine rsqrt by a Newton step
-#ifndef BEM_REFINE_BANDS
-#define BEM_REFINE_BANDS 0
+// mixed path: hold d = P - C through the node loop (1) or form it again for the field rebuild (0)
+#ifndef BEM_KEEP_D
+#define BEM_KEEP_D 0
 #endif
-constexpr int kRefineBands = BEM_REFINE_BANDS;
 
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
 constexpr int kWarps = 4;     // warps per CTA
@@ -225,7 +224,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // rsqrt gives +0 and its terms are exact zeros, while the other points'
 // arithmetic is bit-for-bit that of a pass without it.  INIT: the sums start
 // from this term.
-template <int NP, bool WANT_E, bool INIT, bool REFINE>
+template <int NP, bool WANT_E, bool INIT>
 __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const float2 (&s)[NP],
                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
     const float2 al = make_float2(ab.x, ab.y), be = make_float2(ab.z, ab.w);
@@ -233,12 +232,7 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const float2 r2 = fma2(al, u[k], fma2(be, v[k], add2(s[k], oo)));
-        float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-        if (REFINE) {  // one Newton step: y <- y + (y/2) (1 - x y^2)
-            const float2 m = mul2(r2, inv);
-            const float2 t = fma2(make_float2(-m.x, -m.y), inv, make_float2(1.0f, 1.0f));
-            inv = fma2(mul2(inv, make_float2(0.5f, 0.5f)), t, inv);
-        }
+        const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
         const float2 a = mul2(w, inv);  // q_i / r_i
         if (INIT) {
             acc[k][0] = a;
@@ -259,27 +253,31 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
 }
 
 // All n nodes of one rule (two records per node in nd, broadcast reads).
-template <int NP, bool WANT_E, bool INIT, bool REFINE>
+template <int NP, bool WANT_E, bool INIT>
 __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
                                        const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
     int i = 0;
     if (INIT) {  // every rule has at least four nodes
-        node2<NP, WANT_E, true, REFINE>(nd[0], nd[1], s, u, v, acc);
+        node2<NP, WANT_E, true>(nd[0], nd[1], s, u, v, acc);
         i = 1;
     }
 #pragma unroll kNodeUnroll
-    for (; i < n; ++i) node2<NP, WANT_E, false, REFINE>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+    for (; i < n; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
 }
 
 // Shared memory of one warp.
 template <typename R, typename R4, int PT, bool ACC64>
 struct WarpSmem {
-    R4 c[32];    // centroid (hi part for mixed), w = type
-    R4 cl[32];   // centroid lo part (mixed), w = L
-    R4 e0[32];   // frame e0, w = q (element charge)
-    R4 e1[32];   // frame e1
-    R thr[32 * 5];
-    R4 nd[2][sizeof(R) == 8 ? kNodeBuf : 2 * kNodeBuf];  // node records (FP64: one per node; mixed: two)
+    static constexpr bool kMixed = sizeof(R) == 4;
+    R4 c[kMixed ? 1 : 32];   // FP64: centroid, w = type
+    R4 e0[32];               // frame e0, w = q (element charge)
+    R4 e1[32];               // frame e1; mixed: w = type (int bits)
+    R thr[32 * 5];           // squared band limits (tau L)^2
+    // mixed: per element, the values each node pass and the field rebuild
+    // read, duplicated into (x, x, y, y) pairs for the packed f32x2 arithmetic:
+    // -C_hi, -C_lo, e0, e1, e0 / 2, e1 / 2 (nine float4)
+    float4 pr[kMixed ? 32 * 9 : 1];
+    R4 nd[2][kMixed ? 2 * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: two)
     double acc64[ACC64 ? PT * 4 * 32 : 1];
 };
 
@@ -465,6 +463,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         cl = R4{0, 0, 0, L};
                         ws.e0[lane] = R4{p.fr[6 * j], p.fr[6 * j + 1], p.fr[6 * j + 2], sg * area};
                         ws.e1[lane] = R4{p.fr[6 * j + 3], p.fr[6 * j + 4], p.fr[6 * j + 5], 0.0};
+                        ws.c[lane] = c;
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
                             const double t = p.tau2d[ty][k] * L * L;
@@ -472,11 +471,21 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             th[k] = (float)t;
                         }
                     } else {
-                        c = p.chi[j];  // w: the element type as int bits
+                        c = p.chi[j];
                         cl = p.clo[j];
                         const float4 a = p.e0f[j], b = p.e1f[j];
                         ws.e0[lane] = R4{a.x, a.y, a.z, (float)(sg * area)};
-                        ws.e1[lane] = R4{b.x, b.y, b.z, 0.0f};
+                        ws.e1[lane] = R4{b.x, b.y, b.z, __int_as_float(ty)};
+                        float4* pr = ws.pr + lane * 9;
+                        pr[0] = make_float4(-c.x, -c.x, -c.y, -c.y);
+                        pr[1] = make_float4(-c.z, -c.z, -cl.x, -cl.x);
+                        pr[2] = make_float4(-cl.y, -cl.y, -cl.z, -cl.z);
+                        pr[3] = make_float4(a.x, a.x, a.y, a.y);
+                        pr[4] = make_float4(a.z, a.z, b.x, b.x);
+                        pr[5] = make_float4(b.y, b.y, b.z, b.z);
+                        pr[6] = make_float4(0.5f * a.x, 0.5f * a.x, 0.5f * a.y, 0.5f * a.y);
+                        pr[7] = make_float4(0.5f * a.z, 0.5f * a.z, 0.5f * b.x, 0.5f * b.x);
+                        pr[8] = make_float4(0.5f * b.y, 0.5f * b.y, 0.5f * b.z, 0.5f * b.z);
                         const float L = cl.w;
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
@@ -484,8 +493,6 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             ws.thr[lane * 5 + k] = th[k];
                         }
                     }
-                    ws.c[lane] = c;
-                    ws.cl[lane] = cl;
                     // conservative band test of the whole tile against this element
                     const float dx = ((float)(wcx - (float)c.x)) - (float)cl.x;
                     const float dy = ((float)(wcy - (float)c.y)) - (float)cl.y;
@@ -502,13 +509,13 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             const int nb = min(32, el1 - b0);
             for (int e = 0; e < nb; ++e) {
                 const int cd = __shfl_sync(0xffffffffu, code, e);
-                const R4 c = ws.c[e];
                 int ty;
-                if constexpr (F64) ty = (int)c.w;
-                else ty = __float_as_int(c.w);
+                if constexpr (F64) ty = (int)ws.c[e].w;
+                else ty = __float_as_int(ws.e1[e].w);
 
                 if constexpr (F64) {
                     // ---------------- FP64 path: P - Q_i = (P - C) - o_i
+                    const R4 c = ws.c[e];
                     R dx[PT], dy[PT], dz[PT];
 #pragma unroll
                     for (int q = 0; q < PT; ++q) {
@@ -604,23 +611,32 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     // ---------------- mixed path (frame form, point pairs)
                     // d = (P_hi - C_hi) + (P_lo - C_lo) of pair k, the first difference exact
                     // (formed again where needed rather than held through the node loop)
+                    const float4* pr = ws.pr + e * 9;
+                    auto lo2 = [](float4 v) { return make_float2(v.x, v.y); };
+                    auto hi2 = [](float4 v) { return make_float2(v.z, v.w); };
                     auto diff = [&](int k, float2& dx, float2& dy, float2& dz) {
-                        const float4 ch = ws.c[e], cl = ws.cl[e];
-                        dx = add2(add2(P2[0][k], dup(-ch.x)), add2(L2[0][k], dup(-cl.x)));
-                        dy = add2(add2(P2[1][k], dup(-ch.y)), add2(L2[1][k], dup(-cl.y)));
-                        dz = add2(add2(P2[2][k], dup(-ch.z)), add2(L2[2][k], dup(-cl.z)));
+                        const float4 r0 = pr[0], r1 = pr[1], r2 = pr[2];
+                        dx = add2(add2(P2[0][k], lo2(r0)), add2(L2[0][k], hi2(r1)));
+                        dy = add2(add2(P2[1][k], hi2(r0)), add2(L2[1][k], lo2(r2)));
+                        dz = add2(add2(P2[2][k], lo2(r1)), add2(L2[2][k], hi2(r2)));
                     };
                     // s = |d|^2, u = d.e0, v = d.e1 of every pair
                     float2 sv[NP], uv[NP], vv[NP];
+#if BEM_KEEP_D
+                    float2 kdx[NP], kdy[NP], kdz[NP];
+#endif
                     {
-                        const float4 f0 = ws.e0[e], f1 = ws.e1[e];
+                        const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
                             diff(k, dx, dy, dz);
+#if BEM_KEEP_D
+                            kdx[k] = dx; kdy[k] = dy; kdz[k] = dz;
+#endif
                             sv[k] = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                            uv[k] = fma2(dx, dup(f0.x), fma2(dy, dup(f0.y), mul2(dz, dup(f0.z))));
-                            vv[k] = fma2(dx, dup(f1.x), fma2(dy, dup(f1.y), mul2(dz, dup(f1.z))));
+                            uv[k] = fma2(dx, lo2(r3), fma2(dy, hi2(r3), mul2(dz, lo2(r4))));
+                            vv[k] = fma2(dx, hi2(r4), fma2(dy, lo2(r5), mul2(dz, hi2(r5))));
                         }
                     }
                     float2 eacc[NP][4];  // this element's sums (started by its first rule pass)
@@ -643,8 +659,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 
                     if (cd >= 1 && cd <= 5) {
                         const int n = expand(band_rule(cd));
-                        if (cd <= kRefineBands) nodes2<NP, WANT_E, true, kRefineBands != 0>(ws.nd[par], n, sv, uv, vv, eacc);
-                        else nodes2<NP, WANT_E, true, false>(ws.nd[par], n, sv, uv, vv, eacc);
+                        nodes2<NP, WANT_E, true>(ws.nd[par], n, sv, uv, vv, eacc);
                         par ^= 1;
                         if (STATS && lane == 0) {
                             atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -679,15 +694,14 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int band = 1; band <= 5; ++band) {
                             if (!(mask & (1u << band))) continue;
                             // points of other bands sit at infinite distance in this pass
-                            constexpr float kInf = kRefineBands ? 3.0e38f : __builtin_huge_valf();
+                            constexpr float kInf = __builtin_huge_valf();
                             float2 sm[NP];
 #pragma unroll
                             for (int k = 0; k < NP; ++k)
                                 sm[k] = make_float2(bq[2 * k] == band ? sv[k].x : kInf,
                                                     bq[2 * k + 1] == band ? sv[k].y : kInf);
                             const int n = expand(band_rule(band));
-                            if (band <= kRefineBands) nodes2<NP, WANT_E, false, kRefineBands != 0>(ws.nd[par], n, sm, uv, vv, eacc);
-                            else nodes2<NP, WANT_E, false, false>(ws.nd[par], n, sm, uv, vv, eacc);
+                            nodes2<NP, WANT_E, false>(ws.nd[par], n, sm, uv, vv, eacc);
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                         }
@@ -706,19 +720,22 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     if constexpr (MODE == 0) {
                         // the element's phi and E = d B + (e0/2) B_alpha' + (e1/2) B_beta'
                         // into the FP32 sums; every kFlush elements move those into FP64
-                        const float4 f0 = ws.e0[e], f1 = ws.e1[e];
-                        const float2 h0x = dup(0.5f * f0.x), h0y = dup(0.5f * f0.y), h0z = dup(0.5f * f0.z);
-                        const float2 h1x = dup(0.5f * f1.x), h1y = dup(0.5f * f1.y), h1z = dup(0.5f * f1.z);
+                        const float4 r6 = pr[6], r7 = pr[7], r8 = pr[8];
+                        const float2 h0x = lo2(r6), h0y = hi2(r6), h0z = lo2(r7);
+                        const float2 h1x = hi2(r7), h1y = lo2(r8), h1z = hi2(r8);
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             acc8[k][0] = add2(acc8[k][0], eacc[k][0]);
                             if (WANT_E) {
                                 float2 dx, dy, dz;
+#if BEM_KEEP_D
+                                dx = kdx[k]; dy = kdy[k]; dz = kdz[k];
+#else
                                 diff(k, dx, dy, dz);
-                                // the element's field first, then one rounding of the running sum
-                                acc8[k][1] = add2(acc8[k][1], fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], mul2(h1x, eacc[k][3]))));
-                                acc8[k][2] = add2(acc8[k][2], fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], mul2(h1y, eacc[k][3]))));
-                                acc8[k][3] = add2(acc8[k][3], fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], mul2(h1z, eacc[k][3]))));
+#endif
+                                acc8[k][1] = fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], fma2(h1x, eacc[k][3], acc8[k][1])));
+                                acc8[k][2] = fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], fma2(h1y, eacc[k][3], acc8[k][2])));
+                                acc8[k][3] = fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], fma2(h1z, eacc[k][3], acc8[k][3])));
                             }
                         }
                         if (((b0 + e) & (kFlush - 1)) == kFlush - 1 || e == nb - 1) {
