@@ -46,9 +46,11 @@
 //    At DR >= 3 the terms of r_i^2 cancel by at most a factor of about 4, so
 //    the split costs about two bits of an FP32 result.  rsqrt and the sums
 //    are FP32: each element's node terms (at most 33) are summed on their
-//    own, eight such element sums are added up, and that sum is flushed into
-//    FP64 accumulators in shared memory.  No FP32 sum runs over more than 33
-//    terms; the FP64 pipe sees two adds per element and point.
+//    own, eight such element sums are added up, and that sum is added into
+//    running sums kept in shared memory as unevaluated FP32 pairs hi + lo
+//    (an exact two-sum: about 48 significant bits), so the FP64 pipe, slow
+//    on this GPU, stays out of the loop.  No plain FP32 sum runs over more
+//    than 33 terms.
 #include <math.h>
 #include <stdio.h>
 
@@ -71,7 +73,7 @@ constexpr int kPtMixed = BEM_MIXED_PT, kPtFp64 = BEM_FP64_PT;
 #define BEM_NODE_UNROLL 4
 #endif
 constexpr int kNodeUnroll = BEM_NODE_UNROLL;
-// mixed path: elements per FP32 running sum before it moves into FP64 (a power of two)
+// mixed path: elements per FP32 sum before it moves into the hi + lo running sums (a power of two)
 #ifndef BEM_FLUSH
 #define BEM_FLUSH 8
 #endif
@@ -216,6 +218,20 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// hi + lo += x exactly up to the rounding of lo (Knuth's two-sum on packed
+// pairs; fma(a, -1, b) is b - a rounded once).  It keeps the running sums
+// of the mixed path on the FP32 pipe: a warp-wide FP64 add occupies this
+// GPU's FP64 pipe for tens of cycles.
+__device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 sm = add2(hi, x);
+    const float2 bv = fma2(hi, m1, sm);  // sm - hi
+    const float2 av = fma2(bv, m1, sm);  // sm - bv
+    const float2 er = add2(fma2(av, m1, hi), fma2(bv, m1, x));
+    hi = sm;
+    lo = add2(lo, er);
+}
+
 // One node of an element at the NP point pairs of a lane, in the frame form:
 // ab = (-2 alpha, -2 alpha, -2 beta, -2 beta), ow = (|o|^2, |o|^2, w q, w q);
 // s, u, v = |d|^2, d.e0, d.e1 per point.  acc[k] = (sum a, sum b,
@@ -278,7 +294,9 @@ struct WarpSmem {
     // -C_hi, -C_lo, e0, e1, e0 / 2, e1 / 2 (nine float4)
     float4 pr[kMixed ? 32 * 9 : 1];
     R4 nd[2][kMixed ? 2 * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: two)
-    double acc64[ACC64 ? PT * 4 * 32 : 1];
+    // mixed evaluation: per point pair, component and lane, the running sum as an
+    // unevaluated FP32 pair hi + lo (hi.x, hi.y, lo.x, lo.y)
+    float4 accdf[ACC64 ? (PT / 2) * 4 * 32 : 1];
 };
 
 template <typename R>
@@ -311,7 +329,7 @@ template <bool F64, int PT, bool WANT_E, int MODE, bool STATS>
 __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK p) {
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
-    constexpr bool ACC64 = !F64 && MODE == 0;  // FP64 accumulators in shared memory
+    constexpr bool ACC64 = !F64 && MODE == 0;  // running sums in shared memory (mixed evaluation)
     using WS = WarpSmem<R, R4, PT, ACC64>;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -433,10 +451,12 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         for (int q = 0; q < PT; ++q) {
             ncnt[q] = 0;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < 4; ++c)
                 if constexpr (F64) acc[q][c] = (R)0;
-                if constexpr (ACC64) ws.acc64[(q * 4 + c) * 32 + lane] = 0.0;
-            }
+        }
+        if constexpr (ACC64) {
+#pragma unroll
+            for (int k = 0; k < NP * 4; ++k) ws.accdf[k * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k)
@@ -719,7 +739,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 
                     if constexpr (MODE == 0) {
                         // the element's phi and E = d B + (e0/2) B_alpha' + (e1/2) B_beta'
-                        // into the FP32 sums; every kFlush elements move those into FP64
+                        // into the FP32 sums; every kFlush elements move those into the hi + lo sums
                         const float4 r6 = pr[6], r7 = pr[7], r8 = pr[8];
                         const float2 h0x = lo2(r6), h0y = hi2(r6), h0z = lo2(r7);
                         const float2 h1x = hi2(r7), h1y = lo2(r8), h1z = hi2(r8);
@@ -743,8 +763,11 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             for (int k = 0; k < NP; ++k)
 #pragma unroll
                                 for (int j = 0; j < 4; ++j) {
-                                    ws.acc64[((2 * k) * 4 + j) * 32 + lane] += (double)acc8[k][j].x;
-                                    ws.acc64[((2 * k + 1) * 4 + j) * 32 + lane] += (double)acc8[k][j].y;
+                                    float4& slot = ws.accdf[(k * 4 + j) * 32 + lane];
+                                    const float4 v = slot;
+                                    float2 hi = make_float2(v.x, v.y), lo = make_float2(v.z, v.w);
+                                    two_sum_add(hi, lo, acc8[k][j]);
+                                    slot = make_float4(hi.x, hi.y, lo.x, lo.y);
                                     acc8[k][j] = make_float2(0.0f, 0.0f);
                                 }
                         }
@@ -768,10 +791,17 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             for (int q = 0; q < PT; ++q) {
                 if (!valid[q]) continue;
                 double4 o;
-                if constexpr (F64) o = make_double4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
-                else
-                    o = make_double4(ws.acc64[(q * 4) * 32 + lane], ws.acc64[(q * 4 + 1) * 32 + lane],
-                                     ws.acc64[(q * 4 + 2) * 32 + lane], ws.acc64[(q * 4 + 3) * 32 + lane]);
+                if constexpr (F64) {
+                    o = make_double4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+                } else {
+                    double c4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 v = ws.accdf[((q >> 1) * 4 + j) * 32 + lane];
+                        c4[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+                    }
+                    o = make_double4(c4[0], c4[1], c4[2], c4[3]);
+                }
                 const size_t slot = (size_t)sidx[q] * p.n_chunks + chunk;
                 p.part[slot] = o;
                 p.near_cnt[slot] = ncnt[q];
