@@ -268,16 +268,36 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
     }
 }
 
-// All n nodes of one rule (two records per node in nd, broadcast reads).
+// All N nodes of one rule (two records per node in nd, broadcast reads),
+// with the trip count known at compile time.
+template <int N, int NP, bool WANT_E, bool INIT>
+__device__ __forceinline__ void nodes2_n(const float4* __restrict__ nd, const float2 (&s)[NP],
+                                         const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
+    if (INIT) node2<NP, WANT_E, true>(nd[0], nd[1], s, u, v, acc);
+#pragma unroll kNodeUnroll
+    for (int i = INIT ? 1 : 0; i < N; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+}
+
+// All n nodes of one rule: the node counts of the paper's rules (App. A, B)
+// get their own compiled loops.
 template <int NP, bool WANT_E, bool INIT>
 __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
                                        const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
+    switch (n) {
+        case 4: nodes2_n<4, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        case 7: nodes2_n<7, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        case 12: nodes2_n<12, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        case 17: nodes2_n<17, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        case 19: nodes2_n<19, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        case 33: nodes2_n<33, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        default: break;
+    }
     int i = 0;
     if (INIT) {  // every rule has at least four nodes
         node2<NP, WANT_E, true>(nd[0], nd[1], s, u, v, acc);
         i = 1;
     }
-#pragma unroll kNodeUnroll
+#pragma unroll 1
     for (; i < n; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
 }
 
