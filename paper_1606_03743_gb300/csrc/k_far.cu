@@ -79,10 +79,6 @@ constexpr int kNodeUnroll = BEM_NODE_UNROLL;
 #endif
 constexpr int kFlush = BEM_FLUSH;
 static_assert((kFlush & (kFlush - 1)) == 0 && kFlush <= 32, "flush interval: a power of two up to 32");
-// mixed path: hold d = P - C through the node loop (1) or form it again for the field rebuild (0)
-#ifndef BEM_KEEP_D
-#define BEM_KEEP_D 0
-#endif
 
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
 constexpr int kWarps = 4;     // warps per CTA
@@ -233,10 +229,11 @@ __device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
 }
 
 // One node of an element at the NP point pairs of a lane, in the frame form:
-// ab = (-2 alpha, -2 alpha, -2 beta, -2 beta), ow = (|o|^2, |o|^2, w q, w q);
-// s, u, v = |d|^2, d.e0, d.e1 per point.  acc[k] = (sum a, sum b,
-// sum b (-2 alpha), sum b (-2 beta)) with a = w q / r, b = a / r^2 (phi only:
-// sum a).  A point that must not take part carries s = +inf: then r^2 = +inf,
+// ab = (-alpha, -alpha, -beta, -beta), ow = (|o|^2, |o|^2, w q, w q);
+// s, u, v = |d|^2, 2 d.e0, 2 d.e1 per point (r^2 = s + |o|^2 - alpha u -
+// beta v).  acc[k] = (sum a, sum b, -sum b alpha, -sum b beta) with
+// a = w q / r, b = a / r^2 (phi only: sum a).  A point that must not take
+// part carries s = +inf: then r^2 = +inf,
 // rsqrt gives +0 and its terms are exact zeros, while the other points'
 // arithmetic is bit-for-bit that of a pass without it.  INIT: the sums start
 // from this term.
@@ -311,8 +308,9 @@ struct WarpSmem {
     R thr[32 * 5];           // squared band limits (tau L)^2
     // mixed: per element, the values each node pass and the field rebuild
     // read, duplicated into (x, x, y, y) pairs for the packed f32x2 arithmetic:
-    // -C_hi, -C_lo, e0, e1, e0 / 2, e1 / 2 (nine float4)
-    float4 pr[kMixed ? 32 * 9 : 1];
+    // -C_hi, -C_lo, e0, e1 (six float4)
+    float4 pr[kMixed ? 32 * 6 : 1];
+
     R4 nd[2][kMixed ? 2 * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: two)
     // mixed evaluation: per point pair, component and lane, the running sum as an
     // unevaluated FP32 pair hi + lo (hi.x, hi.y, lo.x, lo.y)
@@ -516,16 +514,13 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         const float4 a = p.e0f[j], b = p.e1f[j];
                         ws.e0[lane] = R4{a.x, a.y, a.z, (float)(sg * area)};
                         ws.e1[lane] = R4{b.x, b.y, b.z, __int_as_float(ty)};
-                        float4* pr = ws.pr + lane * 9;
+                        float4* pr = ws.pr + lane * 6;
                         pr[0] = make_float4(-c.x, -c.x, -c.y, -c.y);
                         pr[1] = make_float4(-c.z, -c.z, -cl.x, -cl.x);
                         pr[2] = make_float4(-cl.y, -cl.y, -cl.z, -cl.z);
                         pr[3] = make_float4(a.x, a.x, a.y, a.y);
                         pr[4] = make_float4(a.z, a.z, b.x, b.x);
                         pr[5] = make_float4(b.y, b.y, b.z, b.z);
-                        pr[6] = make_float4(0.5f * a.x, 0.5f * a.x, 0.5f * a.y, 0.5f * a.y);
-                        pr[7] = make_float4(0.5f * a.z, 0.5f * a.z, 0.5f * b.x, 0.5f * b.x);
-                        pr[8] = make_float4(0.5f * b.y, 0.5f * b.y, 0.5f * b.z, 0.5f * b.z);
                         const float L = cl.w;
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
@@ -650,8 +645,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 } else {
                     // ---------------- mixed path (frame form, point pairs)
                     // d = (P_hi - C_hi) + (P_lo - C_lo) of pair k, the first difference exact
-                    // (formed again where needed rather than held through the node loop)
-                    const float4* pr = ws.pr + e * 9;
+                    const float4* pr = ws.pr + e * 6;
                     auto lo2 = [](float4 v) { return make_float2(v.x, v.y); };
                     auto hi2 = [](float4 v) { return make_float2(v.z, v.w); };
                     auto diff = [&](int k, float2& dx, float2& dy, float2& dz) {
@@ -662,21 +656,17 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     };
                     // s = |d|^2, u = d.e0, v = d.e1 of every pair
                     float2 sv[NP], uv[NP], vv[NP];
-#if BEM_KEEP_D
-                    float2 kdx[NP], kdy[NP], kdz[NP];
-#endif
                     {
                         const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
                             diff(k, dx, dy, dz);
-#if BEM_KEEP_D
-                            kdx[k] = dx; kdy[k] = dy; kdz[k] = dz;
-#endif
                             sv[k] = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                            uv[k] = fma2(dx, lo2(r3), fma2(dy, hi2(r3), mul2(dz, lo2(r4))));
-                            vv[k] = fma2(dx, hi2(r4), fma2(dy, lo2(r5), mul2(dz, hi2(r5))));
+                            const float2 u = fma2(dx, lo2(r3), fma2(dy, hi2(r3), mul2(dz, lo2(r4))));
+                            const float2 v = fma2(dx, hi2(r4), fma2(dy, lo2(r5), mul2(dz, hi2(r5))));
+                            uv[k] = add2(u, u);  // 2 d.e0, 2 d.e1 (exact doublings)
+                            vv[k] = add2(v, v);
                         }
                     }
                     float2 eacc[NP][4];  // this element's sums (started by its first rule pass)
@@ -689,7 +679,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y),
                                         oz = fmaf(al, f0.z, be * f1.z);
                             const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
-                            const float am = -2.0f * al, bm = -2.0f * be, wq = rs.w[st + i] * f0.w;
+                            const float am = -al, bm = -be, wq = rs.w[st + i] * f0.w;
                             ws.nd[par][2 * i] = make_float4(am, am, bm, bm);
                             ws.nd[par][2 * i + 1] = make_float4(oo, oo, wq, wq);
                         }
@@ -758,21 +748,17 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     }
 
                     if constexpr (MODE == 0) {
-                        // the element's phi and E = d B + (e0/2) B_alpha' + (e1/2) B_beta'
+                        // the element's phi and E = d B - e0 sum b alpha - e1 sum b beta
                         // into the FP32 sums; every kFlush elements move those into the hi + lo sums
-                        const float4 r6 = pr[6], r7 = pr[7], r8 = pr[8];
-                        const float2 h0x = lo2(r6), h0y = hi2(r6), h0z = lo2(r7);
-                        const float2 h1x = hi2(r7), h1y = lo2(r8), h1z = hi2(r8);
+                        const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
+                        const float2 h0x = lo2(r3), h0y = hi2(r3), h0z = lo2(r4);
+                        const float2 h1x = hi2(r4), h1y = lo2(r5), h1z = hi2(r5);
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             acc8[k][0] = add2(acc8[k][0], eacc[k][0]);
                             if (WANT_E) {
-                                float2 dx, dy, dz;
-#if BEM_KEEP_D
-                                dx = kdx[k]; dy = kdy[k]; dz = kdz[k];
-#else
+                                float2 dx, dy, dz;  // formed again rather than held through the node loop
                                 diff(k, dx, dy, dz);
-#endif
                                 acc8[k][1] = fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], fma2(h1x, eacc[k][3], acc8[k][1])));
                                 acc8[k][2] = fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], fma2(h1y, eacc[k][3], acc8[k][2])));
                                 acc8[k][3] = fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], fma2(h1z, eacc[k][3], acc8[k][3])));
