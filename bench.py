@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (latency) measurement")
     ap.add_argument("--no-assembly", action="store_true", help="skip the collocation-assembly measurement")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--no-large", action="store_true", help="skip the 500k-element x 4M-point mixed vs FP64 run")
+    ap.add_argument("--large-points", type=int, default=4_000_000)
+    ap.add_argument("--large-fp64-points", type=int, default=32768)
+    ap.add_argument("--large-oracle-points", type=int, default=2048)
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -291,6 +295,8 @@ def main():
         line["latency"] = {"p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "workload": line["serving"]["workload"]}
     if rank == 0 and world == 1 and not a.no_assembly:
         line["assembly"] = assembly(a, bem, torch)
+    if rank == 0 and world == 1 and not a.no_large:
+        line["large_mixed_vs_fp64"] = large_mixed_vs_fp64(a, bem, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()
@@ -356,7 +362,6 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     t0c = time.perf_counter()
     rphi, rE, mdr, esum = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[:ns], nthreads=nt,
                                             return_min_dr=True, return_esum=True)
-    kappa = esum / np.linalg.norm(rE, axis=1)
     cpu_s = time.perf_counter() - t0c
     out["cpu_baseline"] = {"value": ns * mesh.n / cpu_s, "unit": UNIT, "cores": nt, "kind": "oracle",
                            "sample": f"first {ns} of the {a.points} points x all {mesh.n} elements ({cpu_s:.1f} s)"}
@@ -366,28 +371,91 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     g64E = f64E.cpu().numpy()
     k = min(ns, n64)
 
-    def errs(p, e, rp, re, sel):
+    out["accuracy_vs_oracle"] = accuracy_report(gphi, gE, g64phi[:k], g64E[:k], rphi, rE, mdr, esum)
+    out["accuracy_vs_oracle"]["run_precision"] = a.precision
+    out["accuracy_vs_oracle"]["points"] = ns
+    m64.close()
+    return out
+
+
+def accuracy_report(gphi, gE, g64phi, g64E, rphi, rE, mdr, esum):
+    """Relative errors of phi, of the vector E and of |E| against the oracle,
+    grouped by the distance-ratio band of each point's nearest element
+    (triangle limits of the paper's Sec. 4 reading: near < 3 <= 33-point < 12
+    <= 19-point < 30 <= 12-point < 120 <= 7-point < 2250 <= 4-point), plus the
+    points outside the near band whose field does not cancel by more than
+    100 (kappa = sum_j |E_j| / |E|)."""
+    kappa = esum / np.linalg.norm(rE, axis=1)
+
+    def errs(p, e, sel):
         n = len(p)
         sel = sel[:n]
-        ep = np.abs(p - rp[:n]) / np.abs(rp[:n])
-        dE = np.linalg.norm(e - re[:n], axis=1)
-        eE = dE / np.linalg.norm(re[:n], axis=1)
+        ep = np.abs(p - rphi[:n]) / np.abs(rphi[:n])
+        nE = np.linalg.norm(rE[:n], axis=1)
+        dE = np.linalg.norm(e - rE[:n], axis=1)
+        eE = dE / nE
+        eA = np.abs(np.linalg.norm(e, axis=1) - nE) / nE
         eEc = dE / esum[:n]  # |dE| / sum_j |E_j|: error relative to the size of the terms
-        return {"max_rel_phi": float(ep[sel].max(initial=0)), "max_rel_E": float(eE[sel].max(initial=0)),
-                "mean_rel_phi": float(ep[sel].mean()) if sel.any() else 0.0,
-                "mean_rel_E": float(eE[sel].mean()) if sel.any() else 0.0,
-                "max_E_over_sum_abs_Ej": float(eEc[sel].max(initial=0)), "n": int(sel.sum())}
+        if not sel.any():
+            return {"n": 0}
+        return {"max_rel_phi": float(ep[sel].max()), "max_rel_E": float(eE[sel].max()),
+                "max_rel_absE": float(eA[sel].max()), "mean_rel_phi": float(ep[sel].mean()),
+                "mean_rel_E": float(eE[sel].mean()), "max_E_over_sum_abs_Ej": float(eEc[sel].max()),
+                "n": int(sel.sum())}
 
-    bands = {"min_DR>=3,kappa<=100": (mdr >= 3) & (kappa <= 100), "min_DR>=3": mdr >= 3, "min_DR<3": mdr < 3}
-    out["accuracy_vs_oracle"] = {
-        "run_precision": a.precision,
-        "bands": {b: errs(gphi, gE, rphi, rE, s) for b, s in bands.items()},
-        "fp64_path": {b: errs(g64phi[:k], g64E[:k], rphi, rE, s) for b, s in bands.items()},
-        "kappa": {"definition": "sum_j |E_j| / |E| (oracle)", "median": float(np.median(kappa)),
-                  "p99": float(np.percentile(kappa, 99)), "max": float(kappa.max()),
-                  "frac_above_100": float((kappa > 100).mean())},
-        "points": ns}
-    m64.close()
+    edges = [0, 3, 12, 30, 120, 2250, np.inf]
+    names = ["near (<3)", "33-pt [3,12)", "19-pt [12,30)", "12-pt [30,120)", "7-pt [120,2250)", "4-pt (>=2250)"]
+    groups = {"min_DR>=3,kappa<=100": (mdr >= 3) & (kappa <= 100), "min_DR>=3": mdr >= 3}
+    for lo, hi, nm in zip(edges[:-1], edges[1:], names):
+        groups["min_DR " + nm] = (mdr >= lo) & (mdr < hi)
+    return {"bands": {b: errs(gphi, gE, s) for b, s in groups.items()},
+            "fp64_path": {b: errs(g64phi, g64E, s) for b, s in groups.items()},
+            "kappa": {"definition": "sum_j |E_j| / |E| (oracle)", "median": float(np.median(kappa)),
+                      "p99": float(np.percentile(kappa, 99)), "max": float(kappa.max()),
+                      "frac_above_100": float((kappa > 100).mean())},
+            "band_of_point": "band of the smallest distance ratio D/L over all elements"}
+
+
+def large_mixed_vs_fp64(a, bem, torch):
+    """500000-element coaxial mesh and 4000000 field points: the mixed path
+    over all points, the plain FP64 kernel on a subset, both against the
+    oracle on a bounded sample, errors per distance-ratio band."""
+    import oracle
+    oracle.build()
+    mesh = synth.coax_mesh_large(seed=4)
+    pts = synth.coax_points(seed=4, n=a.large_points)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = {"workload": (f"{mesh.n} elements (coaxial, 400x500 rectangles per cylinder + 2 x 50000 cap triangles), "
+                        f"{a.large_points} field points")}
+    res = {}
+    for prec, name, n in ((bem.MIXED, "mixed", a.large_points), (bem.FP64, "fp64", a.large_fp64_points)):
+        m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                     torch.from_numpy(mesh.sigma).to(dev), precision=prec)
+        p_d = torch.from_numpy(pts[:n]).to(dev)
+        phi = torch.empty(n, dtype=torch.float64, device=dev)
+        E = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        bem.bem_eval(m.handle, p_d, phi, E, stream=stream.cuda_stream)  # sizes the workspace
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        bem.bem_eval(m.handle, p_d, phi, E, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        out[name] = {"value": n * mesh.n / (ms * 1e-3), "unit": UNIT, "n_points": n, "ms": ms}
+        res[name] = (phi[: a.large_oracle_points].cpu().numpy(), E[: a.large_oracle_points].cpu().numpy())
+        m.close()
+        del p_d, phi, E
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    ns = a.large_oracle_points
+    t0c = time.perf_counter()
+    rphi, rE, mdr, esum = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[:ns],
+                                            nthreads=oracle.max_threads(), return_min_dr=True, return_esum=True)
+    out["oracle_s"] = time.perf_counter() - t0c
+    out["accuracy_vs_oracle"] = accuracy_report(res["mixed"][0], res["mixed"][1], res["fp64"][0], res["fp64"][1],
+                                                rphi, rE, mdr, esum)
+    out["accuracy_vs_oracle"]["points"] = ns
     return out
 
 
