@@ -45,6 +45,7 @@ extern "C" {
 #define BEM_ERR_CUDA -4     /* a CUDA runtime call or kernel launch failed */
 #define BEM_ERR_TIMEOUT -5  /* a bounded wait ran out (serving loop) */
 #define BEM_ERR_NOT_FOUND -6 /* unknown serving ticket */
+#define BEM_ERR_NOT_CONVERGED -7 /* bem_solve stopped at its iteration limit above the tolerance */
 
 /* element types */
 #define BEM_TRIANGLE 0
@@ -142,6 +143,41 @@ int bem_assemble(bem_mesh* mesh, const double* colloc, int64_t m, double* A, voi
  *   x [n_el], y [n_el]
  */
 int bem_matvec(bem_mesh* mesh, const double* x, double* y, void* stream);
+
+/*
+ * bem_solve -- charge densities for prescribed potentials: solves
+ *   sum_j A[i][j] sigma[j] = rhs[i]   (i, j = 0 .. n_el - 1)
+ * with A the collocation matrix at the element centroids (bem_matvec): the
+ * linear system for the charge densities of the BEM electrode problem,
+ * solved before phi and E are evaluated from them (Sec. 1 names direct and
+ * iterative solvers; the field code of Sec. 5 keeps its matrices unstored
+ * and iterates).  This is restarted GMRES with a Jacobi (diagonal) right
+ * preconditioner, every product a bem_matvec and every vector operation a
+ * kernel of this library, so the matrix is never stored.  Each product has
+ * the mesh's precision: an FP64 mesh reaches relative residuals near 1e-14,
+ * a mixed mesh near 1e-7.
+ *   rhs   [n_el]  potentials at the centroids (V), host or device
+ *   sigma [n_el]  out: charge densities (C/m^2); in: the initial guess when
+ *                 opt->flags has BEM_SOLVE_X0 (else the solve starts from 0)
+ *   opt           may be NULL: restart 50, max_iter 1000 products, tol 1e-12
+ *                 (FP64 mesh) or 1e-6 (mixed mesh)
+ *   info  [3]     may be NULL: products used, final relative residual
+ *                 |rhs - A sigma| / |rhs| (recomputed, not the GMRES estimate),
+ *                 1 if converged else 0
+ * Returns BEM_ERR_NOT_CONVERGED (sigma holds the last iterate) if the
+ * residual is above tol after max_iter products.  The mesh's own sigma is
+ * not changed (bem_set_sigma sets it).  Deterministic: the same inputs give
+ * the same bits.
+ */
+#define BEM_SOLVE_X0 1
+typedef struct {
+    int32_t restart;  /* Krylov dimension per cycle (0: 50, at most 200) */
+    int32_t max_iter; /* matrix-vector products in total (0: 1000) */
+    double tol;       /* relative residual to reach (0: the default above) */
+    int32_t flags;    /* BEM_SOLVE_X0 */
+} bem_solve_options;
+int bem_solve(bem_mesh* mesh, const double* rhs, double* sigma, const bem_solve_options* opt, double* info,
+              void* stream);
 
 /* Element centroids Q_cen (Sec. 2), n_el x 3, written to a host or device array. */
 int bem_centroids(bem_mesh* mesh, double* out, void* stream);

@@ -23,12 +23,13 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "SOLVE_X0", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
 STATUS = {0: "BEM_OK", -1: "BEM_ERR_INVALID", -2: "BEM_ERR_OOM", -3: "BEM_ERR_CAPACITY", -4: "BEM_ERR_CUDA",
-          -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOT_FOUND"}
+          -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOT_FOUND", -7: "BEM_ERR_NOT_CONVERGED"}
+SOLVE_X0 = 1
 
 
 class BemError(RuntimeError):
@@ -40,6 +41,10 @@ class BemError(RuntimeError):
 class bem_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("flags", C.c_int32), ("limits", C.POINTER(C.c_double)),
                 ("eps0", C.c_double), ("device_mem_budget", C.c_size_t)]
+
+
+class bem_solve_options(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double), ("flags", C.c_int32)]
 
 
 class bem_server_options(C.Structure):
@@ -89,6 +94,8 @@ def load_library(build_if_missing: bool = True):
     lib.bem_cancel.argtypes = [vp, C.c_uint64]
     lib.bem_server_pause.argtypes = [vp, C.c_int32]
     lib.bem_server_stats.argtypes = [vp, C.c_int32, d]
+    lib.bem_solve.argtypes = [vp, vp, vp, C.POINTER(bem_solve_options), d, vp]
+    lib.bem_solve.restype = C.c_int
     for name in ("bem_server_create", "bem_submit", "bem_poll", "bem_wait", "bem_cancel", "bem_server_pause",
                  "bem_server_stats"):
         getattr(lib, name).restype = C.c_int
@@ -238,6 +245,26 @@ def bem_matvec(mesh: int, x, y, stream=None) -> None:
     _check(load_library().bem_matvec(mesh, xp, _ptr(y), _stream(stream)))
 
 
+def bem_solve(mesh: int, rhs, sigma, restart: int = 0, max_iter: int = 0, tol: float = 0.0, x0: bool = False,
+              stream=None) -> dict:
+    """Charge densities sigma with A sigma = rhs at the centroids (restarted,
+    Jacobi-preconditioned GMRES on bem_matvec).  sigma is written in place
+    (and read as the initial guess when x0).  Returns {products, residual,
+    converged}; raises BemError (BEM_ERR_NOT_CONVERGED included) on failure."""
+    n = bem_num_elements(mesh)
+    rr, rp = _prep(rhs, np.float64, (n,))
+    opt = bem_solve_options(restart, max_iter, tol, SOLVE_X0 if x0 else 0)
+    info = np.zeros(3)
+    rc = load_library().bem_solve(mesh, rp, _ptr(sigma), C.byref(opt), info.ctypes.data_as(C.POINTER(C.c_double)),
+                                  _stream(stream))
+    out = {"products": int(info[0]), "residual": float(info[1]), "converged": bool(info[2])}
+    if rc < 0:
+        err = BemError(rc, bem_last_error())
+        err.info = out
+        raise err
+    return out
+
+
 def bem_centroids(mesh: int, out, stream=None) -> None:
     _check(load_library().bem_centroids(mesh, _ptr(out), _stream(stream)))
 
@@ -322,6 +349,15 @@ class Mesh:
 
     def set_sigma(self, sigma, stream=None):
         bem_set_sigma(self._h, sigma, stream)
+
+    def solve(self, rhs, x0=None, restart: int = 0, max_iter: int = 0, tol: float = 0.0, stream=None):
+        """(sigma, info) with A sigma = rhs at the centroids (bem_solve); sigma
+        is the same array kind as rhs."""
+        sigma = _empty_like_kind(rhs, (self.n,))
+        if x0 is not None:
+            sigma[:] = x0
+        info = bem_solve(self._h, rhs, sigma, restart, max_iter, tol, x0 is not None, stream)
+        return sigma, info
 
     def centroids(self, like=None, stream=None):
         out = _empty_like_kind(like if like is not None else np.zeros(0), (self.n, 3))

@@ -143,6 +143,9 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
                      unsigned long long n_near, cudaStream_t s);
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int out_stride4,
                     cudaStream_t s, const int* n_dev = nullptr);
+// kc x potential of each element at its own centroid (sigma = 1): the diagonal of the
+// collocation matrix at the centroids (k_near.cu)
+int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s);
 int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double* A, unsigned long long n_near,
                          cudaStream_t s);
 

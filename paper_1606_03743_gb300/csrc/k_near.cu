@@ -167,7 +167,28 @@ __global__ void k_near_assemble(const int4* __restrict__ rec, const unsigned lon
     }
 }
 
+// Self potential of each element at its own centroid (unit sigma), times kc:
+// the diagonal of the collocation matrix at the centroids.
+__global__ void k_self_potential(int n, const int* __restrict__ type, const double* __restrict__ verts,
+                                 const double* __restrict__ cen, double kc, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double f[4];
+    polygon_field(type[j] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)j,
+                  D3{cen[3 * j], cen[3 * j + 1], cen[3 * j + 2]}, f);
+    out[j] = kc * f[0];
+}
+
 }  // namespace
+
+int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s) {
+    const int n = m->d.n;
+    if (n == 0) return BEM_OK;
+    k_self_potential<<<(n + 255) / 256, 256, 0, s>>>(n, m->d.type, m->d.verts, m->d.cen, m->kc, out);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
 
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
                      unsigned long long /*n_near_hint*/, cudaStream_t s) {
