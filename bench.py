@@ -532,7 +532,7 @@ def assembly(a, bem, torch):
     col = synth.collocation_points(mesh)
     dev = torch.device("cuda", torch.cuda.current_device())
     out = {"workload": f"{mesh.n} elements (18000-triangle geodesic sphere + 2000-rectangle cylinder), "
-                       f"{mesh.n} x {mesh.n} FP64 matrix"}
+                       f"{mesh.n} x {mesh.n} FP64 matrix; solve with the sphere at 1 V, the cylinder at 0 V"}
     c_d = torch.from_numpy(col).to(dev)
     A = torch.empty((mesh.n, mesh.n), dtype=torch.float64, device=dev)
     x = torch.from_numpy(mesh.sigma).to(dev)
@@ -555,6 +555,23 @@ def assembly(a, bem, torch):
         out[name] = {"assemble_ms": ta * 1e3, "matrix_write_GBps": nbytes / ta / 1e9,
                      "entries_per_s": mesh.n * mesh.n / ta, "matvec_ms": tm * 1e3,
                      "matvec_pairs_per_s": mesh.n * mesh.n / tm}
+        # the electrode problem: sphere (triangles) at 1 V, inner cylinder at 0 V
+        rhs = torch.from_numpy(np.where(mesh.types == 0, 1.0, 0.0)).to(dev)
+        sig = torch.empty(mesh.n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = bem.bem_solve(m.handle, rhs, sig)
+        torch.cuda.synchronize()
+        out[name]["solve"] = {"ms": (time.perf_counter() - t0) * 1e3, "products": info["products"],
+                              "relative_residual": info["residual"], "converged": info["converged"],
+                              "method": "restarted GMRES(50), Jacobi right preconditioner, matrix-free products"}
+        if prec == bem.FP64:
+            t0 = time.perf_counter()
+            info = bem.bem_solve(m.handle, rhs, sig, refine=True)
+            torch.cuda.synchronize()
+            out[name]["solve_refined"] = {"ms": (time.perf_counter() - t0) * 1e3, "products": info["products"],
+                                          "relative_residual": info["residual"], "converged": info["converged"],
+                                          "method": "FP64 residuals, GMRES on mixed-precision products to 1e-6"}
         m.close()
     del A
     return out

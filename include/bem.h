@@ -164,17 +164,23 @@ int bem_matvec(bem_mesh* mesh, const double* x, double* y, void* stream);
  *   info  [3]     may be NULL: products used, final relative residual
  *                 |rhs - A sigma| / |rhs| (recomputed, not the GMRES estimate),
  *                 1 if converged else 0
+ * With BEM_SOLVE_REFINE on an FP64 mesh the solve refines iteratively: FP64
+ * residuals b - A sigma, corrections from GMRES on mixed-precision products
+ * (to 1e-6), sigma += correction, until the FP64 residual meets tol -- the
+ * same answer for a fraction of the FP64 products (this GPU's FP64 rate is
+ * about 1/74 of its FP32 rate); info[0] then counts both kinds of product.
  * Returns BEM_ERR_NOT_CONVERGED (sigma holds the last iterate) if the
  * residual is above tol after max_iter products.  The mesh's own sigma is
  * not changed (bem_set_sigma sets it).  Deterministic: the same inputs give
  * the same bits.
  */
 #define BEM_SOLVE_X0 1
+#define BEM_SOLVE_REFINE 2
 typedef struct {
     int32_t restart;  /* Krylov dimension per cycle (0: 50, at most 200) */
     int32_t max_iter; /* matrix-vector products in total (0: 1000) */
     double tol;       /* relative residual to reach (0: the default above) */
-    int32_t flags;    /* BEM_SOLVE_X0 */
+    int32_t flags;    /* BEM_SOLVE_X0 | BEM_SOLVE_REFINE */
 } bem_solve_options;
 int bem_solve(bem_mesh* mesh, const double* rhs, double* sigma, const bem_solve_options* opt, double* info,
               void* stream);

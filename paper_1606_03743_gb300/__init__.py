@@ -23,13 +23,13 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "SOLVE_X0", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "SOLVE_X0", "SOLVE_REFINE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
 STATUS = {0: "BEM_OK", -1: "BEM_ERR_INVALID", -2: "BEM_ERR_OOM", -3: "BEM_ERR_CAPACITY", -4: "BEM_ERR_CUDA",
           -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOT_FOUND", -7: "BEM_ERR_NOT_CONVERGED"}
-SOLVE_X0 = 1
+SOLVE_X0, SOLVE_REFINE = 1, 2
 
 
 class BemError(RuntimeError):
@@ -246,14 +246,15 @@ def bem_matvec(mesh: int, x, y, stream=None) -> None:
 
 
 def bem_solve(mesh: int, rhs, sigma, restart: int = 0, max_iter: int = 0, tol: float = 0.0, x0: bool = False,
-              stream=None) -> dict:
+              refine: bool = False, stream=None) -> dict:
     """Charge densities sigma with A sigma = rhs at the centroids (restarted,
-    Jacobi-preconditioned GMRES on bem_matvec).  sigma is written in place
+    Jacobi-preconditioned GMRES on bem_matvec; refine: mixed-precision inner
+    solves with FP64 residuals on an FP64 mesh).  sigma is written in place
     (and read as the initial guess when x0).  Returns {products, residual,
     converged}; raises BemError (BEM_ERR_NOT_CONVERGED included) on failure."""
     n = bem_num_elements(mesh)
     rr, rp = _prep(rhs, np.float64, (n,))
-    opt = bem_solve_options(restart, max_iter, tol, SOLVE_X0 if x0 else 0)
+    opt = bem_solve_options(restart, max_iter, tol, (SOLVE_X0 if x0 else 0) | (SOLVE_REFINE if refine else 0))
     info = np.zeros(3)
     rc = load_library().bem_solve(mesh, rp, _ptr(sigma), C.byref(opt), info.ctypes.data_as(C.POINTER(C.c_double)),
                                   _stream(stream))
@@ -350,13 +351,14 @@ class Mesh:
     def set_sigma(self, sigma, stream=None):
         bem_set_sigma(self._h, sigma, stream)
 
-    def solve(self, rhs, x0=None, restart: int = 0, max_iter: int = 0, tol: float = 0.0, stream=None):
+    def solve(self, rhs, x0=None, restart: int = 0, max_iter: int = 0, tol: float = 0.0, refine: bool = False,
+              stream=None):
         """(sigma, info) with A sigma = rhs at the centroids (bem_solve); sigma
         is the same array kind as rhs."""
         sigma = _empty_like_kind(rhs, (self.n,))
         if x0 is not None:
             sigma[:] = x0
-        info = bem_solve(self._h, rhs, sigma, restart, max_iter, tol, x0 is not None, stream)
+        info = bem_solve(self._h, rhs, sigma, restart, max_iter, tol, x0 is not None, refine, stream)
         return sigma, info
 
     def centroids(self, like=None, stream=None):

@@ -40,6 +40,18 @@ def test_fp64_solve_matches_direct_solve(bem, problem):
     assert np.linalg.norm(A @ sigma - rhs) / np.linalg.norm(rhs) <= 1e-11
 
 
+def test_refined_solve_matches_direct_solve(bem, problem):
+    """Mixed-precision inner solves with FP64 residuals reach the FP64 answer."""
+    mesh, A, rhs, ref = problem
+    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=bem.FP64) as m:
+        sigma, info = m.solve(rhs, refine=True)
+        plain, pinfo = m.solve(rhs)
+    assert info["converged"] and info["residual"] <= 1e-12
+    assert np.abs(sigma - ref).max() / np.abs(ref).max() <= 1e-10
+    assert np.linalg.norm(A @ sigma - rhs) / np.linalg.norm(rhs) <= 1e-11
+    assert np.abs(sigma - plain).max() / np.abs(ref).max() <= 1e-10
+
+
 def test_mixed_solve_reaches_its_tolerance(bem, problem):
     mesh, A, rhs, ref = problem
     with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=bem.MIXED) as m:
