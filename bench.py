@@ -295,6 +295,8 @@ def main():
         line["latency"] = {"p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "workload": line["serving"]["workload"]}
     if rank == 0 and world == 1 and not a.no_assembly:
         line["assembly"] = assembly(a, bem, torch)
+    if rank == 0 and world == 1 and not a.no_extras:
+        line["node_table_ablation"] = node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_avg, ops)
     if rank == 0 and world == 1 and not a.no_large:
         line["large_mixed_vs_fp64"] = large_mixed_vs_fp64(a, bem, torch)
     if rank == 0:
@@ -375,6 +377,36 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     out["accuracy_vs_oracle"]["run_precision"] = a.precision
     out["accuracy_vs_oracle"]["points"] = ns
     m64.close()
+    return out
+
+
+def node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_ms_fly, ops):
+    """The same workload with the nodes precomputed per element (the paper's
+    Sec. 6 / Table 4 comparison) against the on-the-fly kernel timed above."""
+    dev = p_d.device
+    m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                 torch.from_numpy(mesh.sigma).to(dev), precision=bem.MIXED, node_table=True)
+    phi2 = torch.empty_like(phi)
+    E2 = torch.empty_like(E)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    bem.bem_eval(m.handle, p_d, phi2, E2, stream=stream.cuda_stream)
+    m.set_timing(True)
+    far = []
+    for _ in range(3):
+        flush.zero_()
+        bem.bem_eval(m.handle, p_d, phi2, E2, stream=stream.cuda_stream)
+        far.append(float(m.last_times()[1]))
+    m.set_timing(False)
+    torch.cuda.synchronize()
+    d_phi = ((phi2 - phi).abs() / phi.abs()).max().item()
+    d_E = ((E2 - E).norm(dim=1) / E.norm(dim=1)).max().item()
+    ms = statistics.mean(far)
+    peak = SM_COUNT * FP32_LANES * 2070e6 / 1e12
+    out = {"far_kernel_ms_on_the_fly": far_ms_fly, "far_kernel_ms_node_table": ms,
+           "frac_node_table": ops / (ms * 1e-3) / 1e12 / peak,
+           "table_bytes": int(mesh.n * 75 * 32),
+           "max_rel_diff_vs_on_the_fly": {"phi": d_phi, "E": d_E}}
+    m.close()
     return out
 
 

@@ -53,16 +53,27 @@ extern "C" {
 
 /* arithmetic of the far-field cubature */
 #define BEM_FP64 0  /* double precision throughout (the paper's arithmetic, Sec. 6) */
-#define BEM_MIXED 1 /* FP32 point-charge sums with split-float (hi/lo) centroid
-                       differences, flushed into FP64 accumulators every tile of
-                       elements; near field and final sums in FP64 */
+#define BEM_MIXED 1 /* FP32 point-charge sums with split-float (hi/lo) point-
+                       centroid differences, running sums as FP32 hi + lo pairs;
+                       near field and final sums in FP64 */
+
+/* bem_options.flags: precomputed node records (mixed meshes only).  The
+ * paper compares Gaussian points precomputed for all elements with points
+ * computed on the fly (Sec. 6, Table 4).  With this flag bem_create stores,
+ * for every element, the node records of all five rules of its type (2400
+ * bytes per element, outside the scratch budget), and the far-field kernel
+ * streams them into its node buffers with asynchronous copies, one element
+ * ahead, instead of computing them per (warp, element).  Results agree with
+ * the on-the-fly path to FP32 rounding (the charge scales the element sums
+ * instead of each node's weight). */
+#define BEM_FLAG_NODE_TABLE 1
 
 typedef struct bem_mesh bem_mesh;
 
 /* Options of bem_create (all fields: 0 / NULL = default). */
 typedef struct {
     int32_t precision;        /* BEM_FP64 (default) or BEM_MIXED */
-    int32_t flags;            /* reserved, must be 0 */
+    int32_t flags;            /* 0 or BEM_FLAG_NODE_TABLE */
     const double* limits;     /* NULL or 10 host doubles: for triangles then
                                  rectangles, the 5 ascending DR limits
                                  [near, 33-pt, 19|17-pt, 12-pt, 7-pt] of the

@@ -23,13 +23,14 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "SOLVE_X0", "SOLVE_REFINE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
 STATUS = {0: "BEM_OK", -1: "BEM_ERR_INVALID", -2: "BEM_ERR_OOM", -3: "BEM_ERR_CAPACITY", -4: "BEM_ERR_CUDA",
           -5: "BEM_ERR_TIMEOUT", -6: "BEM_ERR_NOT_FOUND", -7: "BEM_ERR_NOT_CONVERGED"}
 SOLVE_X0, SOLVE_REFINE = 1, 2
+FLAG_NODE_TABLE = 1
 
 
 class BemError(RuntimeError):
@@ -180,7 +181,7 @@ def bem_rule(type_: int, r: int) -> np.ndarray:
 
 
 def bem_create(types, verts, sigma, precision: int = FP64, limits=None, eps0: float = 0.0,
-               device_mem_budget: int = 0, stream=None) -> int:
+               device_mem_budget: int = 0, stream=None, flags: int = 0) -> int:
     lib = load_library()
     t, tp = _prep(types, np.int32)
     n = int(t.shape[0])
@@ -188,7 +189,7 @@ def bem_create(types, verts, sigma, precision: int = FP64, limits=None, eps0: fl
     s, sp = _prep(sigma, np.float64, (n,))
     opt = bem_options()
     opt.precision = int(precision)
-    opt.flags = 0
+    opt.flags = int(flags)
     lim_keep = None
     if limits is not None:
         lim_keep = np.ascontiguousarray(np.asarray(limits, np.float64).reshape(10))
@@ -303,8 +304,9 @@ class Mesh:
     arrays or torch tensors; precision FP64 or MIXED (see include/bem.h)."""
 
     def __init__(self, types, verts, sigma, precision: int = FP64, limits=None, eps0: float = 0.0,
-                 device_mem_budget: int = 0, stream=None):
-        self._h = bem_create(types, verts, sigma, precision, limits, eps0, device_mem_budget, stream)
+                 device_mem_budget: int = 0, stream=None, node_table: bool = False):
+        self._h = bem_create(types, verts, sigma, precision, limits, eps0, device_mem_budget, stream,
+                             FLAG_NODE_TABLE if node_table else 0)
         self.n = bem_num_elements(self._h)
         self.precision = precision
 

@@ -147,6 +147,7 @@ void free_mesh(bem_mesh* m) {
     cudaFree(d.clo);
     cudaFree(d.e0);
     cudaFree(d.e1);
+    cudaFree(d.nodes);
     cudaFree(d.cen);
     cudaFree(d.fr);
     cudaFree(d.geo);
@@ -284,8 +285,8 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
         delete m;
         return BEM_ERR_INVALID;
     }
-    if (opt && opt->flags != 0) {
-        set_error("bem_create: flags must be 0");
+    if (opt && (opt->flags & ~BEM_FLAG_NODE_TABLE)) {
+        set_error("bem_create: unknown flags 0x%x", (unsigned)opt->flags);
         delete m;
         return BEM_ERR_INVALID;
     }
@@ -368,6 +369,21 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     if (rc) {
         free_mesh(m);
         return rc;
+    }
+    if (opt && (opt->flags & BEM_FLAG_NODE_TABLE) && m->precision == kMixed) {
+        cudaError_t e = cudaMalloc((void**)&d.nodes, sizeof(float4) * 2 * kTableSlots * nn);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("bem_create: cudaMalloc of the node table (%zu bytes) failed: %s",
+                      sizeof(float4) * 2 * kTableSlots * nn, cudaGetErrorString(e));
+            rc = BEM_ERR_OOM;
+        } else {
+            rc = launch_fill_nodes(m, s);
+        }
+        if (rc) {
+            free_mesh(m);
+            return rc;
+        }
     }
     if ((rc = ensure_near(m, std::max<size_t>(size_t(1) << 20, 4 * nn)))) {
         free_mesh(m);

@@ -29,6 +29,8 @@ __host__ __device__ inline int band_rule(int band) { return 5 - band; }
 
 // ---------------------------------------------------------------- mesh data in HBM
 // Structure of arrays, one entry per element, element order as given.
+constexpr int kTableSlots = 75;  // node records per element in the node table (4 + 7 + 12 + 19 + 33)
+
 struct MeshDev {
     int n = 0;
     // mixed path records (float4, 64 B per element)
@@ -36,6 +38,7 @@ struct MeshDev {
     float4* clo = nullptr;  // centroid lo part xyz, w = L
     float4* e0 = nullptr;   // frame vector e0 xyz, w = area
     float4* e1 = nullptr;   // frame vector e1 xyz, w = 0
+    float4* nodes = nullptr;  // BEM_FLAG_NODE_TABLE: [n][kTableSlots][2] node records of every rule
     // FP64 path / near field / assembly
     double* cen = nullptr;    // [n][3] centroid
     double* fr = nullptr;     // [n][6] e0, e1 (FP64)
@@ -143,6 +146,8 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
                      unsigned long long n_near, cudaStream_t s);
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int out_stride4,
                     cudaStream_t s, const int* n_dev = nullptr);
+// fill MeshDev::nodes from the element records (k_far.cu)
+int launch_fill_nodes(bem_mesh* m, cudaStream_t s);
 // kc x potential of each element at its own centroid (sigma = 1): the diagonal of the
 // collocation matrix at the centroids (k_near.cu)
 int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s);

@@ -95,6 +95,7 @@ struct FarK {
     int n_chunks, chunk_len, n_items;
     int* work;  // work-item counter (zeroed before the launch)
     const float4 *chi, *clo, *e0f, *e1f;  // mixed element records
+    const float4* nodes;                  // node table (BEM_FLAG_NODE_TABLE) or nullptr
     const double *cen, *fr, *geo;         // FP64 element data
     const int* type;
     const double* sigma;  // nullptr: unit density (assembly)
@@ -213,6 +214,14 @@ __device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// 16-byte asynchronous copy global -> shared (no registers), and its group fences
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // hi + lo += x exactly up to the rounding of lo (Knuth's two-sum on packed
 // pairs; fma(a, -1, b) is b - a rounded once).  It keeps the running sums
@@ -343,7 +352,7 @@ constexpr size_t far_smem_bytes() {
 #ifndef BEM_MIN_BLOCKS
 #define BEM_MIN_BLOCKS 4
 #endif
-template <bool F64, int PT, bool WANT_E, int MODE, bool STATS>
+template <bool F64, int PT, bool WANT_E, int MODE, bool STATS, bool PRE>
 __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK p) {
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
@@ -394,7 +403,17 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         if (lane == 0) item = atomicAdd(p.work, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        const int tile = item / p.n_chunks, chunk = item - tile * p.n_chunks;
+        // on-the-fly nodes: the chunks of one tile are neighbours; node table: the
+        // tiles of one chunk are (so that the chunk's records stay in L2)
+        int tile, chunk;
+        if (PRE) {
+            const int n_tiles = (n_pts + p.tile_pts - 1) / p.tile_pts;
+            chunk = item / n_tiles;
+            tile = item - chunk * n_tiles;
+        } else {
+            tile = item / p.n_chunks;
+            chunk = item - tile * p.n_chunks;
+        }
         const int base = tile * (32 * PT);
 
         // ---- field points of this lane
@@ -482,7 +501,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             for (int c = 0; c < 4; ++c) acc8[k][c] = make_float2(0.0f, 0.0f);
 
         const int el0 = chunk * p.chunk_len, el1 = min(p.n_el, el0 + p.chunk_len);
-        int par = 0;  // node buffer parity
+        int par = 0;    // node buffer parity
+        int pre_n = 0;  // node table: node count of the next element's records already in flight
         for (int b0 = el0; b0 < el1; b0 += 32) {
             // ---- stage the batch: one element per lane
             __syncwarp();
@@ -686,9 +706,37 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         __syncwarp();
                         return n;
                     };
+                    // node table: copy rule r of element el (type t) into buffer buf
+                    // asynchronously (lane i: node i); the caller waits and syncs
+                    auto fetch = [&](int el, int t, int r, int buf) -> int {
+                        const int n = rs.n[t * 5 + r];
+                        const float4* src = p.nodes + ((size_t)el * kTableSlots + rs.start[t * 5 + r]) * 2;
+                        for (int i = lane; i < n; i += 32) {
+                            cp_async16(&ws.nd[buf][2 * i], src + 2 * i);
+                            cp_async16(&ws.nd[buf][2 * i + 1], src + 2 * i + 1);
+                        }
+                        cp_async_commit();
+                        return n;
+                    };
 
                     if (cd >= 1 && cd <= 5) {
-                        const int n = expand(band_rule(cd));
+                        int n;
+                        if constexpr (PRE) {
+                            // this element's records (fetched during the previous element if
+                            // that was a one-band element), then the next element's, whose
+                            // copy runs while this element's node loop does
+                            n = pre_n ? pre_n : fetch(b0 + e, ty, band_rule(cd), par);
+                            cp_async_wait_all();
+                            __syncwarp();
+                            pre_n = 0;
+                            if (e + 1 < nb) {
+                                const int cdn = __shfl_sync(0xffffffffu, code, e + 1);
+                                if (cdn >= 1 && cdn <= 5)
+                                    pre_n = fetch(b0 + e + 1, __float_as_int(ws.e1[e + 1].w), band_rule(cdn), par ^ 1);
+                            }
+                        } else {
+                            n = expand(band_rule(cd));
+                        }
                         nodes2<NP, WANT_E, true>(ws.nd[par], n, sv, uv, vv, eacc);
                         par ^= 1;
                         if (STATS && lane == 0) {
@@ -730,7 +778,14 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             for (int k = 0; k < NP; ++k)
                                 sm[k] = make_float2(bq[2 * k] == band ? sv[k].x : kInf,
                                                     bq[2 * k + 1] == band ? sv[k].y : kInf);
-                            const int n = expand(band_rule(band));
+                            int n;
+                            if constexpr (PRE) {
+                                n = fetch(b0 + e, ty, band_rule(band), par);
+                                cp_async_wait_all();
+                                __syncwarp();
+                            } else {
+                                n = expand(band_rule(band));
+                            }
                             nodes2<NP, WANT_E, false>(ws.nd[par], n, sm, uv, vv, eacc);
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
@@ -747,6 +802,14 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         }
                     }
 
+                    if constexpr (PRE) {  // the table's weights carry no charge: scale the element's sums
+                        const float q = ws.e0[e].w;
+                        const float2 q2 = make_float2(q, q);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k)
+#pragma unroll
+                            for (int j = 0; j < (WANT_E ? 4 : 1); ++j) eacc[k][j] = mul2(eacc[k][j], q2);
+                    }
                     if constexpr (MODE == 0) {
                         // the element's phi and E = d B - e0 sum b alpha - e1 sum b beta
                         // into the FP32 sums; every kFlush elements move those into the hi + lo sums
@@ -884,10 +947,10 @@ int upload_rules(int dev) {
     return BEM_OK;
 }
 
-template <bool F64, int PT, bool WANT_E, int MODE, bool STATS>
+template <bool F64, int PT, bool WANT_E, int MODE, bool STATS, bool PRE>
 int launch_one(const FarK& k, cudaStream_t s) {
     constexpr size_t sm = far_smem_bytes<F64, PT, WANT_E, MODE>();
-    auto fn = k_far<F64, PT, WANT_E, MODE, STATS>;
+    auto fn = k_far<F64, PT, WANT_E, MODE, STATS, PRE>;
     static int per_sm = 0, sms = 0;  // per instantiation
     if (!per_sm) {
         BEM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -908,9 +971,43 @@ int launch_one(const FarK& k, cudaStream_t s) {
 
 template <bool F64, int PT, bool WANT_E, int MODE>
 int launch_stats(const FarK& k, cudaStream_t s, bool stats) {
-    return stats ? launch_one<F64, PT, WANT_E, MODE, true>(k, s) : launch_one<F64, PT, WANT_E, MODE, false>(k, s);
+    if constexpr (!F64) {
+        if (k.nodes)
+            return stats ? launch_one<F64, PT, WANT_E, MODE, true, true>(k, s)
+                         : launch_one<F64, PT, WANT_E, MODE, false, true>(k, s);
+    }
+    return stats ? launch_one<F64, PT, WANT_E, MODE, true, false>(k, s)
+                 : launch_one<F64, PT, WANT_E, MODE, false, false>(k, s);
+}
+
+// Node records of every rule for every element (BEM_FLAG_NODE_TABLE): thread
+// (element j, slot) writes what the kernel's on-the-fly expansion writes,
+// with the bare weight w in place of w q.
+__global__ void k_fill_nodes(int n, const float4* __restrict__ e0f, const float4* __restrict__ e1f,
+                             const int* __restrict__ type, float4* __restrict__ out) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)n * kTableSlots) return;
+    const int j = (int)(id / kTableSlots), slot = (int)(id - (long long)j * kTableSlots);
+    const int t = type[j];
+    const float al = c_alpha_f[t * kSlots + slot], be = c_beta_f[t * kSlots + slot], w = c_w_f[t * kSlots + slot];
+    const float4 f0 = e0f[j], f1 = e1f[j];
+    const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y), oz = fmaf(al, f0.z, be * f1.z);
+    const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
+    out[2 * id] = make_float4(-al, -al, -be, -be);
+    out[2 * id + 1] = make_float4(oo, oo, w, w);
 }
 }  // namespace
+
+int launch_fill_nodes(bem_mesh* m, cudaStream_t s) {
+    int rc = upload_rules(m->device);
+    if (rc) return rc;
+    const long long total = (long long)m->d.n * kTableSlots;
+    if (total == 0) return BEM_OK;
+    k_fill_nodes<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(m->d.n, m->d.e0, m->d.e1, m->d.type, m->d.nodes);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
 
 int far_points_per_tile(int precision) { return 32 * (precision == kFP64 ? kPtFp64 : kPtMixed); }
 
@@ -924,6 +1021,7 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.n_el = m->d.n;
     k.work = a.work;
     k.chi = m->d.chi; k.clo = m->d.clo; k.e0f = m->d.e0; k.e1f = m->d.e1;
+    k.nodes = m->precision == kFP64 ? nullptr : m->d.nodes;
     k.cen = m->d.cen; k.fr = m->d.fr; k.geo = m->d.geo;
     k.type = m->d.type;
     k.sigma = a.sigma;
