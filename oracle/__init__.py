@@ -68,6 +68,10 @@ def _load():
         lib.oracle_max_threads.restype = C.c_int
         lib.oracle_element_batch.argtypes = [C.c_int64, i32, d, d, C.c_int, C.c_int, d, d, i32, C.c_int]
         lib.oracle_element_batch.restype = C.c_int
+        lib.oracle_element_grad.argtypes = [C.c_int, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
+        lib.oracle_element_grad.restype = C.c_int
+        lib.oracle_eval_grad.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, C.c_int]
+        lib.oracle_eval_grad.restype = C.c_int
         _lib = lib
         return lib
 
@@ -131,6 +135,40 @@ def element(type_: int, verts, P, method: int = METHOD_PAPER, param: int = 0, li
     if rc != 0:
         raise ValueError("oracle_element: bad arguments")
     return out, band.value
+
+
+def element_grad(type_: int, verts, P, method: int = METHOD_PAPER, param: int = 0, limits=None):
+    """Field gradient dE_i/dx_j of one element with sigma = 1, WITHOUT the
+    1/(4 pi eps0) factor, as (xx, yy, zz, xy, xz, yz).  Returns (out[6], band)."""
+    v = np.zeros((4, 3))
+    vv = np.asarray(verts, float).reshape(-1, 3)
+    v[: vv.shape[0]] = vv
+    P = _f64(P, (3,))
+    lim = None if limits is None else _f64(limits, (10,))
+    out = np.zeros(6)
+    band = C.c_int(-1)
+    rc = _load().oracle_element_grad(type_, _dp(v), _dp(P), method, param, _dp(lim), _dp(out), C.byref(band))
+    if rc != 0:
+        raise ValueError("oracle_element_grad: bad arguments")
+    return out, band.value
+
+
+def eval_grad(types, verts, sigma, pts, limits=None, eps0: float = 0.0, nthreads: int | None = None):
+    """Field gradient (n, 6) = (xx, yy, zz, xy, xz, yz) of dE_i/dx_j at the
+    field points, summed over all elements in index order by the method,
+    including 1/(4 pi eps0)."""
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    verts = _f64(verts, (types.shape[0], 4, 3))
+    sigma = _f64(sigma, (types.shape[0],))
+    pts = _f64(pts).reshape(-1, 3)
+    G = np.zeros((pts.shape[0], 6))
+    lim = None if limits is None else _f64(limits, (10,))
+    rc = _load().oracle_eval_grad(types.shape[0], types.ctypes.data_as(C.POINTER(C.c_int32)), _dp(verts),
+                                  _dp(sigma), _dp(lim), eps0, pts.shape[0], _dp(pts), _dp(G),
+                                  nthreads or max_threads())
+    if rc != 0:
+        raise ValueError("oracle_eval_grad: bad arguments")
+    return G
 
 
 def element_batch(types, verts, P, method: int = METHOD_PAPER, param: int = 0, limits=None,

@@ -801,3 +801,198 @@ int oracle_element_batch(int64_t n, const int32_t* type, const double* verts, co
     }
     return bad ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Field gradient dE_i / dx_j, output as (xx, yy, zz, xy, xz, yz), unit  */
+/* sigma, without 1/(4 pi eps0).                                        */
+/*                                                                      */
+/* Sec. 7 notes that point charges give higher derivatives of the field */
+/* directly: a charge q at Q adds q (delta_ij / r^3 - 3 r_i r_j / r^5)  */
+/* with r = P - Q.  The analytic branch differentiates the near-field    */
+/* decomposition E = sum_e m_e l_e + n Omega used above: the gradient of */
+/* the edge integral l_e is -J_e, J_e = int_e (P - Q) / R^3 ds (the     */
+/* field of the edge as a unit line charge), and the gradient of the    */
+/* solid angle is -sum_e t_e x J_e (the Biot-Savart field of the         */
+/* boundary), so                                                        */
+/*   dE_i / dx_j = - sum_e m_e,i J_e,j - n_i (sum_e t_e x J_e)_j .      */
+/* ------------------------------------------------------------------ */
+static void charge_grad(double q, const double r[3], double g[6])
+{
+    const double r2 = dot3(r, r), inv = 1.0 / sqrt(r2);
+    const double inv3 = inv * inv * inv, c = 3.0 * q * inv3 / r2;
+    g[0] += q * inv3 - c * r[0] * r[0];
+    g[1] += q * inv3 - c * r[1] * r[1];
+    g[2] += q * inv3 - c * r[2] * r[2];
+    g[3] -= c * r[0] * r[1];
+    g[4] -= c * r[0] * r[2];
+    g[5] -= c * r[1] * r[2];
+}
+
+static void cubature_grad(const elem_t* e, int rule, const double P[3], double g[6])
+{
+    const rule_t* r = e->type == 0 ? &TRI[rule] : &RECT[rule];
+    int i;
+    for (i = 0; i < 6; ++i) g[i] = 0.0;
+    for (i = 0; i < r->n; ++i) {
+        double Q[3], d[3];
+        rule_node(e, r, i, Q);
+        sub3(P, Q, d);
+        charge_grad(r->w[i] * e->area, d, g);
+    }
+}
+
+static void gl2_grad(const elem_t* e, int n, const double P[3], double g[6])
+{
+    double x[NGL_MAX], w[NGL_MAX];
+    int i, j, k;
+    gauss_legendre(n, x, w);
+    for (k = 0; k < 6; ++k) g[k] = 0.0;
+    for (i = 0; i < n; ++i) {
+        for (j = 0; j < n; ++j) {
+            double Q[3], d[3], wt;
+            if (e->type == 1) {
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->cen[k] + 0.5 * e->a * x[i] * e->ux[k] + 0.5 * e->b * x[j] * e->uy[k];
+                wt = w[i] * w[j] * e->a * e->b / 4.0;
+            } else {
+                const double u = 0.5 * (x[i] + 1.0), v = 0.5 * (x[j] + 1.0);
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->v[0][k] + u * (e->v[1][k] - e->v[0][k]) + u * v * (e->v[2][k] - e->v[1][k]);
+                wt = 0.25 * w[i] * w[j] * 2.0 * e->area * u;
+            }
+            sub3(P, Q, d);
+            charge_grad(wt, d, g);
+        }
+    }
+}
+
+/* J = int over the edge V1 -> V2 of (P - Q) / R^3 ds.  With t the unit
+ * tangent, u_k = (V_k - P)·t and rho = (V1 - P) - u1 t (from P to the edge
+ * line, perpendicular):  J = -rho (u2/R2 - u1/R1) / |rho|^2 + t (1/R2 - 1/R1).
+ * The two differences are rewritten as quotients without cancellation; a
+ * point on the closed edge (a singularity of the edge's field) gives 0. */
+static void edge_line_field(const double V1[3], const double V2[3], const double P[3], double J[3])
+{
+    double t[3], r1[3], r2[3], rho[3], len, u1, u2, R1, R2, rho2, f, g;
+    int k;
+    sub3(V2, V1, t);
+    len = norm3(t);
+    for (k = 0; k < 3; ++k) t[k] /= len;
+    sub3(V1, P, r1);
+    sub3(V2, P, r2);
+    u1 = dot3(r1, t);
+    u2 = dot3(r2, t);
+    R1 = norm3(r1);
+    R2 = norm3(r2);
+    for (k = 0; k < 3; ++k) rho[k] = r1[k] - u1 * t[k];
+    rho2 = dot3(rho, rho);
+    J[0] = J[1] = J[2] = 0.0;
+    if (R1 == 0.0 || R2 == 0.0) return;
+    if (u1 >= 0.0) {        /* the edge lies ahead of the foot of the perpendicular */
+        f = (u2 - u1) * (u2 + u1) / (R1 * R2 * (u2 * R1 + u1 * R2));
+    } else if (u2 <= 0.0) { /* ... or behind it */
+        f = (u1 - u2) * (u1 + u2) / (R1 * R2 * (-u1 * R2 - u2 * R1));
+    } else {                /* the foot lies on the edge */
+        if (rho2 == 0.0) return;
+        f = (u2 / R2 - u1 / R1) / rho2;
+    }
+    g = (u1 - u2) * (u1 + u2) / (R1 * R2 * (R1 + R2)); /* 1/R2 - 1/R1 */
+    for (k = 0; k < 3; ++k) J[k] = -rho[k] * f + t[k] * g;
+}
+
+static void analytic_grad(const elem_t* e, const double P[3], double g[6])
+{
+    const int nv = e->type == 0 ? 3 : 4;
+    double n[3], e1[3], e2[3], nl, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gw[3] = {0, 0, 0};
+    int j, a, b;
+    sub3(e->v[1], e->v[0], e1);
+    sub3(e->v[2], e->v[0], e2);
+    cross3(e1, e2, n);
+    nl = norm3(n);
+    for (a = 0; a < 3; ++a) n[a] /= nl;
+    for (j = 0; j < nv; ++j) {
+        const double* V1 = e->v[j];
+        const double* V2 = e->v[(j + 1) % nv];
+        double t[3], m[3], J[3], tj[3], len;
+        sub3(V2, V1, t);
+        len = norm3(t);
+        for (a = 0; a < 3; ++a) t[a] /= len;
+        cross3(t, n, m);
+        edge_line_field(V1, V2, P, J);
+        for (a = 0; a < 3; ++a)
+            for (b = 0; b < 3; ++b) G[a][b] -= m[a] * J[b];
+        cross3(t, J, tj);
+        for (a = 0; a < 3; ++a) gw[a] += tj[a];
+    }
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b) G[a][b] -= n[a] * gw[b];
+    g[0] = G[0][0]; g[1] = G[1][1]; g[2] = G[2][2];
+    g[3] = G[0][1]; g[4] = G[0][2]; g[5] = G[1][2];
+}
+
+/* gradient of ONE element, sigma = 1, without 1/(4 pi eps0); methods as
+ * oracle_element (SUBDIV not offered) */
+int oracle_element_grad(int type, const double* verts, const double* P, int method, int param,
+                        const double* limits, double* out /* 6 */, int* band_out)
+{
+    elem_t e;
+    int band = -1;
+    build_rules();
+    elem_setup(&e, type, verts);
+    switch (method) {
+    case OR_METHOD_PAPER:
+        band = choose_band(&e, P, limits ? limits + 5 * type : DEFAULT_LIMITS[type], NULL);
+        if (band == 0) analytic_grad(&e, P, out);
+        else cubature_grad(&e, band - 1, P, out);
+        break;
+    case OR_METHOD_GL2:
+        if (param < 1 || param > NGL_MAX) return -1;
+        gl2_grad(&e, param, P, out);
+        break;
+    case OR_METHOD_ANALYTIC:
+        analytic_grad(&e, P, out);
+        break;
+    case OR_METHOD_RULE:
+        if (param < 0 || param > 4) return -1;
+        cubature_grad(&e, param, P, out);
+        break;
+    default:
+        return -1;
+    }
+    if (band_out) *band_out = band;
+    return 0;
+}
+
+/* field gradient at n_pts points, summed over all elements in index order
+ * by the method (rule bands, analytic near field), times 1/(4 pi eps0);
+ * G is n_pts x 6 (xx, yy, zz, xy, xz, yz) */
+int oracle_eval_grad(int64_t n_el, const int32_t* type, const double* verts, const double* sigma,
+                     const double* limits, double eps0, int64_t n_pts, const double* pts, double* G, int nthreads)
+{
+    const double kc = coulomb_k(eps0);
+    int64_t p, j;
+    build_rules();
+    if (n_el < 0 || n_pts < 0) return -1;
+    for (j = 0; j < n_el; ++j)
+        if (type[j] != 0 && type[j] != 1) return -1;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (p = 0; p < n_pts; ++p) {
+        const double* P = pts + 3 * p;
+        double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
+        int64_t jj;
+        int k;
+        for (jj = 0; jj < n_el; ++jj) {
+            elem_t e;
+            double f[6];
+            int band;
+            elem_setup(&e, type[jj], verts + 12 * jj);
+            band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], NULL);
+            if (band == 0) analytic_grad(&e, P, f);
+            else cubature_grad(&e, band - 1, P, f);
+            for (k = 0; k < 6; ++k) nsum_add(&s[k], &c[k], sigma[jj] * f[k]);
+        }
+        for (k = 0; k < 6; ++k) G[6 * p + k] = kc * (s[k] + c[k]);
+    }
+    return 0;
+}
