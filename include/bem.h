@@ -135,6 +135,23 @@ int bem_set_sigma(bem_mesh* mesh, const double* sigma, void* stream);
 int bem_eval(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
 
 /*
+ * bem_eval_grad -- the field gradient dE_i / dx_j at n field points.  The
+ * paper notes that point charges give higher derivatives of the field
+ * directly (Sec. 7, for field maps by Hermite interpolation): each node
+ * charge q_i adds q_i (delta_ij / r^3 - 3 r_i r_j / r^5), with the same rule
+ * bands as bem_eval; below the near limit the analytic gradient of the
+ * uniformly charged polygon is used (the derivative of the near-field
+ * formula: edge line fields and the gradient of the solid angle).  Always
+ * evaluated in FP64, whatever the mesh's precision.
+ *   points [n][3]
+ *   G      [n][6]  (dEx/dx, dEy/dy, dEz/dz, dEx/dy, dEx/dz, dEy/dz) in V/m^2;
+ *                  the tensor is symmetric and, off the elements, traceless
+ * Host or device arrays; allocates its partial sums per call.  A point on an
+ * element edge gets that edge's (singular) contribution left out.
+ */
+int bem_eval_grad(bem_mesh* mesh, const double* points, int64_t n, double* G, void* stream);
+
+/*
  * bem_assemble -- BEM collocation matrix (the linear system for the charge
  * densities that the paper's BEM context solves, Sec. 1 and Sec. 5):
  *   A[i][j] = potential at colloc[i] of element j with sigma_j = 1,

@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
@@ -95,6 +95,8 @@ def load_library(build_if_missing: bool = True):
     lib.bem_cancel.argtypes = [vp, C.c_uint64]
     lib.bem_server_pause.argtypes = [vp, C.c_int32]
     lib.bem_server_stats.argtypes = [vp, C.c_int32, d]
+    lib.bem_eval_grad.argtypes = [vp, vp, C.c_int64, vp, vp]
+    lib.bem_eval_grad.restype = C.c_int
     lib.bem_solve.argtypes = [vp, vp, vp, C.POINTER(bem_solve_options), d, vp]
     lib.bem_solve.restype = C.c_int
     for name in ("bem_server_create", "bem_submit", "bem_poll", "bem_wait", "bem_cancel", "bem_server_pause",
@@ -246,6 +248,13 @@ def bem_matvec(mesh: int, x, y, stream=None) -> None:
     _check(load_library().bem_matvec(mesh, xp, _ptr(y), _stream(stream)))
 
 
+def bem_eval_grad(mesh: int, points, G, stream=None) -> None:
+    """Field gradient (n, 6) = (dEx/dx, dEy/dy, dEz/dz, dEx/dy, dEx/dz, dEy/dz) at the points."""
+    pp, ptr = _prep(points, np.float64)
+    n = (pp.numel() if _is_torch(pp) else pp.size) // 3
+    _check(load_library().bem_eval_grad(mesh, ptr, n, _ptr(G), _stream(stream)))
+
+
 def bem_solve(mesh: int, rhs, sigma, restart: int = 0, max_iter: int = 0, tol: float = 0.0, x0: bool = False,
               refine: bool = False, stream=None) -> dict:
     """Charge densities sigma with A sigma = rhs at the centroids (restarted,
@@ -338,6 +347,13 @@ class Mesh:
         E = _empty_like_kind(points, (n, 3)) if want_E else None
         bem_eval(self._h, points, phi, E, stream)
         return phi, E
+
+    def eval_grad(self, points, stream=None):
+        """Field gradient (n, 6) at the points (bem_eval_grad), same array kind as points."""
+        n = (points.numel() if _is_torch(points) else np.asarray(points).size) // 3
+        G = _empty_like_kind(points, (n, 6))
+        bem_eval_grad(self._h, points, G, stream)
+        return G
 
     def assemble(self, colloc, stream=None):
         m = (colloc.numel() if _is_torch(colloc) else np.asarray(colloc).size) // 3

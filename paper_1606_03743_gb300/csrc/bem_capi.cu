@@ -519,6 +519,110 @@ int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* 
     return BEM_OK;
 }
 
+
+}  // extern "C"
+
+namespace {
+// Device buffer freed on scope exit.
+template <typename T>
+struct Scratch {
+    T* p = nullptr;
+    ~Scratch() {
+        if (p) cudaFree(p);
+    }
+    int alloc(size_t count) {
+        const cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * (count > 0 ? count : 1));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            set_error("bem_eval_grad: cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
+            return BEM_ERR_OOM;
+        }
+        return BEM_OK;
+    }
+};
+
+// One slice of bem_eval_grad: the FP64 far kernel in its gradient mode, the
+// compacted near pairs' analytic gradients, the per-point sums.
+int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStream_t s) {
+    int rc;
+    if ((rc = ensure_points(m, (size_t)n))) return rc;
+    Work& w = m->w;
+    const double* dpts;
+    if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s))) return rc;
+    if ((rc = launch_sort_points(m, dpts, (int)n, s))) return rc;
+    if ((rc = check_points(m, "bem_eval_grad", s))) return rc;
+    const size_t np = (size_t)n * (size_t)m->n_chunks;
+    const bool g_dev = is_device_ptr(G);
+    const size_t need = sizeof(double4) * 2 * np + (g_dev ? 0 : sizeof(double) * 6 * (size_t)n);
+    if (m->w.bytes + need > m->budget) {
+        set_error("bem_eval_grad: needs %zu bytes beyond the %zu in use (budget %zu)", need, m->w.bytes, m->budget);
+        return BEM_ERR_OOM;
+    }
+    Scratch<double4> part_g;
+    Scratch<double> gout;
+    if ((rc = part_g.alloc(2 * np))) return rc;
+    if (!g_dev && (rc = gout.alloc(6 * (size_t)n))) return rc;
+    double* dG = g_dev ? G : gout.p;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, kCounters * sizeof(unsigned long long), s));
+        FarArgs a{};
+        a.pts = dpts;
+        a.perm = w.perm;
+        a.n_pts = (int)n;
+        a.sigma = m->d.sigma;
+        a.part = w.part;
+        a.part_g = part_g.p;
+        a.near_cnt = w.near_cnt;
+        a.work = reinterpret_cast<int*>(w.counters + 14);
+        a.near_rec = w.near_rec;
+        a.counters = w.counters;
+        a.near_cap = w.cap_near;
+        a.kc = m->kc;
+        a.want_e = 1;
+        a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
+        if ((rc = launch_far(m, a, s))) return rc;
+        if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)np, w.scan_tmp, s))) return rc;
+        unsigned long long n_near = 0;
+        BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters, sizeof n_near, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (n_near > w.cap_near) {
+            if ((rc = ensure_near(m, (size_t)n_near))) return rc;  // grow and run again
+            continue;
+        }
+        Scratch<double4> gval;
+        if ((rc = gval.alloc(2 * (size_t)n_near))) return rc;
+        if ((rc = launch_near_grad(m, dpts, w.perm, m->d.sigma, gval.p, n_near, s))) return rc;
+        if ((rc = launch_finalize_grad(m, w.perm, (int)n, part_g.p, gval.p, n_near, dG, s))) return rc;
+        if (!g_dev) BEM_CUDA_TRY(cudaMemcpyAsync(G, dG, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA_TRY(cudaStreamSynchronize(s));
+        m->last_stats[12] = (int64_t)n_near;
+        return BEM_OK;
+    }
+    set_error("bem_eval_grad: near-pair list did not converge");
+    return BEM_ERR_CAPACITY;
+}
+}  // namespace
+
+extern "C" {
+
+int bem_eval_grad(bem_mesh* m, const double* points, int64_t n, double* G, void* stream) {
+    int rc = check_mesh(m, "bem_eval_grad");
+    if (rc) return rc;
+    if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && (!points || !G))) {
+        set_error("bem_eval_grad: bad arguments (n = %lld)", (long long)n);
+        return BEM_ERR_INVALID;
+    }
+    if (n == 0) return BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    for (int64_t off = 0; off < n; off += kEvalSlice) {
+        const int64_t k = std::min(kEvalSlice, n - off);
+        if ((rc = grad_slice(m, points + 3 * off, k, G + 6 * off, s))) return rc;
+    }
+    return BEM_OK;
+}
+
 int bem_matvec(bem_mesh* m, const double* x, double* y, void* stream) {
     int rc = check_mesh(m, "bem_matvec");
     if (rc) return rc;

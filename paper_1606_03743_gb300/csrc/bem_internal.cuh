@@ -126,6 +126,7 @@ struct FarArgs {
     int n_pts;
     const double* sigma; // per element charge density (eval) or the x of a matvec
     double4* part;       // out: far sums per (sorted point, chunk)
+    double4* part_g;     // gradient pass (FP64 kernel): 6 far sums per (sorted point, chunk), two double4
     int* near_cnt;       // out: near pairs per (sorted point, chunk)
     int* work;           // work-item counter, zero at launch
     int4* near_rec;      // out: near pair list
@@ -148,6 +149,11 @@ int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double
                     cudaStream_t s, const int* n_dev = nullptr);
 // fill MeshDev::nodes from the element records (k_far.cu)
 int launch_fill_nodes(bem_mesh* m, cudaStream_t s);
+// field gradient over the compacted near list and its per-point finalisation (k_near.cu)
+int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
+                     unsigned long long gcap, cudaStream_t s);
+int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* part_g, const double4* gval,
+                         unsigned long long gcap, double* G, cudaStream_t s);
 // kc x potential of each element at its own centroid (sigma = 1): the diagonal of the
 // collocation matrix at the centroids (k_near.cu)
 int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s);

@@ -100,6 +100,7 @@ struct FarK {
     const int* type;
     const double* sigma;  // nullptr: unit density (assembly)
     double4* part;        // per (point, chunk) far sums, [n_pts][n_chunks]
+    double4* part_g;      // gradient pass: per (point, chunk) 6 sums as two double4
     int* near_cnt;        // per (point, chunk) near pairs, [n_pts][n_chunks]
     int4* near_rec;
     unsigned long long* counters;
@@ -207,6 +208,39 @@ __device__ __forceinline__ void nodes(const R4* __restrict__ nd, int n, const R 
     }
 #pragma unroll kNodeUnroll
     for (; i < n; ++i) node<R, R4, PT, WANT_E, MASKED, false>(nd[i], dx, dy, dz, acc, mq);
+}
+
+// Field gradient of one point charge (offset o, charge o.w) at the PT points
+// of a lane: g += q (I / r^3 - 3 r r^T / r^5), components (xx, yy, zz, xy,
+// xz, yz) of dE_i / dx_j (the point-charge derivatives of Sec. 7).  MASKED as
+// node(): point q's charge is scaled by mq[q].
+template <typename R, typename R4, int PT, bool MASKED>
+__device__ __forceinline__ void node_grad(const R4 o, const R (&dx)[PT], const R (&dy)[PT], const R (&dz)[PT],
+                                          R (&g)[PT][6], const R (&mq)[PT]) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const R rx = dx[q] - o.x, ry = dy[q] - o.y, rz = dz[q] - o.z;
+        const R r2 = fmad(rx, rx, fmad(ry, ry, rz * rz));
+        R wq = o.w;
+        if (MASKED) wq *= mq[q];
+        const R inv = rsq(r2), i2 = inv * inv;
+        const R b = wq * inv * i2;   // q_i / r^3
+        const R c = (R)3 * b * i2;   // 3 q_i / r^5
+        const R cx = c * rx, cy = c * ry;
+        g[q][0] = fmad(-cx, rx, g[q][0] + b);
+        g[q][1] = fmad(-cy, ry, g[q][1] + b);
+        g[q][2] = fmad(-c * rz, rz, g[q][2] + b);
+        g[q][3] = fmad(-cx, ry, g[q][3]);
+        g[q][4] = fmad(-cx, rz, g[q][4]);
+        g[q][5] = fmad(-cy, rz, g[q][5]);
+    }
+}
+
+template <typename R, typename R4, int PT, bool MASKED>
+__device__ __forceinline__ void nodes_grad(const R4* __restrict__ nd, int n, const R (&dx)[PT], const R (&dy)[PT],
+                                           const R (&dz)[PT], R (&g)[PT][6], const R (&mq)[PT]) {
+#pragma unroll 2
+    for (int i = 0; i < n; ++i) node_grad<R, R4, PT, MASKED>(nd[i], dx, dy, dz, g, mq);
 }
 
 // ---- mixed path: two field points per packed f32x2 operation
@@ -343,7 +377,8 @@ constexpr size_t far_smem_bytes() {
 
 // ------------------------------------------------------------ the kernel
 // MODE 0: evaluation (sum over elements); MODE 1: assembly (one value per
-// (point, element) pair written to A, potential only, sigma = 1).
+// (point, element) pair written to A, potential only, sigma = 1); MODE 2
+// (FP64 only): field gradient sums.
 // STATS: count pairs per (type, band) into counters[2 + 6 type + band], and
 // into counters[16..18] the (warp, element) pairs that ran one band for the
 // whole warp, those that fell back to per-point bands, and the node
@@ -482,6 +517,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 
         // ---- accumulators
         R acc[F64 ? PT : 1][4];  // FP64 evaluation: the running sums
+        R accg[MODE == 2 ? PT : 1][6];  // gradient pass: the running sums
         float2 acc8[NP][4];      // mixed: FP32 sum of up to 8 element sums (point pairs)
         int ncnt[PT];
 #pragma unroll
@@ -490,6 +526,10 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if constexpr (F64) acc[q][c] = (R)0;
+            if constexpr (MODE == 2) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) accg[q][c] = (R)0;
+            }
         }
         if constexpr (ACC64) {
 #pragma unroll
@@ -596,7 +636,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 
                     if (cd >= 1 && cd <= 5) {
                         const int n = expand(band_rule(cd));
-                        nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, ones);
+                        if constexpr (MODE == 2) nodes_grad<R, R4, PT, false>(ws.nd[par], n, dx, dy, dz, accg, ones);
+                        else nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, ones);
                         par ^= 1;
                         if (STATS && lane == 0) {
                             atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -641,7 +682,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                                 mz[q] = on ? dz[q] : (R)1e3;
                             }
                             const int n = expand(band_rule(band));
-                            nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, mx, my, mz, dst, mq);
+                            if constexpr (MODE == 2) nodes_grad<R, R4, PT, true>(ws.nd[par], n, mx, my, mz, accg, mq);
+                            else nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, mx, my, mz, dst, mq);
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                         }
@@ -876,6 +918,16 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 p.near_cnt[slot] = ncnt[q];
             }
         }
+        if constexpr (MODE == 2) {
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                if (!valid[q]) continue;
+                const size_t slot = (size_t)sidx[q] * p.n_chunks + chunk;
+                p.part_g[2 * slot] = make_double4(accg[q][0], accg[q][1], accg[q][2], accg[q][3]);
+                p.part_g[2 * slot + 1] = make_double4(accg[q][4], accg[q][5], 0.0, 0.0);
+                p.near_cnt[slot] = ncnt[q];
+            }
+        }
     }
     if (STATS) {
         __syncthreads();
@@ -1026,6 +1078,7 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.type = m->d.type;
     k.sigma = a.sigma;
     k.part = a.part;
+    k.part_g = a.part_g;
     k.near_cnt = a.near_cnt;
     k.near_rec = a.near_rec;
     k.counters = a.counters;
@@ -1042,8 +1095,8 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
             k.tau2d[t][i] = m->limits[t][i] * m->limits[t][i];
             k.tau2f[t][i] = (float)k.tau2d[t][i];
         }
-    const bool f64 = m->precision == kFP64;
-    const int tile = far_points_per_tile(m->precision);
+    const bool f64 = m->precision == kFP64 || a.part_g;  // gradients: always the FP64 kernel
+    const int tile = far_points_per_tile(f64 ? kFP64 : kMixed);
     const int n_tiles = (a.n_pts + tile - 1) / tile;
     if (a.A) {
         // assembly has no reduction over elements: cut them finely enough to fill the GPU
@@ -1059,6 +1112,7 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.n_items = n_tiles * k.n_chunks;
     k.tile_pts = tile;
     const bool st = a.stats != 0;
+    if (a.part_g) return launch_stats<true, kPtFp64, true, 2>(k, s, st);
     if (a.A) {
         if (f64) return launch_stats<true, kPtFp64, false, 1>(k, s, st);
         return launch_stats<false, kPtMixed, false, 1>(k, s, st);

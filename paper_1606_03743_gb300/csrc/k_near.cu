@@ -86,6 +86,111 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double
     out[3] = fma(nrm.z, om, ez);
 }
 
+// Field of an edge V1 -> V2 as a unit line charge at P: J = int (P - Q)/R^3 ds
+// = -rho (u2/R2 - u1/R1) / |rho|^2 + t (1/R2 - 1/R1), with t the unit tangent,
+// u_k = (V_k - P)·t, rho = (V1 - P) - u1 t; the differences are rewritten as
+// quotients without cancellation.  A point on the closed edge gives 0.
+__device__ D3 edge_line_field(D3 c1, D3 c2) {  // corners relative to P
+    D3 t = sub(c2, c1);
+    t = scale(t, 1.0 / sqrt(dot(t, t)));
+    const double u1 = dot(c1, t), u2 = dot(c2, t);
+    const double R1 = sqrt(dot(c1, c1)), R2 = sqrt(dot(c2, c2));
+    const D3 rho = sub(c1, scale(t, u1));
+    const double rho2 = dot(rho, rho);
+    if (R1 == 0.0 || R2 == 0.0) return D3{0.0, 0.0, 0.0};
+    double f;
+    if (u1 >= 0.0) f = (u2 - u1) * (u2 + u1) / (R1 * R2 * (u2 * R1 + u1 * R2));
+    else if (u2 <= 0.0) f = (u1 - u2) * (u1 + u2) / (R1 * R2 * (-u1 * R2 - u2 * R1));
+    else if (rho2 > 0.0) f = (u2 / R2 - u1 / R1) / rho2;
+    else return D3{0.0, 0.0, 0.0};
+    const double g = (u1 - u2) * (u1 + u2) / (R1 * R2 * (R1 + R2));  // 1/R2 - 1/R1
+    return D3{fma(-rho.x, f, t.x * g), fma(-rho.y, f, t.y * g), fma(-rho.z, f, t.z * g)};
+}
+
+// Field gradient dE_i/dx_j (xx, yy, zz, xy, xz, yz; unit sigma, without
+// 1/(4 pi eps0)) of the polygon at P, from the decomposition above: the
+// gradient of l_e is -J_e and that of Omega is -sum_e t_e x J_e, so
+//   dE/dx = -sum_e m_e J_e^T - n (sum_e t_e x J_e)^T.
+__device__ void polygon_grad(int nv, const double* __restrict__ V, D3 P, double out[6]) {
+    D3 c[4];
+    for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
+    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
+    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    D3 w{0.0, 0.0, 0.0};
+    for (int k = 0; k < nv; ++k) {
+        const int k2 = (k + 1 == nv) ? 0 : k + 1;
+        D3 t = sub(c[k2], c[k]);
+        t = scale(t, 1.0 / sqrt(dot(t, t)));
+        const D3 m = cross(t, nrm);
+        const D3 J = edge_line_field(c[k], c[k2]);
+        const double mv[3] = {m.x, m.y, m.z}, Jv[3] = {J.x, J.y, J.z};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[a][b] = fma(-mv[a], Jv[b], G[a][b]);
+        const D3 tj = cross(t, J);
+        w = D3{w.x + tj.x, w.y + tj.y, w.z + tj.z};
+    }
+    const double nv3[3] = {nrm.x, nrm.y, nrm.z}, wv[3] = {w.x, w.y, w.z};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[a][b] = fma(-nv3[a], wv[b], G[a][b]);
+    out[0] = G[0][0];
+    out[1] = G[1][1];
+    out[2] = G[2][2];
+    out[3] = G[0][1];
+    out[4] = G[0][2];
+    out[5] = G[1][2];
+}
+
+// Gradient of each compacted near pair, times sigma, at the pair's slot (two double4).
+__global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
+                            unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
+                            const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
+                            const double* __restrict__ verts, const double* __restrict__ sigma,
+                            double4* __restrict__ gval) {
+    const unsigned long long n = min(counters[0], cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int4 r = rec[i];
+        const int src = perm[r.x];
+        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
+        double f[6];
+        polygon_grad(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
+        const double sg = sigma[r.y];
+        const unsigned long long slot =
+            (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
+        if (slot < gcap) {
+            gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
+            gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
+        }
+    }
+}
+
+// far gradient sums of the chunks in chunk order + near pairs in element
+// order, times 1/(4 pi eps0), written at the point's original position.
+__global__ void k_finalize_grad(int n, int n_chunks, const int* __restrict__ perm, const double4* __restrict__ part_g,
+                                const int* __restrict__ near_cnt, const int* __restrict__ near_off,
+                                const double4* __restrict__ gval, unsigned long long gcap, double kc,
+                                double* __restrict__ G) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const size_t p0 = (size_t)i * n_chunks;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    int cnt = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const double4 a = part_g[2 * (p0 + c)], b = part_g[2 * (p0 + c) + 1];
+        s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w; s[4] += b.x; s[5] += b.y;
+        cnt += near_cnt[p0 + c];
+    }
+    const unsigned long long off = (unsigned long long)near_off[p0];
+    for (int k = 0; k < cnt; ++k) {
+        if (off + k >= gcap) break;
+        const double4 a = gval[2 * (off + k)], b = gval[2 * (off + k) + 1];
+        s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w; s[4] += b.x; s[5] += b.y;
+    }
+    const int o = perm[i];
+    for (int k = 0; k < 6; ++k) G[6 * (size_t)o + k] = kc * s[k];
+}
+
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
@@ -207,6 +312,26 @@ int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double
     k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, n_dev, m->n_chunks, perm, w.part, w.near_cnt, w.near_off,
                                                    w.near_val,
                                                    (unsigned long long)w.cap_near, m->kc, phi, E, stride4);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
+
+int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
+                     unsigned long long gcap, cudaStream_t s) {
+    Work& w = m->w;
+    k_near_grad<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, gcap, pts, perm,
+                                        w.near_off, m->n_chunks, m->d.type, m->d.verts, sigma, gval);
+    BEM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return BEM_OK;
+}
+
+int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* part_g, const double4* gval,
+                         unsigned long long gcap, double* G, cudaStream_t s) {
+    Work& w = m->w;
+    k_finalize_grad<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, m->n_chunks, perm, part_g, w.near_cnt, w.near_off,
+                                                        gval, gcap, m->kc, G);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
