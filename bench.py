@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-assembly", action="store_true", help="skip the collocation-assembly measurement")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-large", action="store_true", help="skip the 500k-element x 4M-point mixed vs FP64 run")
+    ap.add_argument("--grad-points", type=int, default=16384, help="points of the field-gradient line")
     ap.add_argument("--large-points", type=int, default=4_000_000)
     ap.add_argument("--large-fp64-points", type=int, default=32768)
     ap.add_argument("--large-oracle-points", type=int, default=2048)
@@ -372,6 +373,27 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     g64phi = f64phi.cpu().numpy()
     g64E = f64E.cpu().numpy()
     k = min(ns, n64)
+
+    # ---- field gradient (FP64 far kernel in its gradient mode + analytic near field)
+    ng = min(a.grad_points, a.points)
+    pg = torch.from_numpy(pts[:ng]).to(dev)
+    Gd = torch.empty((ng, 6), dtype=torch.float64, device=dev)
+    bem.bem_eval_grad(m.handle, pg, Gd, stream=stream.cuda_stream)
+    t0.record(stream)
+    bem.bem_eval_grad(m.handle, pg, Gd, stream=stream.cuda_stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    msg = t0.elapsed_time(t1)
+    ngo = min(ng, 512)
+    t0c = time.perf_counter()
+    Gref = oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, pts[:ngo], nthreads=nt)
+    cpu_g = time.perf_counter() - t0c
+    Gg = Gd[:ngo].cpu().numpy()
+    gerr = np.abs(Gg - Gref).max(axis=1) / np.abs(Gref).max(axis=1)
+    out["field_gradient"] = {"value": ng * mesh.n / (msg * 1e-3), "unit": UNIT, "n_points": ng, "ms": msg,
+                             "precision": "f64", "oracle_pairs_per_s": ngo * mesh.n / cpu_g,
+                             "max_rel_err_vs_oracle": float(gerr.max()), "oracle_points": ngo,
+                             "max_rel_trace": float((np.abs(Gg[:, :3].sum(1)) / np.abs(Gg).max(axis=1)).max())}
 
     out["accuracy_vs_oracle"] = accuracy_report(gphi, gE, g64phi[:k], g64E[:k], rphi, rE, mdr, esum)
     out["accuracy_vs_oracle"]["run_precision"] = a.precision
