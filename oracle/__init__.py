@@ -68,6 +68,10 @@ def _load():
         lib.oracle_max_threads.restype = C.c_int
         lib.oracle_element_batch.argtypes = [C.c_int64, i32, d, d, C.c_int, C.c_int, d, d, i32, C.c_int]
         lib.oracle_element_batch.restype = C.c_int
+        lib.oracle_element_linear.argtypes = [C.c_int, d, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
+        lib.oracle_element_linear.restype = C.c_int
+        lib.oracle_eval_linear.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d, C.c_int]
+        lib.oracle_eval_linear.restype = C.c_int
         lib.oracle_element_grad.argtypes = [C.c_int, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
         lib.oracle_element_grad.restype = C.c_int
         lib.oracle_eval_grad.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, C.c_int]
@@ -135,6 +139,43 @@ def element(type_: int, verts, P, method: int = METHOD_PAPER, param: int = 0, li
     if rc != 0:
         raise ValueError("oracle_element: bad arguments")
     return out, band.value
+
+
+def element_linear(type_: int, verts, coef, P, method: int = METHOD_PAPER, param: int = 0, limits=None):
+    """phi, E of one element with the linear density sigma = coef[0] + coef[1]
+    alpha + coef[2] beta (the element's frame coordinates), WITHOUT the
+    1/(4 pi eps0) factor.  Returns (out[4], band)."""
+    v = np.zeros((4, 3))
+    vv = np.asarray(verts, float).reshape(-1, 3)
+    v[: vv.shape[0]] = vv
+    P = _f64(P, (3,))
+    cf = _f64(coef, (3,))
+    lim = None if limits is None else _f64(limits, (10,))
+    out = np.zeros(4)
+    band = C.c_int(-1)
+    rc = _load().oracle_element_linear(type_, _dp(v), _dp(cf), _dp(P), method, param, _dp(lim), _dp(out),
+                                       C.byref(band))
+    if rc != 0:
+        raise ValueError("oracle_element_linear: bad arguments")
+    return out, band.value
+
+
+def eval_linear(types, verts, coef, pts, limits=None, eps0: float = 0.0, nthreads: int | None = None):
+    """phi (n,), E (n, 3) of elements with linear densities coef (n_el, 3), by
+    the method, including 1/(4 pi eps0)."""
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    verts = _f64(verts, (types.shape[0], 4, 3))
+    coef = _f64(coef, (types.shape[0], 3))
+    pts = _f64(pts).reshape(-1, 3)
+    phi = np.zeros(pts.shape[0])
+    E = np.zeros((pts.shape[0], 3))
+    lim = None if limits is None else _f64(limits, (10,))
+    rc = _load().oracle_eval_linear(types.shape[0], types.ctypes.data_as(C.POINTER(C.c_int32)), _dp(verts),
+                                    _dp(coef), _dp(lim), eps0, pts.shape[0], _dp(pts), _dp(phi), _dp(E),
+                                    nthreads or max_threads())
+    if rc != 0:
+        raise ValueError("oracle_eval_linear: bad arguments")
+    return phi, E
 
 
 def element_grad(type_: int, verts, P, method: int = METHOD_PAPER, param: int = 0, limits=None):

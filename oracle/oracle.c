@@ -996,3 +996,285 @@ int oracle_eval_grad(int64_t n_el, const int32_t* type, const double* verts, con
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Linear charge density (Sec. 7: the cubature applies unchanged to     */
+/* non-constant densities; the paper treats constant ones).             */
+/*                                                                      */
+/* sigma(Q) = s_c + s_a alpha + s_b beta, with (alpha, beta) the         */
+/* element's coordinates Q - Q_cen = alpha e0 + beta e1 (triangle: e0 =  */
+/* A - Q_cen, e1 = B - Q_cen, i.e. alpha = lambda_A - lambda_C, beta =   */
+/* lambda_B - lambda_C of Eq. 3.3; rectangle: e0 = (a/2) u_x, e1 =        */
+/* (b/2) u_y, i.e. the natural coordinates x, y of Eq. 3.2).  Written as */
+/* sigma(Q) = s_c + g·(Q - Q_cen) with g = s_a grad(alpha) + s_b         */
+/* grad(beta), the in-plane dual vectors of e0, e1.                      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double sc, g[3], C[3];
+} lin_t;
+
+static void linear_density(const elem_t* e, const double* coef, lin_t* s)
+{
+    double e0[3], e1[3], g00, g01, g11, det, d0[3], d1[3];
+    int k;
+    if (e->type == 0) {
+        sub3(e->v[0], e->cen, e0);
+        sub3(e->v[1], e->cen, e1);
+    } else {
+        for (k = 0; k < 3; ++k) {
+            e0[k] = 0.5 * e->a * e->ux[k];
+            e1[k] = 0.5 * e->b * e->uy[k];
+        }
+    }
+    g00 = dot3(e0, e0);
+    g01 = dot3(e0, e1);
+    g11 = dot3(e1, e1);
+    det = g00 * g11 - g01 * g01;
+    for (k = 0; k < 3; ++k) {
+        d0[k] = (g11 * e0[k] - g01 * e1[k]) / det; /* grad(alpha) */
+        d1[k] = (g00 * e1[k] - g01 * e0[k]) / det; /* grad(beta) */
+    }
+    s->sc = coef[0];
+    for (k = 0; k < 3; ++k) {
+        s->g[k] = coef[1] * d0[k] + coef[2] * d1[k];
+        s->C[k] = e->cen[k];
+    }
+}
+
+static double lin_sigma(const lin_t* s, const double Q[3])
+{
+    double d[3];
+    sub3(Q, s->C, d);
+    return s->sc + dot3(s->g, d);
+}
+
+/* Eq. 4.1 with q_i = w_i area sigma(Q_i) */
+static void cubature_field_lin(const elem_t* e, int rule, const double P[3], const lin_t* s, double out[4])
+{
+    const rule_t* r = e->type == 0 ? &TRI[rule] : &RECT[rule];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int i, k;
+    for (i = 0; i < r->n; ++i) {
+        double Q[3], d[3], dist, qi;
+        rule_node(e, r, i, Q);
+        sub3(P, Q, d);
+        dist = norm3(d);
+        qi = r->w[i] * e->area * lin_sigma(s, Q);
+        acc[0] += qi / dist;
+        for (k = 0; k < 3; ++k) acc[k + 1] += qi * d[k] / (dist * dist * dist);
+    }
+    for (k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+static void gl2_field_lin(const elem_t* e, int n, const double P[3], const lin_t* s, double out[4])
+{
+    double x[NGL_MAX], w[NGL_MAX], acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int i, j, k;
+    gauss_legendre(n, x, w);
+    for (i = 0; i < n; ++i) {
+        for (j = 0; j < n; ++j) {
+            double Q[3], d[3], dist, wt;
+            if (e->type == 1) {
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->cen[k] + 0.5 * e->a * x[i] * e->ux[k] + 0.5 * e->b * x[j] * e->uy[k];
+                wt = w[i] * w[j] * e->a * e->b / 4.0;
+            } else {
+                const double u = 0.5 * (x[i] + 1.0), v = 0.5 * (x[j] + 1.0);
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->v[0][k] + u * (e->v[1][k] - e->v[0][k]) + u * v * (e->v[2][k] - e->v[1][k]);
+                wt = 0.25 * w[i] * w[j] * 2.0 * e->area * u;
+            }
+            wt *= lin_sigma(s, Q);
+            sub3(P, Q, d);
+            dist = norm3(d);
+            acc[0] += wt / dist;
+            for (k = 0; k < 3; ++k) acc[k + 1] += wt * d[k] / (dist * dist * dist);
+        }
+    }
+    for (k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+/* brute force as subdiv_field, with the parent element's density */
+static void subdiv_field_lin(const elem_t* e, int level, int n, const double P[3], const lin_t* s, double out[4])
+{
+    int k, c;
+    if (level == 0) {
+        gl2_field_lin(e, n, P, s, out);
+        return;
+    }
+    for (k = 0; k < 4; ++k) out[k] = 0.0;
+    if (e->type == 0) {
+        double m01[3], m12[3], m20[3], tris[4][4][3], part[4];
+        int t;
+        for (k = 0; k < 3; ++k) {
+            m01[k] = 0.5 * (e->v[0][k] + e->v[1][k]);
+            m12[k] = 0.5 * (e->v[1][k] + e->v[2][k]);
+            m20[k] = 0.5 * (e->v[2][k] + e->v[0][k]);
+        }
+        for (k = 0; k < 3; ++k) {
+            tris[0][0][k] = e->v[0][k]; tris[0][1][k] = m01[k];     tris[0][2][k] = m20[k];
+            tris[1][0][k] = m01[k];     tris[1][1][k] = e->v[1][k]; tris[1][2][k] = m12[k];
+            tris[2][0][k] = m20[k];     tris[2][1][k] = m12[k];     tris[2][2][k] = e->v[2][k];
+            tris[3][0][k] = m12[k];     tris[3][1][k] = m20[k];     tris[3][2][k] = m01[k];
+            for (c = 0; c < 4; ++c) tris[c][3][k] = 0.0;
+        }
+        for (t = 0; t < 4; ++t) {
+            elem_t sub;
+            elem_setup(&sub, 0, &tris[t][0][0]);
+            subdiv_field_lin(&sub, level - 1, n, P, s, part);
+            for (c = 0; c < 4; ++c) out[c] += part[c];
+        }
+    } else {
+        int qx, qy;
+        for (qx = 0; qx < 2; ++qx) {
+            for (qy = 0; qy < 2; ++qy) {
+                double corners[4][3], part[4];
+                const double x0 = qx - 1.0, y0 = qy - 1.0;
+                const double xs[4] = {x0, x0 + 1.0, x0 + 1.0, x0};
+                const double ys[4] = {y0, y0, y0 + 1.0, y0 + 1.0};
+                elem_t sub;
+                for (c = 0; c < 4; ++c)
+                    for (k = 0; k < 3; ++k)
+                        corners[c][k] = e->cen[k] + 0.5 * e->a * xs[c] * e->ux[k] + 0.5 * e->b * ys[c] * e->uy[k];
+                elem_setup(&sub, 1, &corners[0][0]);
+                subdiv_field_lin(&sub, level - 1, n, P, s, part);
+                for (c = 0; c < 4; ++c) out[c] += part[c];
+            }
+        }
+    }
+}
+
+/* Analytic near field for the linear density.  With P' the foot of P in
+ * the element plane (P = P' + h n) and w = Q - P', sigma(Q) = sigma(P') +
+ * g·w, and
+ *   int sigma / R dA = sigma(P') I0 + g · int w / R dA
+ *   int w / R dA     = sum_e m_e int_e R ds          (in-plane grad R = w / R)
+ *   int_e R ds       = (s2 R2 - s1 R1 + rho_e^2 l_e) / 2,  rho_e^2 = d_e^2 + h^2
+ *   int sigma (P - Q) / R^3 dA = sigma(P') E0 + h n (g · int w / R^3 dA)
+ *                                - (int w w^T / R^3 dA) g
+ *   int w / R^3 dA      = - sum_e m_e l_e           (grad (1/R) = -w / R^3)
+ *   int w w^T / R^3 dA  = Pi I0 - sum_e (int_e w / R ds) m_e^T,
+ *   int_e w / R ds      = d_e l_e m_e + (R2 - R1) t_e
+ * (the divergence theorem in the plane on w / R; Pi the in-plane
+ * projector), where I0, E0 are the constant-density results of
+ * analytic_field and d_e, l_e, s_k, R_k, m_e, t_e are as defined there. */
+static void analytic_field_lin(const elem_t* e, const double P[3], const lin_t* s, double out[4])
+{
+    const int nv = e->type == 0 ? 3 : 4;
+    double f0[4], n[3], e1[3], e2[3], nl, h, Pp[3], sP, I1[3] = {0.0, 0.0, 0.0}, Ec[3], hsum = 0.0;
+    int k, j;
+    analytic_field(e, P, f0);
+    sub3(e->v[1], e->v[0], e1);
+    sub3(e->v[2], e->v[0], e2);
+    cross3(e1, e2, n);
+    nl = norm3(n);
+    for (k = 0; k < 3; ++k) n[k] /= nl;
+    {
+        double pv[3];
+        sub3(P, e->v[0], pv);
+        h = dot3(pv, n);
+    }
+    for (k = 0; k < 3; ++k) Pp[k] = P[k] - h * n[k];
+    sP = lin_sigma(s, Pp);
+    for (k = 0; k < 3; ++k) Ec[k] = -s->g[k] * f0[0];
+    for (j = 0; j < nv; ++j) {
+        const double* V1 = e->v[j];
+        const double* V2 = e->v[(j + 1) % nv];
+        double t[3], m[3], r1[3], r2[3], len, s1, s2, R1, R2, d, perp2, l, gm;
+        sub3(V2, V1, t);
+        len = norm3(t);
+        for (k = 0; k < 3; ++k) t[k] /= len;
+        cross3(t, n, m);
+        sub3(V1, P, r1);
+        sub3(V2, P, r2);
+        s1 = dot3(r1, t);
+        s2 = dot3(r2, t);
+        R1 = norm3(r1);
+        R2 = norm3(r2);
+        d = dot3(r1, m);
+        perp2 = d * d + h * h;
+        l = edge_log(s1, s2, R1, R2, perp2);
+        for (k = 0; k < 3; ++k) I1[k] += m[k] * 0.5 * (s2 * R2 - s1 * R1 + perp2 * l);
+        gm = dot3(s->g, m);
+        hsum += gm * l;
+        for (k = 0; k < 3; ++k) Ec[k] += gm * (d * l * m[k] + (R2 - R1) * t[k]);
+    }
+    out[0] = sP * f0[0] + dot3(s->g, I1);
+    for (k = 0; k < 3; ++k) out[k + 1] = sP * f0[k + 1] - h * n[k] * hsum + Ec[k];
+}
+
+/* phi and E of ONE element with linear density coef = (s_c, s_a, s_b),
+ * without 1/(4 pi eps0); methods as oracle_element */
+int oracle_element_linear(int type, const double* verts, const double* coef, const double* P, int method, int param,
+                          const double* limits, double* out /* 4 */, int* band_out)
+{
+    elem_t e;
+    lin_t s;
+    int band = -1;
+    build_rules();
+    elem_setup(&e, type, verts);
+    linear_density(&e, coef, &s);
+    switch (method) {
+    case OR_METHOD_PAPER:
+        band = choose_band(&e, P, limits ? limits + 5 * type : DEFAULT_LIMITS[type], NULL);
+        if (band == 0) analytic_field_lin(&e, P, &s, out);
+        else cubature_field_lin(&e, band - 1, P, &s, out);
+        break;
+    case OR_METHOD_GL2:
+        if (param < 1 || param > NGL_MAX) return -1;
+        gl2_field_lin(&e, param, P, &s, out);
+        break;
+    case OR_METHOD_ANALYTIC:
+        analytic_field_lin(&e, P, &s, out);
+        break;
+    case OR_METHOD_RULE:
+        if (param < 0 || param > 4) return -1;
+        cubature_field_lin(&e, param, P, &s, out);
+        break;
+    case OR_METHOD_SUBDIV:
+        if (param < 0 || param > 12) return -1;
+        subdiv_field_lin(&e, param, 16, P, &s, out);
+        break;
+    default:
+        return -1;
+    }
+    if (band_out) *band_out = band;
+    return 0;
+}
+
+/* phi and E at n_pts points for elements with linear densities coef
+ * (n_el x 3), by the method, summed in index order, times 1/(4 pi eps0) */
+int oracle_eval_linear(int64_t n_el, const int32_t* type, const double* verts, const double* coef,
+                       const double* limits, double eps0, int64_t n_pts, const double* pts, double* phi, double* E,
+                       int nthreads)
+{
+    const double kc = coulomb_k(eps0);
+    int64_t p, j;
+    build_rules();
+    if (n_el < 0 || n_pts < 0) return -1;
+    for (j = 0; j < n_el; ++j)
+        if (type[j] != 0 && type[j] != 1) return -1;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (p = 0; p < n_pts; ++p) {
+        const double* P = pts + 3 * p;
+        double sm[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+        int64_t jj;
+        int k;
+        for (jj = 0; jj < n_el; ++jj) {
+            elem_t e;
+            lin_t s;
+            double f[4];
+            int band;
+            elem_setup(&e, type[jj], verts + 12 * jj);
+            linear_density(&e, coef + 3 * jj, &s);
+            band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], NULL);
+            if (band == 0) analytic_field_lin(&e, P, &s, f);
+            else cubature_field_lin(&e, band - 1, P, &s, f);
+            for (k = 0; k < 4; ++k) nsum_add(&sm[k], &c[k], f[k]);
+        }
+        phi[p] = kc * (sm[0] + c[0]);
+        for (k = 0; k < 3; ++k) E[3 * p + k] = kc * (sm[k + 1] + c[k + 1]);
+    }
+    return 0;
+}
