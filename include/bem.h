@@ -122,6 +122,27 @@ int64_t bem_num_elements(const bem_mesh* mesh);
 int bem_set_sigma(bem_mesh* mesh, const double* sigma, void* stream);
 
 /*
+ * bem_set_sigma_linear -- charge densities that vary linearly over each
+ * element.  The paper treats constant densities and notes that the
+ * cubature applies as well to densities that vary over the element
+ * (Sec. 7): each node then carries q_i = w_i area sigma(Q_i).  For element j
+ * with frame coordinates (alpha, beta) of Q - Q_cen = alpha e0 + beta e1
+ * (see bem_rule: triangle alpha = lambda_A - lambda_C, beta = lambda_B -
+ * lambda_C; rectangle the natural coordinates x, y of Eq. 3.2)
+ *   sigma_j(Q) = coef[3j] + coef[3j+1] alpha + coef[3j+2] beta
+ * (a triangle with vertex values sA, sB, sC: coef = (m, sA - m, sB - m),
+ * m = (sA + sB + sC) / 3).  bem_eval, bem_eval_noalloc and the server then
+ * use these densities: the far field with sigma at every node (the rule
+ * bands stay those of constant densities, which costs one polynomial degree
+ * of margin: ~1e-11 relative at the band edges instead of ~1e-15), the near
+ * field by the analytic integral of the linear density.  bem_set_sigma
+ * returns the mesh to constant densities.  bem_assemble and bem_matvec keep
+ * their constant unit / x densities; bem_eval_grad rejects a linear mesh.
+ *   coef [n_el][3], host or device
+ */
+int bem_set_sigma_linear(bem_mesh* mesh, const double* coef, void* stream);
+
+/*
  * bem_eval -- phi and E at n field points (Eq. 2.1 approximated by Eq. 4.1
  * with the rule bands of Sec. 4 and the analytic near field).
  *   points [n][3]  field points

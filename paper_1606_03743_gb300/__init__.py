@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "bem_set_sigma_linear", "linear_coef_from_corner_values", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
@@ -95,6 +95,8 @@ def load_library(build_if_missing: bool = True):
     lib.bem_cancel.argtypes = [vp, C.c_uint64]
     lib.bem_server_pause.argtypes = [vp, C.c_int32]
     lib.bem_server_stats.argtypes = [vp, C.c_int32, d]
+    lib.bem_set_sigma_linear.argtypes = [vp, vp, vp]
+    lib.bem_set_sigma_linear.restype = C.c_int
     lib.bem_eval_grad.argtypes = [vp, vp, C.c_int64, vp, vp]
     lib.bem_eval_grad.restype = C.c_int
     lib.bem_solve.argtypes = [vp, vp, vp, C.POINTER(bem_solve_options), d, vp]
@@ -248,6 +250,29 @@ def bem_matvec(mesh: int, x, y, stream=None) -> None:
     _check(load_library().bem_matvec(mesh, xp, _ptr(y), _stream(stream)))
 
 
+def bem_set_sigma_linear(mesh: int, coef, stream=None) -> None:
+    """Linear densities: coef (n_el, 3) = (sigma at the centroid, d sigma / d alpha, d sigma / d beta)."""
+    cc, cp = _prep(coef, np.float64, (bem_num_elements(mesh), 3))
+    _check(load_library().bem_set_sigma_linear(mesh, cp, _stream(stream)))
+
+
+def linear_coef_from_corner_values(types, values):
+    """(n, 3) coefficients of bem_set_sigma_linear from density values at the
+    corners: triangles (sA, sB, sC) interpolated linearly; rectangles the linear
+    least-squares fit of the four corner values (exact when they lie on a plane:
+    s0 + s2 = s1 + s3)."""
+    types = np.asarray(types)
+    v = np.asarray(values, np.float64).reshape(len(types), -1)
+    out = np.zeros((len(types), 3))
+    tri = types == TRIANGLE
+    m = v[tri, :3].mean(axis=1)
+    out[tri] = np.stack([m, v[tri, 0] - m, v[tri, 1] - m], axis=1)
+    r = ~tri
+    s0, s1, s2, s3 = v[r, 0], v[r, 1], v[r, 2], v[r, 3]  # corners at (x, y) = (-1,-1), (1,-1), (1,1), (-1,1)
+    out[r] = np.stack([(s0 + s1 + s2 + s3) / 4, (s1 + s2 - s0 - s3) / 4, (s2 + s3 - s0 - s1) / 4], axis=1)
+    return out
+
+
 def bem_eval_grad(mesh: int, points, G, stream=None) -> None:
     """Field gradient (n, 6) = (dEx/dx, dEy/dy, dEz/dz, dEx/dy, dEx/dz, dEy/dz) at the points."""
     pp, ptr = _prep(points, np.float64)
@@ -368,6 +393,9 @@ class Mesh:
 
     def set_sigma(self, sigma, stream=None):
         bem_set_sigma(self._h, sigma, stream)
+
+    def set_sigma_linear(self, coef, stream=None):
+        bem_set_sigma_linear(self._h, coef, stream)
 
     def solve(self, rhs, x0=None, restart: int = 0, max_iter: int = 0, tol: float = 0.0, refine: bool = False,
               stream=None):

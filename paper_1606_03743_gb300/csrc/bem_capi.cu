@@ -154,6 +154,7 @@ void free_mesh(bem_mesh* m) {
     cudaFree(d.verts);
     cudaFree(d.type);
     cudaFree(d.sigma);
+    cudaFree(d.slope);
     cudaFree(m->w.cell_cnt);
     cudaFree(m->w.cell_off);
     cudaFree(m->w.counters);
@@ -206,6 +207,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         a.perm = w.perm;
         a.n_pts = n;
         a.sigma = dsigma;
+        a.slope = eval_slope(m, dsigma);
         a.part = w.part;
         a.near_cnt = w.near_cnt;
         a.work = reinterpret_cast<int*>(w.counters + 14);
@@ -221,7 +223,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         if (rc) return rc;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[2], s));
         if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n * m->n_chunks, w.scan_tmp, s))) return rc;
-        if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s))) return rc;
+        if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s, eval_slope(m, dsigma)))) return rc;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[3], s));
         if ((rc = launch_finalize(m, w.perm, n, dphi, dE, stride4, s))) return rc;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[4], s));
@@ -410,6 +412,37 @@ int bem_set_sigma(bem_mesh* m, const double* sigma, void* stream) {
     BEM_CUDA_TRY(cudaSetDevice(m->device));
     BEM_CUDA_TRY(cudaMemcpyAsync(m->d.sigma, sigma, sizeof(double) * m->d.n, cudaMemcpyDefault, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    m->linear = false;
+    return BEM_OK;
+}
+
+int bem_set_sigma_linear(bem_mesh* m, const double* coef, void* stream) {
+    int rc = check_mesh(m, "bem_set_sigma_linear");
+    if (rc) return rc;
+    if (!coef) {
+        set_error("bem_set_sigma_linear: coef is NULL");
+        return BEM_ERR_INVALID;
+    }
+    const size_t n = (size_t)m->d.n;
+    if (n == 0) return BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    if (!m->d.slope) {
+        const cudaError_t e = cudaMalloc((void**)&m->d.slope, sizeof(double) * 2 * n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            m->d.slope = nullptr;
+            set_error("bem_set_sigma_linear: cudaMalloc failed: %s", cudaGetErrorString(e));
+            return BEM_ERR_OOM;
+        }
+    }
+    // (n x 3) -> sigma (n) and slopes (n x 2): strided copies of the columns
+    BEM_CUDA_TRY(cudaMemcpy2DAsync(m->d.sigma, sizeof(double), coef, 3 * sizeof(double), sizeof(double), n,
+                                   cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaMemcpy2DAsync(m->d.slope, 2 * sizeof(double), coef + 1, 3 * sizeof(double),
+                                   2 * sizeof(double), n, cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    m->linear = true;
     return BEM_OK;
 }
 
@@ -609,6 +642,10 @@ extern "C" {
 int bem_eval_grad(bem_mesh* m, const double* points, int64_t n, double* G, void* stream) {
     int rc = check_mesh(m, "bem_eval_grad");
     if (rc) return rc;
+    if (m->linear) {
+        set_error("bem_eval_grad: gradients are provided for constant densities only (bem_set_sigma)");
+        return BEM_ERR_INVALID;
+    }
     if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && (!points || !G))) {
         set_error("bem_eval_grad: bad arguments (n = %lld)", (long long)n);
         return BEM_ERR_INVALID;

@@ -45,7 +45,8 @@ struct MeshDev {
     double* geo = nullptr;    // [n][2] L, area
     double* verts = nullptr;  // [n][12] corners as given
     int* type = nullptr;      // [n]
-    double* sigma = nullptr;  // [n]
+    double* sigma = nullptr;  // [n] (linear density: the value at the centroid)
+    double* slope = nullptr;  // [n][2] linear density: d sigma / d alpha, d sigma / d beta (bem_set_sigma_linear)
 };
 
 // Per-call scratch (grown on demand, owned by the mesh).
@@ -83,6 +84,7 @@ struct bem_mesh {
     double limits[2][5];      // DR band limits per type
     double coord_max = 0.0;   // largest |coordinate| of any element corner
     double grid = 1.0;        // mixed path: spacing (a power of two) of the hi parts of points and centroids
+    bool linear = false;      // densities are linear over the elements (d.slope holds the slopes)
     int n_chunks = 1;         // element chunks of the far-field pass (fixed by the mesh)
     int chunk_len = 0;        // elements per chunk (a multiple of 32)
     size_t budget = 0;
@@ -125,6 +127,7 @@ struct FarArgs {
     const int* perm;     // sorted -> original
     int n_pts;
     const double* sigma; // per element charge density (eval) or the x of a matvec
+    const double* slope; // linear densities: [n][2] slopes, or nullptr (constant densities)
     double4* part;       // out: far sums per (sorted point, chunk)
     double4* part_g;     // gradient pass (FP64 kernel): 6 far sums per (sorted point, chunk), two double4
     int* near_cnt;       // out: near pairs per (sorted point, chunk)
@@ -144,7 +147,11 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s);
 int far_points_per_tile(int precision);
 // Analytic near field over the compacted list and the per-point finalisation (k_near.cu).
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
-                     unsigned long long n_near, cudaStream_t s);
+                     unsigned long long n_near, cudaStream_t s, const double* slope = nullptr);
+// slopes of the mesh's densities for an evaluation with the mesh's own sigma (nullptr if constant)
+inline const double* eval_slope(const bem_mesh* m, const double* sigma) {
+    return (m->linear && sigma == m->d.sigma) ? m->d.slope : nullptr;
+}
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int out_stride4,
                     cudaStream_t s, const int* n_dev = nullptr);
 // fill MeshDev::nodes from the element records (k_far.cu)

@@ -99,6 +99,7 @@ struct FarK {
     const double *cen, *fr, *geo;         // FP64 element data
     const int* type;
     const double* sigma;  // nullptr: unit density (assembly)
+    const double* slope;  // linear densities: [n_el][2] slopes in the element frame, or nullptr
     double4* part;        // per (point, chunk) far sums, [n_pts][n_chunks]
     double4* part_g;      // gradient pass: per (point, chunk) 6 sums as two double4
     int* near_cnt;        // per (point, chunk) near pairs, [n_pts][n_chunks]
@@ -349,6 +350,7 @@ struct WarpSmem {
     R4 e0[32];               // frame e0, w = q (element charge)
     R4 e1[32];               // frame e1; mixed: w = type (int bits)
     R thr[32 * 5];           // squared band limits (tau L)^2
+    R sl[2 * 32];            // linear densities: area x (d sigma / d alpha, d sigma / d beta), else 0
     // mixed: per element, the values each node pass and the field rebuild
     // read, duplicated into (x, x, y, y) pairs for the packed f32x2 arithmetic:
     // -C_hi, -C_lo, e0, e1 (six float4)
@@ -553,6 +555,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     const int ty = p.type[j];
                     const double sg = p.sigma ? p.sigma[j] : 1.0;
                     const double area = p.geo[2 * j + 1];
+                    ws.sl[2 * lane] = p.slope ? (R)(p.slope[2 * j] * area) : (R)0;
+                    ws.sl[2 * lane + 1] = p.slope ? (R)(p.slope[2 * j + 1] * area) : (R)0;
                     R4 c, cl;
                     float th[5];
                     if constexpr (F64) {
@@ -627,8 +631,10 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         const R4 a = ws.e0[e], b = ws.e1[e];
                         for (int i = lane; i < n; i += 32) {
                             const R al = rs.al[st + i], be = rs.be[st + i];
+                            // charge w_i area sigma(Q_i) (linear densities: sigma at the node)
+                            const R qi = fmad(al, ws.sl[2 * e], fmad(be, ws.sl[2 * e + 1], a.w));
                             ws.nd[par][i] = R4{fmad(al, a.x, be * b.x), fmad(al, a.y, be * b.y),
-                                               fmad(al, a.z, be * b.z), rs.w[st + i] * a.w};
+                                               fmad(al, a.z, be * b.z), rs.w[st + i] * qi};
                         }
                         __syncwarp();
                         return n;
@@ -741,7 +747,9 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y),
                                         oz = fmaf(al, f0.z, be * f1.z);
                             const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
-                            const float am = -al, bm = -be, wq = rs.w[st + i] * f0.w;
+                            // charge w_i area sigma(Q_i) (linear densities: sigma at the node)
+                            const float qi = fmaf(al, ws.sl[2 * e], fmaf(be, ws.sl[2 * e + 1], f0.w));
+                            const float am = -al, bm = -be, wq = rs.w[st + i] * qi;
                             ws.nd[par][2 * i] = make_float4(am, am, bm, bm);
                             ws.nd[par][2 * i + 1] = make_float4(oo, oo, wq, wq);
                         }
@@ -1073,7 +1081,9 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.n_el = m->d.n;
     k.work = a.work;
     k.chi = m->d.chi; k.clo = m->d.clo; k.e0f = m->d.e0; k.e1f = m->d.e1;
-    k.nodes = m->precision == kFP64 ? nullptr : m->d.nodes;
+    // the node table's weights carry the element charge as one factor: constant densities only
+    k.nodes = (m->precision == kFP64 || a.slope) ? nullptr : m->d.nodes;
+    k.slope = a.slope;
     k.cen = m->d.cen; k.fr = m->d.fr; k.geo = m->d.geo;
     k.type = m->d.type;
     k.sigma = a.sigma;

@@ -191,11 +191,67 @@ __global__ void k_finalize_grad(int n, int n_chunks, const int* __restrict__ per
     for (int k = 0; k < 6; ++k) G[6 * (size_t)o + k] = kc * s[k];
 }
 
+// phi and E (without 1/(4 pi eps0)) of the polygon with the linear density
+// sigma(Q) = sc + g.(Q - C) (g in the element plane).  With P' the foot of P
+// in the plane (P = P' + h n), w = Q - P' and the constant-density results
+// I0 = int dA / R, E0 (polygon_field):
+//   phi = sigma(P') I0 + g . sum_e m_e (s2 R2 - s1 R1 + rho_e^2 l_e) / 2
+//   E   = sigma(P') E0 - g I0 - h n sum_e (g.m_e) l_e
+//         + sum_e (g.m_e) (d_e l_e m_e + (R2 - R1) t_e)
+// (the in-plane divergence theorem on grad R = w / R, grad (1/R) = -w / R^3
+// and on w / R; rho_e^2 = d_e^2 + h^2 is the squared distance of P from the
+// edge line).
+__device__ void polygon_field_lin(int nv, const double* __restrict__ V, D3 P, double sc, D3 g, D3 C, double out[4]) {
+    double f0[4];
+    polygon_field(nv, V, P, f0);
+    D3 c[4];
+    for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
+    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
+    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    const double h = -dot(c[0], nrm);
+    const D3 Pp = sub(P, scale(nrm, h));
+    const double sP = sc + dot(g, sub(Pp, C));
+    double r[4];
+    for (int k = 0; k < nv; ++k) r[k] = sqrt(dot(c[k], c[k]));
+    double i1 = 0.0, hsum = 0.0;
+    D3 ec = scale(g, -f0[0]);
+    for (int k = 0; k < nv; ++k) {
+        const int k2 = (k + 1 == nv) ? 0 : k + 1;
+        D3 t = sub(c[k2], c[k]);
+        t = scale(t, 1.0 / sqrt(dot(t, t)));
+        const D3 m = cross(t, nrm);
+        const double s1 = dot(c[k], t), s2 = dot(c[k2], t);
+        const double d = dot(c[k], m);
+        double num, den;
+        if (s1 >= 0.0) {
+            num = r[k2] + s2;
+            den = r[k] + s1;
+        } else if (s2 <= 0.0) {
+            num = r[k] - s1;
+            den = r[k2] - s2;
+        } else {
+            num = (r[k2] + s2) * (r[k] - s1);
+            den = fma(d, d, h * h);
+        }
+        const double l = den == 0.0 ? 0.0 : log(num / den);
+        const double gm = dot(g, m);
+        i1 = fma(gm, 0.5 * (s2 * r[k2] - s1 * r[k] + fma(d, d, h * h) * l), i1);
+        hsum = fma(gm, l, hsum);
+        const double a = gm * d * l, b = gm * (r[k2] - r[k]);
+        ec = D3{ec.x + a * m.x + b * t.x, ec.y + a * m.y + b * t.y, ec.z + a * m.z + b * t.z};
+    }
+    out[0] = fma(sP, f0[0], i1);
+    out[1] = fma(sP, f0[1], fma(-h * nrm.x, hsum, ec.x));
+    out[2] = fma(sP, f0[2], fma(-h * nrm.y, hsum, ec.y));
+    out[3] = fma(sP, f0[3], fma(-h * nrm.z, hsum, ec.z));
+}
+
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
                             const double* __restrict__ verts, const double* __restrict__ sigma,
-                            double4* __restrict__ val) {
+                            const double* __restrict__ slope, const double* __restrict__ fr,
+                            const double* __restrict__ cen, double4* __restrict__ val) {
     const unsigned long long n = min(counters[0], cap);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -203,8 +259,23 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
         const int src = perm[r.x];
         const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
         double f[4];
-        polygon_field(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
-        const double sg = sigma[r.y];
+        const int nv = type[r.y] == BEM_RECTANGLE ? 4 : 3;
+        double sg = sigma[r.y];
+        if (slope) {
+            // linear density: g = s_a grad(alpha) + s_b grad(beta), the in-plane duals of e0, e1
+            const double* F = fr + 6 * (size_t)r.y;
+            const D3 e0{F[0], F[1], F[2]}, e1{F[3], F[4], F[5]};
+            const double g00 = dot(e0, e0), g01 = dot(e0, e1), g11 = dot(e1, e1);
+            const double det = g00 * g11 - g01 * g01;
+            const double sa = slope[2 * (size_t)r.y] / det, sb = slope[2 * (size_t)r.y + 1] / det;
+            const double c0 = sa * g11 - sb * g01, c1 = sb * g00 - sa * g01;
+            const D3 g{c0 * e0.x + c1 * e1.x, c0 * e0.y + c1 * e1.y, c0 * e0.z + c1 * e1.z};
+            polygon_field_lin(nv, verts + 12 * (size_t)r.y, P, sg, g,
+                              D3{cen[3 * (size_t)r.y], cen[3 * (size_t)r.y + 1], cen[3 * (size_t)r.y + 2]}, f);
+            sg = 1.0;
+        } else {
+            polygon_field(nv, verts + 12 * (size_t)r.y, P, f);
+        }
         const unsigned long long slot =
             (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
         if (slot < cap) val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
@@ -296,11 +367,12 @@ int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s) {
 }
 
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
-                     unsigned long long /*n_near_hint*/, cudaStream_t s) {
+                     unsigned long long /*n_near_hint*/, cudaStream_t s, const double* slope) {
     (void)n_pts;
     Work& w = m->w;
     k_near_eval<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
-                                        m->n_chunks, m->d.type, m->d.verts, sigma, w.near_val);
+                                        m->n_chunks, m->d.type, m->d.verts, sigma, slope, m->d.fr, m->d.cen,
+                                        w.near_val);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;

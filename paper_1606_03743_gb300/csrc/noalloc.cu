@@ -150,6 +150,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.perm = w.perm;
     a.n_pts = (int)n;
     a.sigma = m->d.sigma;
+    a.slope = eval_slope(m, m->d.sigma);
     a.part = w.part;
     a.near_cnt = w.near_cnt;
     a.work = reinterpret_cast<int*>(w.counters + 14);
@@ -162,7 +163,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
     if ((rc = launch_far(&view, a, s))) return rc;
     if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)n * m->n_chunks, w.scan_tmp, s))) return rc;
-    if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s))) return rc;
+    if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s, eval_slope(m, m->d.sigma)))) return rc;
     if ((rc = launch_finalize(&view, w.perm, (int)n, phi, E, 0, s))) return rc;
     unsigned long long n_near = 0;
     BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters, sizeof n_near, cudaMemcpyDeviceToHost, s));

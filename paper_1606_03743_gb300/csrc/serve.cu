@@ -127,6 +127,7 @@ int enqueue_pipeline(bem_server* sv, Slot& sl) {
     a.n_pts = cap;
     a.n_dev = sl.d_n;
     a.sigma = m->d.sigma;
+    a.slope = eval_slope(m, m->d.sigma);
     a.part = w.part;
     a.near_cnt = w.near_cnt;
     a.work = reinterpret_cast<int*>(w.counters + 14);
@@ -138,7 +139,7 @@ int enqueue_pipeline(bem_server* sv, Slot& sl) {
     a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
     if ((rc = launch_far(m, a, s))) return rc;
     if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, ns, w.scan_tmp, s))) return rc;
-    if ((rc = launch_near_eval(m, sl.d_pts, w.perm, cap, m->d.sigma, 0, s))) return rc;
+    if ((rc = launch_near_eval(m, sl.d_pts, w.perm, cap, m->d.sigma, 0, s, eval_slope(m, m->d.sigma)))) return rc;
     return launch_finalize(m, w.perm, cap, sl.d_phi, sl.d_E, 0, s, sl.d_n);
 }
 
