@@ -395,6 +395,32 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
                              "max_rel_err_vs_oracle": float(gerr.max()), "oracle_points": ngo,
                              "max_rel_trace": float((np.abs(Gg[:, :3].sum(1)) / np.abs(Gg).max(axis=1)).max())}
 
+    # ---- linear densities over the elements (the same mesh, sigma varying by up to 30 % across each element)
+    coef = np.stack([mesh.sigma, *(np.random.default_rng(31).normal(0.0, 0.15, (2, mesh.n)) * mesh.sigma)], axis=1)
+    m.set_sigma_linear(coef)
+    lphi = torch.empty(a.points, dtype=torch.float64, device=dev)
+    lE = torch.empty((a.points, 3), dtype=torch.float64, device=dev)
+    p_all = torch.from_numpy(pts).to(dev)
+    bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
+    t0.record(stream)
+    bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    msl = t0.elapsed_time(t1)
+    m.set_sigma(mesh.sigma)
+    nlo = 512
+    lref_phi, lref_E = oracle.eval_linear(mesh.types, mesh.verts, coef, pts[:nlo], nthreads=nt)
+    gl_phi, gl_E = lphi[:nlo].cpu().numpy(), lE[:nlo].cpu().numpy()
+    far = mdr[:nlo] >= 3
+    kap = (esum / np.linalg.norm(rE, axis=1))[:nlo]
+    sel = far & (kap <= 100)
+    out["linear_density"] = {
+        "value": a.points * mesh.n / (msl * 1e-3), "unit": UNIT, "ms": msl, "precision": a.precision,
+        "density": "sigma = s_c + s_a alpha + s_b beta per element, s_a, s_b ~ N(0, 0.15 s_c)",
+        "max_rel_phi_vs_oracle": float((np.abs(gl_phi - lref_phi) / np.abs(lref_phi))[sel].max()),
+        "max_rel_E_vs_oracle": float((np.linalg.norm(gl_E - lref_E, axis=1) / np.linalg.norm(lref_E, axis=1))[sel].max()),
+        "oracle_points": nlo, "gate_points": "min DR >= 3 and kappa (constant density) <= 100"}
+
     out["accuracy_vs_oracle"] = accuracy_report(gphi, gE, g64phi[:k], g64E[:k], rphi, rE, mdr, esum)
     out["accuracy_vs_oracle"]["run_precision"] = a.precision
     out["accuracy_vs_oracle"]["points"] = ns
