@@ -73,6 +73,10 @@ constexpr int kPtMixed = BEM_MIXED_PT, kPtFp64 = BEM_FP64_PT;
 #define BEM_NODE_UNROLL 4
 #endif
 constexpr int kNodeUnroll = BEM_NODE_UNROLL;
+// rules with at most this many nodes get fully unrolled node loops
+#ifndef BEM_FULL_UNROLL_MAX
+#define BEM_FULL_UNROLL_MAX 12
+#endif
 // mixed path: elements per FP32 sum before it moves into the hi + lo running sums (a power of two)
 #ifndef BEM_FLUSH
 #define BEM_FLUSH 8
@@ -315,8 +319,13 @@ template <int N, int NP, bool WANT_E, bool INIT>
 __device__ __forceinline__ void nodes2_n(const float4* __restrict__ nd, const float2 (&s)[NP],
                                          const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
     if (INIT) node2<NP, WANT_E, true>(nd[0], nd[1], s, u, v, acc);
+    if constexpr (N <= BEM_FULL_UNROLL_MAX) {
+#pragma unroll
+        for (int i = INIT ? 1 : 0; i < N; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+    } else {
 #pragma unroll kNodeUnroll
-    for (int i = INIT ? 1 : 0; i < N; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+        for (int i = INIT ? 1 : 0; i < N; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+    }
 }
 
 // All n nodes of one rule: the node counts of the paper's rules (App. A, B)
