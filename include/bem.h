@@ -304,7 +304,7 @@ int64_t bem_kernel_launches(void);
  */
 #define BEM_NOALLOC_MAX_POINTS 16384
 #define BEM_NOALLOC_MAX_NEAR 262144
-#define BEM_NOALLOC_BYTES (24u << 20)
+#define BEM_NOALLOC_BYTES (40u << 20)
 int bem_eval_noalloc(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
 
 /* ------------------------------------------------------------------------

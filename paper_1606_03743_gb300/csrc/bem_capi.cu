@@ -311,10 +311,9 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     }
     m->d.n = (int)n;
     // the far-field pass splits the elements into chunks fixed by the mesh
-    // (so a point's sum is always split the same way): at least ~2500
-    // elements each, at most 16 chunks, enough work items to fill the GPU
-    // even for a few thousand points
-    m->n_chunks = (int)std::min<int64_t>(16, std::max<int64_t>(1, (n + 2499) / 2500));
+    // (so a point's sum is always split the same way): enough work items to
+    // fill the GPU even for a few thousand points
+    m->n_chunks = (int)std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, (n + kChunkMinElements - 1) / kChunkMinElements));
     m->chunk_len = (int)(((n + m->n_chunks - 1) / m->n_chunks + 31) / 32 * 32);
     m->n_chunks = (int)((n + m->chunk_len - 1) / m->chunk_len);
     MeshDev& d = m->d;

@@ -31,6 +31,19 @@ __host__ __device__ inline int band_rule(int band) { return 5 - band; }
 // Structure of arrays, one entry per element, element order as given.
 constexpr int kTableSlots = 75;  // node records per element in the node table (4 + 7 + 12 + 19 + 33)
 
+// Element chunks of the far-field pass (fixed per mesh, so that a point's
+// sum is always split the same way): at least kChunkMinElements elements
+// each, at most kMaxChunks; more chunks give small point batches more work
+// items to fill the GPU with.
+#ifndef BEM_MAX_CHUNKS
+#define BEM_MAX_CHUNKS 32
+#endif
+#ifndef BEM_CHUNK_MIN
+#define BEM_CHUNK_MIN 625
+#endif
+constexpr int kMaxChunks = BEM_MAX_CHUNKS;
+constexpr int kChunkMinElements = BEM_CHUNK_MIN;
+
 struct MeshDev {
     int n = 0;
     // mixed path records (float4, 64 B per element)

@@ -87,6 +87,11 @@ static_assert((kFlush & (kFlush - 1)) == 0 && kFlush <= 32, "flush interval: a p
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
 constexpr int kWarps = 4;     // warps per CTA
 constexpr int kNodeBuf = 36;  // node records per buffer (33 used at most)
+constexpr int kAsmGroup = 4;  // mixed assembly: elements per staged group (a 32-byte row segment)
+// assembly work items per resident warp (elements are chunked finely enough for this many)
+#ifndef BEM_ASM_ITEMS
+#define BEM_ASM_ITEMS 32
+#endif
 
 __constant__ float c_alpha_f[2 * kSlots], c_beta_f[2 * kSlots], c_w_f[2 * kSlots];
 __constant__ double c_alpha_d[2 * kSlots], c_beta_d[2 * kSlots], c_w_d[2 * kSlots];
@@ -352,9 +357,13 @@ __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, con
 }
 
 // Shared memory of one warp.
-template <typename R, typename R4, int PT, bool ACC64>
+template <typename R, typename R4, int PT, bool ACC64, bool ATILE = false>
 struct WarpSmem {
     static constexpr bool kMixed = sizeof(R) == 4;
+    // mixed assembly: kc x potential of kAsmGroup elements for the warp's points, written out
+    // as short contiguous row segments; and the matrix row of each point of the tile
+    double at[ATILE ? kAsmGroup * PT * 32 : 1];
+    int rows[ATILE ? PT * 32 : 1];
     R4 c[kMixed ? 1 : 32];   // FP64: centroid, w = type
     R4 e0[32];               // frame e0, w = q (element charge)
     R4 e1[32];               // frame e1; mixed: w = type (int bits)
@@ -383,7 +392,7 @@ constexpr size_t far_smem_bytes() {
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
     constexpr bool ACC64 = !F64 && MODE == 0;
-    return ((sizeof(RuleSmem<R>) + 15) / 16) * 16 + kWarps * sizeof(WarpSmem<R, R4, PT, ACC64>);
+    return ((sizeof(RuleSmem<R>) + 15) / 16) * 16 + kWarps * sizeof(WarpSmem<R, R4, PT, ACC64, !F64 && MODE == 1>);
 }
 
 // ------------------------------------------------------------ the kernel
@@ -403,7 +412,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
     constexpr bool ACC64 = !F64 && MODE == 0;  // running sums in shared memory (mixed evaluation)
-    using WS = WarpSmem<R, R4, PT, ACC64>;
+    constexpr bool ATILE = !F64 && MODE == 1;  // mixed assembly: row segments staged in shared memory
+    using WS = WarpSmem<R, R4, PT, ACC64, ATILE>;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RuleSmem<R>& rs = *reinterpret_cast<RuleSmem<R>*>(smem_raw);
@@ -552,6 +562,11 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             for (int c = 0; c < 4; ++c) acc8[k][c] = make_float2(0.0f, 0.0f);
 
         const int el0 = chunk * p.chunk_len, el1 = min(p.n_el, el0 + p.chunk_len);
+        if constexpr (ATILE) {
+#pragma unroll
+            for (int q = 0; q < PT; ++q) ws.rows[q * 32 + lane] = valid[q] ? p.perm[sidx[q]] : -1;
+            __syncwarp();
+        }
         int par = 0;    // node buffer parity
         int pre_n = 0;  // node table: node count of the next element's records already in flight
         for (int b0 = el0; b0 < el1; b0 += 32) {
@@ -901,13 +916,28 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         }
                     }
                     if constexpr (MODE == 1) {
-                        // assembly: one potential per pair, times 1/(4 pi eps0); near pairs are filled later
+                        // assembly: one potential per pair, times 1/(4 pi eps0), staged for a group
+                        // of kAsmGroup elements and written as row segments (near pairs are
+                        // filled later)
+                        const int g = e & (kAsmGroup - 1);
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
-                            if (valid[2 * k])
-                                p.A[(size_t)p.perm[sidx[2 * k]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[k][0].x;
-                            if (valid[2 * k + 1])
-                                p.A[(size_t)p.perm[sidx[2 * k + 1]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[k][0].y;
+                            ws.at[g * (PT * 32) + (2 * k) * 32 + lane] = p.kc * (double)eacc[k][0].x;
+                            ws.at[g * (PT * 32) + (2 * k + 1) * 32 + lane] = p.kc * (double)eacc[k][0].y;
+                        }
+                        if (g == kAsmGroup - 1 || e == nb - 1) {
+                            __syncwarp();
+                            const int gn = g + 1, col0 = b0 + e - g;
+                            // lane l: point slot 8 j + l / 4, column l % 4 of the group
+                            const int sub = lane & (kAsmGroup - 1);
+#pragma unroll 4
+                            for (int j = 0; j < PT * 32 / 8; ++j) {
+                                const int ps = j * 8 + (lane >> 2);
+                                const int row = ws.rows[ps];
+                                if (row >= 0 && sub < gn)
+                                    p.A[(size_t)row * p.n_el + (col0 + sub)] = ws.at[sub * (PT * 32) + ps];
+                            }
+                            __syncwarp();
                         }
                     }
                 }
@@ -1119,7 +1149,7 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     const int n_tiles = (a.n_pts + tile - 1) / tile;
     if (a.A) {
         // assembly has no reduction over elements: cut them finely enough to fill the GPU
-        const int chunks = (152 * 16 * 2 + n_tiles - 1) / n_tiles;
+        const int chunks = (152 * 16 * BEM_ASM_ITEMS + n_tiles - 1) / n_tiles;
         int len = (m->d.n + chunks - 1) / chunks;
         len = ((len + 31) / 32) * 32;
         k.chunk_len = len;

@@ -25,7 +25,7 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 
 constexpr size_t kMaxPts = BEM_NOALLOC_MAX_POINTS;
 constexpr size_t kMaxNear = BEM_NOALLOC_MAX_NEAR;
-constexpr size_t kMaxChunks = 16;      // element chunks of the far-field pass (at most 16 per mesh)
+constexpr size_t kChunksCap = kMaxChunks;  // element chunks of the far-field pass (at most kMaxChunks per mesh)
 constexpr size_t kCellsMax = 32768;    // the sort uses at most 2^(3*5) cells for <= 2^14 points
 constexpr size_t kScanInts = 16384;    // block sums of every scan level, with room to spare
 
@@ -35,9 +35,9 @@ constexpr size_t kOffKey = kOffPerm + align_up(4 * kMaxPts);
 constexpr size_t kOffCellCnt = kOffKey + align_up(4 * kMaxPts);
 constexpr size_t kOffCellOff = kOffCellCnt + align_up(4 * kCellsMax);
 constexpr size_t kOffPart = kOffCellOff + align_up(4 * kCellsMax);
-constexpr size_t kOffNearCnt = kOffPart + align_up(32 * kMaxPts * kMaxChunks);
-constexpr size_t kOffNearOff = kOffNearCnt + align_up(4 * kMaxPts * kMaxChunks);
-constexpr size_t kOffScan = kOffNearOff + align_up(4 * kMaxPts * kMaxChunks);
+constexpr size_t kOffNearCnt = kOffPart + align_up(32 * kMaxPts * kChunksCap);
+constexpr size_t kOffNearOff = kOffNearCnt + align_up(4 * kMaxPts * kChunksCap);
+constexpr size_t kOffScan = kOffNearOff + align_up(4 * kMaxPts * kChunksCap);
 constexpr size_t kOffRec = kOffScan + align_up(4 * kScanInts);
 constexpr size_t kOffVal = kOffRec + align_up(16 * kMaxNear);
 constexpr size_t kOffCounters = kOffVal + align_up(32 * kMaxNear);
@@ -128,7 +128,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     w.bbox = reinterpret_cast<float4*>(base + kOffBbox);
     view.stats = false;
     view.timing = false;
-    if (m->n_chunks > (int)kMaxChunks || scan_tmp_ints((int)(kMaxPts * kMaxChunks)) > kScanInts ||
+    if (m->n_chunks > (int)kChunksCap || scan_tmp_ints((int)(kMaxPts * kChunksCap)) > kScanInts ||
         scan_tmp_ints((int)kCellsMax) > kScanInts) {
         set_error("bem_eval_noalloc: internal scan scratch too small");
         return BEM_ERR_CAPACITY;
