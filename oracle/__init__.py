@@ -68,6 +68,10 @@ def _load():
         lib.oracle_max_threads.restype = C.c_int
         lib.oracle_element_batch.argtypes = [C.c_int64, i32, d, d, C.c_int, C.c_int, d, d, i32, C.c_int]
         lib.oracle_element_batch.restype = C.c_int
+        lib.oracle_element_quad.argtypes = [C.c_int, d, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
+        lib.oracle_element_quad.restype = C.c_int
+        lib.oracle_eval_quad.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d, C.c_int]
+        lib.oracle_eval_quad.restype = C.c_int
         lib.oracle_element_linear.argtypes = [C.c_int, d, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
         lib.oracle_element_linear.restype = C.c_int
         lib.oracle_eval_linear.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d, C.c_int]
@@ -175,6 +179,42 @@ def eval_linear(types, verts, coef, pts, limits=None, eps0: float = 0.0, nthread
                                     nthreads or max_threads())
     if rc != 0:
         raise ValueError("oracle_eval_linear: bad arguments")
+    return phi, E
+
+
+def element_quad(type_: int, verts, coef, P, method: int = METHOD_PAPER, param: int = 0, limits=None):
+    """phi, E of one element with the quadratic density sigma = c0 + c1 alpha + c2 beta
+    + c3 alpha^2 + c4 alpha beta + c5 beta^2 (coef = c0..c5), WITHOUT 1/(4 pi eps0)."""
+    v = np.zeros((4, 3))
+    vv = np.asarray(verts, float).reshape(-1, 3)
+    v[: vv.shape[0]] = vv
+    P = _f64(P, (3,))
+    cf = _f64(coef, (6,))
+    lim = None if limits is None else _f64(limits, (10,))
+    out = np.zeros(4)
+    band = C.c_int(-1)
+    rc = _load().oracle_element_quad(type_, _dp(v), _dp(cf), _dp(P), method, param, _dp(lim), _dp(out),
+                                     C.byref(band))
+    if rc != 0:
+        raise ValueError("oracle_element_quad: bad arguments")
+    return out, band.value
+
+
+def eval_quad(types, verts, coef, pts, limits=None, eps0: float = 0.0, nthreads: int | None = None):
+    """phi (n,), E (n, 3) of elements with quadratic densities coef (n_el, 6), by the
+    method, including 1/(4 pi eps0)."""
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    verts = _f64(verts, (types.shape[0], 4, 3))
+    coef = _f64(coef, (types.shape[0], 6))
+    pts = _f64(pts).reshape(-1, 3)
+    phi = np.zeros(pts.shape[0])
+    E = np.zeros((pts.shape[0], 3))
+    lim = None if limits is None else _f64(limits, (10,))
+    rc = _load().oracle_eval_quad(types.shape[0], types.ctypes.data_as(C.POINTER(C.c_int32)), _dp(verts),
+                                  _dp(coef), _dp(lim), eps0, pts.shape[0], _dp(pts), _dp(phi), _dp(E),
+                                  nthreads or max_threads())
+    if rc != 0:
+        raise ValueError("oracle_eval_quad: bad arguments")
     return phi, E
 
 

@@ -1011,6 +1011,7 @@ int oracle_eval_grad(int64_t n_el, const int32_t* type, const double* verts, con
 /* ------------------------------------------------------------------ */
 typedef struct {
     double sc, g[3], C[3];
+    double H[3][3]; /* quadratic densities: the in-plane Hessian (0 for linear ones) */
 } lin_t;
 
 static void linear_density(const elem_t* e, const double* coef, lin_t* s)
@@ -1039,13 +1040,54 @@ static void linear_density(const elem_t* e, const double* coef, lin_t* s)
         s->g[k] = coef[1] * d0[k] + coef[2] * d1[k];
         s->C[k] = e->cen[k];
     }
+    memset(s->H, 0, sizeof s->H);
+}
+
+/* quadratic density sigma = c0 + c1 alpha + c2 beta + c3 alpha^2 + c4 alpha beta
+ * + c5 beta^2: with grad(alpha) = d0, grad(beta) = d1 the Hessian in space is
+ * H = 2 c3 d0 d0^T + c4 (d0 d1^T + d1 d0^T) + 2 c5 d1 d1^T */
+static void quadratic_density(const elem_t* e, const double* coef, lin_t* s)
+{
+    double e0[3], e1[3], g00, g01, g11, det, d0[3], d1[3];
+    int a, b;
+    linear_density(e, coef, s);
+    if (e->type == 0) {
+        sub3(e->v[0], e->cen, e0);
+        sub3(e->v[1], e->cen, e1);
+    } else {
+        for (a = 0; a < 3; ++a) {
+            e0[a] = 0.5 * e->a * e->ux[a];
+            e1[a] = 0.5 * e->b * e->uy[a];
+        }
+    }
+    g00 = dot3(e0, e0);
+    g01 = dot3(e0, e1);
+    g11 = dot3(e1, e1);
+    det = g00 * g11 - g01 * g01;
+    for (a = 0; a < 3; ++a) {
+        d0[a] = (g11 * e0[a] - g01 * e1[a]) / det;
+        d1[a] = (g00 * e1[a] - g01 * e0[a]) / det;
+    }
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b)
+            s->H[a][b] = 2.0 * coef[3] * d0[a] * d0[b] + coef[4] * (d0[a] * d1[b] + d1[a] * d0[b]) +
+                         2.0 * coef[5] * d1[a] * d1[b];
+}
+
+static double quad_form(const double H[3][3], const double x[3], const double y[3])
+{
+    int a, b;
+    double r = 0.0;
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b) r += x[a] * H[a][b] * y[b];
+    return r;
 }
 
 static double lin_sigma(const lin_t* s, const double Q[3])
 {
     double d[3];
     sub3(Q, s->C, d);
-    return s->sc + dot3(s->g, d);
+    return s->sc + dot3(s->g, d) + 0.5 * quad_form(s->H, d, d);
 }
 
 /* Eq. 4.1 with q_i = w_i area sigma(Q_i) */
@@ -1270,6 +1312,178 @@ int oracle_eval_linear(int64_t n_el, const int32_t* type, const double* verts, c
             linear_density(&e, coef + 3 * jj, &s);
             band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], NULL);
             if (band == 0) analytic_field_lin(&e, P, &s, f);
+            else cubature_field_lin(&e, band - 1, P, &s, f);
+            for (k = 0; k < 4; ++k) nsum_add(&sm[k], &c[k], f[k]);
+        }
+        phi[p] = kc * (sm[0] + c[0]);
+        for (k = 0; k < 3; ++k) E[3 * p + k] = kc * (sm[k + 1] + c[k + 1]);
+    }
+    return 0;
+}
+
+/* Analytic near field for the quadratic density sigma(Q) = sigma(P') + g·w +
+ * w^T H w / 2 (w = Q - P', P' the foot of P in the plane, g and H the
+ * gradient and Hessian there).  Besides the integrals of the linear case:
+ *   int w w^T / R dA   = sum_e (d_e J_e m_e + (R2^3 - R1^3)/3 t_e) m_e^T - Pi int R dA
+ *   int R dA           = (sum_e d_e J_e + h^2 I0) / 3,      J_e = int_e R ds
+ *   int (w^T H w) w / R^3 dA = 2 H int w / R dA - sum_e m_e int_e (w^T H w) / R ds
+ *   int_e (w^T H w) / R ds = d_e^2 m^T H m l_e + 2 d_e m^T H t (R2 - R1)
+ *                            + t^T H t (s2 R2 - s1 R1 - rho_e^2 l_e) / 2
+ * (the in-plane divergence theorem on w R, w_i w_j / R and the edge
+ * parametrisation w = d_e m_e + u t_e), so that
+ *   phi = sigma(P') I0 + g·I1 + (H : I2) / 2
+ *   E   = sigma(P') E0 + [h n (g·K1) - K2 g] + [h n (H : K2) - T] / 2
+ * with I1 = int w / R, I2 = int w w^T / R, K1 = int w / R^3, K2 = int w w^T / R^3,
+ * T = int (w^T H w) w / R^3 (all dA). */
+static void analytic_field_quad(const elem_t* e, const double P[3], const lin_t* s, double out[4])
+{
+    const int nv = e->type == 0 ? 3 : 4;
+    double f0[4], n[3], e1[3], e2[3], nl, h, Pp[3], dl[3], sP, g[3], I1[3] = {0, 0, 0};
+    double K2[3][3], I2[3][3], Qm[3] = {0, 0, 0}, sumdJ = 0.0, hsum = 0.0, intR, HI2 = 0.0, HK2 = 0.0, T[3];
+    int k, j, a, b;
+    analytic_field(e, P, f0);
+    sub3(e->v[1], e->v[0], e1);
+    sub3(e->v[2], e->v[0], e2);
+    cross3(e1, e2, n);
+    nl = norm3(n);
+    for (k = 0; k < 3; ++k) n[k] /= nl;
+    {
+        double pv[3];
+        sub3(P, e->v[0], pv);
+        h = dot3(pv, n);
+    }
+    for (k = 0; k < 3; ++k) Pp[k] = P[k] - h * n[k];
+    sub3(Pp, s->C, dl);
+    sP = s->sc + dot3(s->g, dl) + 0.5 * quad_form(s->H, dl, dl);
+    for (a = 0; a < 3; ++a) {
+        g[a] = s->g[a];
+        for (b = 0; b < 3; ++b) g[a] += s->H[a][b] * dl[b];
+    }
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b) {
+            const double pi = (a == b ? 1.0 : 0.0) - n[a] * n[b];
+            K2[a][b] = pi * f0[0];
+            I2[a][b] = 0.0;
+        }
+    for (j = 0; j < nv; ++j) {
+        const double* V1 = e->v[j];
+        const double* V2 = e->v[(j + 1) % nv];
+        double t[3], m[3], r1[3], r2[3], len, s1, s2, R1, R2, d, perp2, l, J, wR[3], cub, Qe;
+        sub3(V2, V1, t);
+        len = norm3(t);
+        for (k = 0; k < 3; ++k) t[k] /= len;
+        cross3(t, n, m);
+        sub3(V1, P, r1);
+        sub3(V2, P, r2);
+        s1 = dot3(r1, t);
+        s2 = dot3(r2, t);
+        R1 = norm3(r1);
+        R2 = norm3(r2);
+        d = dot3(r1, m);
+        perp2 = d * d + h * h;
+        l = edge_log(s1, s2, R1, R2, perp2);
+        J = 0.5 * (s2 * R2 - s1 * R1 + perp2 * l);
+        for (k = 0; k < 3; ++k) I1[k] += m[k] * J;
+        sumdJ += d * J;
+        for (k = 0; k < 3; ++k) wR[k] = d * l * m[k] + (R2 - R1) * t[k];
+        cub = (R2 * R2 * R2 - R1 * R1 * R1) / 3.0;
+        for (a = 0; a < 3; ++a)
+            for (b = 0; b < 3; ++b) {
+                K2[a][b] -= wR[a] * m[b];
+                I2[a][b] += (d * J * m[a] + cub * t[a]) * m[b];
+            }
+        Qe = d * d * quad_form(s->H, m, m) * l + 2.0 * d * quad_form(s->H, m, t) * (R2 - R1) +
+             quad_form(s->H, t, t) * 0.5 * (s2 * R2 - s1 * R1 - perp2 * l);
+        for (k = 0; k < 3; ++k) Qm[k] += m[k] * Qe;
+        hsum += dot3(g, m) * l;
+    }
+    intR = (sumdJ + h * h * f0[0]) / 3.0;
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b) {
+            I2[a][b] -= ((a == b ? 1.0 : 0.0) - n[a] * n[b]) * intR;
+            HI2 += s->H[a][b] * I2[a][b];
+            HK2 += s->H[a][b] * K2[a][b];
+        }
+    for (a = 0; a < 3; ++a) {
+        T[a] = -Qm[a];
+        for (b = 0; b < 3; ++b) T[a] += 2.0 * s->H[a][b] * I1[b];
+    }
+    out[0] = sP * f0[0] + dot3(g, I1) + 0.5 * HI2;
+    for (a = 0; a < 3; ++a) {
+        double Kg = 0.0;
+        for (b = 0; b < 3; ++b) Kg += K2[a][b] * g[b];
+        out[a + 1] = sP * f0[a + 1] - h * n[a] * hsum - Kg + 0.5 * (h * n[a] * HK2 - T[a]);
+    }
+}
+
+/* phi and E of ONE element with the quadratic density coef = (c0, ..., c5),
+ * sigma = c0 + c1 alpha + c2 beta + c3 alpha^2 + c4 alpha beta + c5 beta^2,
+ * without 1/(4 pi eps0); methods as oracle_element */
+int oracle_element_quad(int type, const double* verts, const double* coef, const double* P, int method, int param,
+                        const double* limits, double* out /* 4 */, int* band_out)
+{
+    elem_t e;
+    lin_t s;
+    int band = -1;
+    build_rules();
+    elem_setup(&e, type, verts);
+    quadratic_density(&e, coef, &s);
+    switch (method) {
+    case OR_METHOD_PAPER:
+        band = choose_band(&e, P, limits ? limits + 5 * type : DEFAULT_LIMITS[type], NULL);
+        if (band == 0) analytic_field_quad(&e, P, &s, out);
+        else cubature_field_lin(&e, band - 1, P, &s, out);
+        break;
+    case OR_METHOD_GL2:
+        if (param < 1 || param > NGL_MAX) return -1;
+        gl2_field_lin(&e, param, P, &s, out);
+        break;
+    case OR_METHOD_ANALYTIC:
+        analytic_field_quad(&e, P, &s, out);
+        break;
+    case OR_METHOD_RULE:
+        if (param < 0 || param > 4) return -1;
+        cubature_field_lin(&e, param, P, &s, out);
+        break;
+    case OR_METHOD_SUBDIV:
+        if (param < 0 || param > 12) return -1;
+        subdiv_field_lin(&e, param, 16, P, &s, out);
+        break;
+    default:
+        return -1;
+    }
+    if (band_out) *band_out = band;
+    return 0;
+}
+
+/* phi and E at n_pts points for elements with quadratic densities coef
+ * (n_el x 6), by the method, summed in index order, times 1/(4 pi eps0) */
+int oracle_eval_quad(int64_t n_el, const int32_t* type, const double* verts, const double* coef,
+                     const double* limits, double eps0, int64_t n_pts, const double* pts, double* phi, double* E,
+                     int nthreads)
+{
+    const double kc = coulomb_k(eps0);
+    int64_t p, j;
+    build_rules();
+    if (n_el < 0 || n_pts < 0) return -1;
+    for (j = 0; j < n_el; ++j)
+        if (type[j] != 0 && type[j] != 1) return -1;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (p = 0; p < n_pts; ++p) {
+        const double* P = pts + 3 * p;
+        double sm[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+        int64_t jj;
+        int k;
+        for (jj = 0; jj < n_el; ++jj) {
+            elem_t e;
+            lin_t s;
+            double f[4];
+            int band;
+            elem_setup(&e, type[jj], verts + 12 * jj);
+            quadratic_density(&e, coef + 6 * jj, &s);
+            band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], NULL);
+            if (band == 0) analytic_field_quad(&e, P, &s, f);
             else cubature_field_lin(&e, band - 1, P, &s, f);
             for (k = 0; k < 4; ++k) nsum_add(&sm[k], &c[k], f[k]);
         }
