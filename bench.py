@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-assembly", action="store_true", help="skip the collocation-assembly measurement")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-large", action="store_true", help="skip the 500k-element x 4M-point mixed vs FP64 run")
-    ap.add_argument("--grad-points", type=int, default=16384, help="points of the field-gradient line")
+    ap.add_argument("--grad-points", type=int, default=16384, help="points of the FP64 field-gradient line")
+    ap.add_argument("--grad-points-mixed", type=int, default=262144, help="points of the mixed field-gradient line")
     ap.add_argument("--large-points", type=int, default=4_000_000)
     ap.add_argument("--large-fp64-points", type=int, default=32768)
     ap.add_argument("--large-oracle-points", type=int, default=2048)
@@ -374,52 +375,69 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     g64E = f64E.cpu().numpy()
     k = min(ns, n64)
 
-    # ---- field gradient (FP64 far kernel in its gradient mode + analytic near field)
-    ng = min(a.grad_points, a.points)
-    pg = torch.from_numpy(pts[:ng]).to(dev)
-    Gd = torch.empty((ng, 6), dtype=torch.float64, device=dev)
-    bem.bem_eval_grad(m.handle, pg, Gd, stream=stream.cuda_stream)
-    t0.record(stream)
-    bem.bem_eval_grad(m.handle, pg, Gd, stream=stream.cuda_stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    msg = t0.elapsed_time(t1)
-    ngo = min(ng, 512)
+    # ---- field gradient: the far kernel's gradient modes (FP64 mesh and mixed mesh) + analytic near field
+    ngo = min(a.grad_points, a.points, 512)
     t0c = time.perf_counter()
     Gref = oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, pts[:ngo], nthreads=nt)
     cpu_g = time.perf_counter() - t0c
-    Gg = Gd[:ngo].cpu().numpy()
-    gerr = np.abs(Gg - Gref).max(axis=1) / np.abs(Gref).max(axis=1)
-    out["field_gradient"] = {"value": ng * mesh.n / (msg * 1e-3), "unit": UNIT, "n_points": ng, "ms": msg,
-                             "precision": "f64", "oracle_pairs_per_s": ngo * mesh.n / cpu_g,
-                             "max_rel_err_vs_oracle": float(gerr.max()), "oracle_points": ngo,
-                             "max_rel_trace": float((np.abs(Gg[:, :3].sum(1)) / np.abs(Gg).max(axis=1)).max())}
+    grads = {}
+    for gkey, gmesh, ng in (("f64", m64, min(a.grad_points, a.points)),
+                            ("mixed", m, min(a.grad_points_mixed, a.points))):
+        pg = torch.from_numpy(pts[:ng]).to(dev)
+        Gd = torch.empty((ng, 6), dtype=torch.float64, device=dev)
+        bem.bem_eval_grad(gmesh.handle, pg, Gd, stream=stream.cuda_stream)
+        t0.record(stream)
+        bem.bem_eval_grad(gmesh.handle, pg, Gd, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        msg = t0.elapsed_time(t1)
+        Gg = Gd[:ngo].cpu().numpy()
+        gerr = np.abs(Gg - Gref).max(axis=1) / np.abs(Gref).max(axis=1)
+        gsel = mdr[:ngo] >= 3
+        grads[gkey] = {"value": ng * mesh.n / (msg * 1e-3), "unit": UNIT, "n_points": ng, "ms": msg,
+                       "max_rel_err_vs_oracle": float(gerr[gsel].max()),
+                       "max_rel_err_vs_oracle_all": float(gerr.max()),
+                       "max_rel_trace": float((np.abs(Gg[:, :3].sum(1)) / np.abs(Gg).max(axis=1)).max())}
+        del Gd, pg
+    out["field_gradient"] = {**grads, "oracle_pairs_per_s": ngo * mesh.n / cpu_g, "oracle_points": ngo,
+                             "error": "max over points of max |dG| / max |G| (components); gated: min DR >= 3",
+                             "mixed_over_f64": grads["mixed"]["value"] / grads["f64"]["value"]}
 
-    # ---- linear densities over the elements (the same mesh, sigma varying by up to 30 % across each element)
-    coef = np.stack([mesh.sigma, *(np.random.default_rng(31).normal(0.0, 0.15, (2, mesh.n)) * mesh.sigma)], axis=1)
-    m.set_sigma_linear(coef)
+    # ---- varying densities over the elements (the same mesh): linear, sigma varying by up to ~30 %
+    # across each element, and quadratic, with second-order terms of a few per cent on top
+    rng_d = np.random.default_rng(31)
+    lin = np.stack([mesh.sigma, *(rng_d.normal(0.0, 0.15, (2, mesh.n)) * mesh.sigma)], axis=1)
+    quad = np.concatenate([lin, (rng_d.normal(0.0, 0.05, (3, mesh.n)) * mesh.sigma).T], axis=1)
+    varying = [("linear_density", lin, m.set_sigma_linear, oracle.eval_linear,
+                "sigma = s_c + s_a alpha + s_b beta per element, s_a, s_b ~ N(0, 0.15 s_c)"),
+               ("quadratic_density", quad, m.set_sigma_quadratic, oracle.eval_quad,
+                "sigma = c0 + c1 alpha + c2 beta + c3 alpha^2 + c4 alpha beta + c5 beta^2, "
+                "c1, c2 ~ N(0, 0.15 c0), c3, c4, c5 ~ N(0, 0.05 c0)")]
     lphi = torch.empty(a.points, dtype=torch.float64, device=dev)
     lE = torch.empty((a.points, 3), dtype=torch.float64, device=dev)
     p_all = torch.from_numpy(pts).to(dev)
-    bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
-    t0.record(stream)
-    bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    msl = t0.elapsed_time(t1)
-    m.set_sigma(mesh.sigma)
     nlo = 512
-    lref_phi, lref_E = oracle.eval_linear(mesh.types, mesh.verts, coef, pts[:nlo], nthreads=nt)
-    gl_phi, gl_E = lphi[:nlo].cpu().numpy(), lE[:nlo].cpu().numpy()
     far = mdr[:nlo] >= 3
     kap = (esum / np.linalg.norm(rE, axis=1))[:nlo]
     sel = far & (kap <= 100)
-    out["linear_density"] = {
-        "value": a.points * mesh.n / (msl * 1e-3), "unit": UNIT, "ms": msl, "precision": a.precision,
-        "density": "sigma = s_c + s_a alpha + s_b beta per element, s_a, s_b ~ N(0, 0.15 s_c)",
-        "max_rel_phi_vs_oracle": float((np.abs(gl_phi - lref_phi) / np.abs(lref_phi))[sel].max()),
-        "max_rel_E_vs_oracle": float((np.linalg.norm(gl_E - lref_E, axis=1) / np.linalg.norm(lref_E, axis=1))[sel].max()),
-        "oracle_points": nlo, "gate_points": "min DR >= 3 and kappa (constant density) <= 100"}
+    for key, coef, setter, ref_fn, desc in varying:
+        setter(coef)
+        bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
+        t0.record(stream)
+        bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        msl = t0.elapsed_time(t1)
+        m.set_sigma(mesh.sigma)
+        lref_phi, lref_E = ref_fn(mesh.types, mesh.verts, coef, pts[:nlo], nthreads=nt)
+        gl_phi, gl_E = lphi[:nlo].cpu().numpy(), lE[:nlo].cpu().numpy()
+        out[key] = {
+            "value": a.points * mesh.n / (msl * 1e-3), "unit": UNIT, "ms": msl, "precision": a.precision,
+            "density": desc,
+            "max_rel_phi_vs_oracle": float((np.abs(gl_phi - lref_phi) / np.abs(lref_phi))[sel].max()),
+            "max_rel_E_vs_oracle": float((np.linalg.norm(gl_E - lref_E, axis=1)
+                                          / np.linalg.norm(lref_E, axis=1))[sel].max()),
+            "oracle_points": nlo, "gate_points": "min DR >= 3 and kappa (constant density) <= 100"}
 
     out["accuracy_vs_oracle"] = accuracy_report(gphi, gE, g64phi[:k], g64E[:k], rphi, rE, mdr, esum)
     out["accuracy_vs_oracle"]["run_precision"] = a.precision

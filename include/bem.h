@@ -143,6 +143,21 @@ int bem_set_sigma(bem_mesh* mesh, const double* sigma, void* stream);
 int bem_set_sigma_linear(bem_mesh* mesh, const double* coef, void* stream);
 
 /*
+ * bem_set_sigma_quadratic -- charge densities that vary quadratically over
+ * each element (the varying densities of Sec. 7, one order above
+ * bem_set_sigma_linear), in the same frame coordinates:
+ *   sigma_j(Q) = c0 + c1 alpha + c2 beta + c3 alpha^2 + c4 alpha beta + c5 beta^2,
+ *   (c0 .. c5) = coef[6j .. 6j+5]
+ * The far field takes sigma at every node (the constant-density rule bands
+ * now lose two polynomial degrees of margin: up to ~1e-8 relative in E at the
+ * edge of the 4-point rule's band), the near field the analytic integral of the
+ * quadratic density.  bem_set_sigma or bem_set_sigma_linear replaces it;
+ * bem_assemble, bem_matvec and bem_eval_grad behave as for a linear mesh.
+ *   coef [n_el][6], host or device
+ */
+int bem_set_sigma_quadratic(bem_mesh* mesh, const double* coef, void* stream);
+
+/*
  * bem_eval -- phi and E at n field points (Eq. 2.1 approximated by Eq. 4.1
  * with the rule bands of Sec. 4 and the analytic near field).
  *   points [n][3]  field points
@@ -162,8 +177,12 @@ int bem_eval(bem_mesh* mesh, const double* points, int64_t n, double* phi, doubl
  * charge q_i adds q_i (delta_ij / r^3 - 3 r_i r_j / r^5), with the same rule
  * bands as bem_eval; below the near limit the analytic gradient of the
  * uniformly charged polygon is used (the derivative of the near-field
- * formula: edge line fields and the gradient of the solid angle).  Always
- * evaluated in FP64, whatever the mesh's precision.
+ * formula: edge line fields and the gradient of the solid angle).  The far
+ * sums take the mesh's precision: FP64, or on a mixed mesh FP32 node terms
+ * (the point-centroid difference split as in bem_eval) with per-element
+ * sums b, c, c alpha, c beta, c alpha^2, c alpha beta, c beta^2 (b = q_i / r^3,
+ * c = q_i / r^5) from which the element's tensor is formed, summed as FP32
+ * hi + lo pairs (~1e-6 relative, as the mixed field); near pairs are FP64.
  *   points [n][3]
  *   G      [n][6]  (dEx/dx, dEy/dy, dEz/dz, dEx/dy, dEx/dz, dEy/dz) in V/m^2;
  *                  the tensor is symmetric and, off the elements, traceless

@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "bem_set_sigma_linear", "linear_coef_from_corner_values", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "bem_set_sigma_linear", "bem_set_sigma_quadratic", "linear_coef_from_corner_values", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
@@ -97,6 +97,8 @@ def load_library(build_if_missing: bool = True):
     lib.bem_server_stats.argtypes = [vp, C.c_int32, d]
     lib.bem_set_sigma_linear.argtypes = [vp, vp, vp]
     lib.bem_set_sigma_linear.restype = C.c_int
+    lib.bem_set_sigma_quadratic.argtypes = [vp, vp, vp]
+    lib.bem_set_sigma_quadratic.restype = C.c_int
     lib.bem_eval_grad.argtypes = [vp, vp, C.c_int64, vp, vp]
     lib.bem_eval_grad.restype = C.c_int
     lib.bem_solve.argtypes = [vp, vp, vp, C.POINTER(bem_solve_options), d, vp]
@@ -256,6 +258,13 @@ def bem_set_sigma_linear(mesh: int, coef, stream=None) -> None:
     _check(load_library().bem_set_sigma_linear(mesh, cp, _stream(stream)))
 
 
+def bem_set_sigma_quadratic(mesh: int, coef, stream=None) -> None:
+    """Quadratic densities: coef (n_el, 6), sigma = c0 + c1 alpha + c2 beta + c3 alpha^2
+    + c4 alpha beta + c5 beta^2 in the element's frame coordinates."""
+    cc, cp = _prep(coef, np.float64, (bem_num_elements(mesh), 6))
+    _check(load_library().bem_set_sigma_quadratic(mesh, cp, _stream(stream)))
+
+
 def linear_coef_from_corner_values(types, values):
     """(n, 3) coefficients of bem_set_sigma_linear from density values at the
     corners: triangles (sA, sB, sC) interpolated linearly; rectangles the linear
@@ -396,6 +405,9 @@ class Mesh:
 
     def set_sigma_linear(self, coef, stream=None):
         bem_set_sigma_linear(self._h, coef, stream)
+
+    def set_sigma_quadratic(self, coef, stream=None):
+        bem_set_sigma_quadratic(self._h, coef, stream)
 
     def solve(self, rhs, x0=None, restart: int = 0, max_iter: int = 0, tol: float = 0.0, refine: bool = False,
               stream=None):

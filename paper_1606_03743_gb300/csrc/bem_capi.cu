@@ -155,6 +155,7 @@ void free_mesh(bem_mesh* m) {
     cudaFree(d.type);
     cudaFree(d.sigma);
     cudaFree(d.slope);
+    cudaFree(d.curv);
     cudaFree(m->w.cell_cnt);
     cudaFree(m->w.cell_off);
     cudaFree(m->w.counters);
@@ -412,6 +413,7 @@ int bem_set_sigma(bem_mesh* m, const double* sigma, void* stream) {
     BEM_CUDA_TRY(cudaMemcpyAsync(m->d.sigma, sigma, sizeof(double) * m->d.n, cudaMemcpyDefault, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
     m->linear = false;
+    m->quadratic = false;
     return BEM_OK;
 }
 
@@ -442,6 +444,43 @@ int bem_set_sigma_linear(bem_mesh* m, const double* coef, void* stream) {
                                    2 * sizeof(double), n, cudaMemcpyDefault, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
     m->linear = true;
+    m->quadratic = false;
+    return BEM_OK;
+}
+
+int bem_set_sigma_quadratic(bem_mesh* m, const double* coef, void* stream) {
+    int rc = check_mesh(m, "bem_set_sigma_quadratic");
+    if (rc) return rc;
+    if (!coef) {
+        set_error("bem_set_sigma_quadratic: coef is NULL");
+        return BEM_ERR_INVALID;
+    }
+    const size_t n = (size_t)m->d.n;
+    if (n == 0) return BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    BEM_CUDA_TRY(cudaSetDevice(m->device));
+    double** bufs[2] = {&m->d.slope, &m->d.curv};
+    const size_t cols[2] = {2, 3};
+    for (int b = 0; b < 2; ++b) {
+        if (*bufs[b]) continue;
+        const cudaError_t e = cudaMalloc((void**)bufs[b], sizeof(double) * cols[b] * n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *bufs[b] = nullptr;
+            set_error("bem_set_sigma_quadratic: cudaMalloc failed: %s", cudaGetErrorString(e));
+            return BEM_ERR_OOM;
+        }
+    }
+    // (n x 6) -> sigma (n), slopes (n x 2) and second-order coefficients (n x 3)
+    BEM_CUDA_TRY(cudaMemcpy2DAsync(m->d.sigma, sizeof(double), coef, 6 * sizeof(double), sizeof(double), n,
+                                   cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaMemcpy2DAsync(m->d.slope, 2 * sizeof(double), coef + 1, 6 * sizeof(double),
+                                   2 * sizeof(double), n, cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaMemcpy2DAsync(m->d.curv, 3 * sizeof(double), coef + 3, 6 * sizeof(double),
+                                   3 * sizeof(double), n, cudaMemcpyDefault, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    m->linear = true;
+    m->quadratic = true;
     return BEM_OK;
 }
 
@@ -574,7 +613,7 @@ struct Scratch {
     }
 };
 
-// One slice of bem_eval_grad: the FP64 far kernel in its gradient mode, the
+// One slice of bem_eval_grad: the far kernel in its gradient mode (the mesh's precision), the
 // compacted near pairs' analytic gradients, the per-point sums.
 int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStream_t s) {
     int rc;

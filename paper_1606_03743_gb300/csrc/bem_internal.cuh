@@ -60,6 +60,7 @@ struct MeshDev {
     int* type = nullptr;      // [n]
     double* sigma = nullptr;  // [n] (linear density: the value at the centroid)
     double* slope = nullptr;  // [n][2] linear density: d sigma / d alpha, d sigma / d beta (bem_set_sigma_linear)
+    double* curv = nullptr;   // [n][3] quadratic density: the alpha^2, alpha beta, beta^2 coefficients
 };
 
 // Per-call scratch (grown on demand, owned by the mesh).
@@ -98,6 +99,7 @@ struct bem_mesh {
     double coord_max = 0.0;   // largest |coordinate| of any element corner
     double grid = 1.0;        // mixed path: spacing (a power of two) of the hi parts of points and centroids
     bool linear = false;      // densities are linear over the elements (d.slope holds the slopes)
+    bool quadratic = false;   // ... and quadratic (d.curv holds the second-order coefficients)
     int n_chunks = 1;         // element chunks of the far-field pass (fixed by the mesh)
     int chunk_len = 0;        // elements per chunk (a multiple of 32)
     size_t budget = 0;
@@ -164,6 +166,10 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
 // slopes of the mesh's densities for an evaluation with the mesh's own sigma (nullptr if constant)
 inline const double* eval_slope(const bem_mesh* m, const double* sigma) {
     return (m->linear && sigma == m->d.sigma) ? m->d.slope : nullptr;
+}
+// second-order coefficients that go with the slopes of an evaluation (nullptr unless quadratic)
+inline const double* eval_curv(const bem_mesh* m, const double* slope) {
+    return (slope && m->quadratic) ? m->d.curv : nullptr;
 }
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int out_stride4,
                     cudaStream_t s, const int* n_dev = nullptr);

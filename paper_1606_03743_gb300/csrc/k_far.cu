@@ -68,6 +68,10 @@ namespace bem {
 #define BEM_FP64_PT 2
 #endif
 constexpr int kPtMixed = BEM_MIXED_PT, kPtFp64 = BEM_FP64_PT;
+#ifndef BEM_GRAD_PT
+#define BEM_GRAD_PT 2
+#endif
+constexpr int kPtGradMixed = BEM_GRAD_PT;  // mixed gradient: seven sums per point pair and node
 // node-loop unroll depth
 #ifndef BEM_NODE_UNROLL
 #define BEM_NODE_UNROLL 4
@@ -109,6 +113,7 @@ struct FarK {
     const int* type;
     const double* sigma;  // nullptr: unit density (assembly)
     const double* slope;  // linear densities: [n_el][2] slopes in the element frame, or nullptr
+    const double* curv;   // quadratic densities: [n_el][3] alpha^2, alpha beta, beta^2 coefficients, or nullptr
     double4* part;        // per (point, chunk) far sums, [n_pts][n_chunks]
     double4* part_g;      // gradient pass: per (point, chunk) 6 sums as two double4
     int* near_cnt;        // per (point, chunk) near pairs, [n_pts][n_chunks]
@@ -290,15 +295,40 @@ __device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
 // rsqrt gives +0 and its terms are exact zeros, while the other points'
 // arithmetic is bit-for-bit that of a pass without it.  INIT: the sums start
 // from this term.
-template <int NP, bool WANT_E, bool INIT>
+//
+// GRAD (field gradient): acc[k] = (sum b, sum c, -sum c alpha, -sum c beta,
+// sum c alpha^2, sum c alpha beta, sum c beta^2) with c = b / r^2 = w q / r^5,
+// from which the rebuild forms sum q (I / r^3 - 3 r r^T / r^5) with
+// r = d - alpha e0 - beta e1.
+template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
 __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const float2 (&s)[NP],
-                                      const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
+                                      const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
     const float2 al = make_float2(ab.x, ab.y), be = make_float2(ab.z, ab.w);
     const float2 oo = make_float2(ow.x, ow.y), w = make_float2(ow.z, ow.w);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const float2 r2 = fma2(al, u[k], fma2(be, v[k], add2(s[k], oo)));
         const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        if constexpr (GRAD) {
+            static_assert(NS == 7, "gradient sums");
+            const float2 i2 = mul2(inv, inv);
+            const float2 b = mul2(mul2(w, inv), i2);  // q_i / r_i^3
+            const float2 c = mul2(b, i2);             // q_i / r_i^5
+            const float2 ca = mul2(c, al), cb = mul2(c, be);
+            if (INIT) {
+                acc[k][0] = b; acc[k][1] = c; acc[k][2] = ca; acc[k][3] = cb;
+                acc[k][4] = mul2(ca, al); acc[k][5] = mul2(ca, be); acc[k][6] = mul2(cb, be);
+            } else {
+                acc[k][0] = add2(acc[k][0], b);
+                acc[k][1] = add2(acc[k][1], c);
+                acc[k][2] = add2(acc[k][2], ca);
+                acc[k][3] = add2(acc[k][3], cb);
+                acc[k][4] = fma2(ca, al, acc[k][4]);
+                acc[k][5] = fma2(ca, be, acc[k][5]);
+                acc[k][6] = fma2(cb, be, acc[k][6]);
+            }
+            continue;
+        }
         const float2 a = mul2(w, inv);  // q_i / r_i
         if (INIT) {
             acc[k][0] = a;
@@ -320,44 +350,46 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
 
 // All N nodes of one rule (two records per node in nd, broadcast reads),
 // with the trip count known at compile time.
-template <int N, int NP, bool WANT_E, bool INIT>
+template <int N, int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
 __device__ __forceinline__ void nodes2_n(const float4* __restrict__ nd, const float2 (&s)[NP],
-                                         const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
-    if (INIT) node2<NP, WANT_E, true>(nd[0], nd[1], s, u, v, acc);
+                                         const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
+    if (INIT) node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], s, u, v, acc);
     if constexpr (N <= BEM_FULL_UNROLL_MAX) {
 #pragma unroll
-        for (int i = INIT ? 1 : 0; i < N; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+        for (int i = INIT ? 1 : 0; i < N; ++i)
+            node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
     } else {
 #pragma unroll kNodeUnroll
-        for (int i = INIT ? 1 : 0; i < N; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+        for (int i = INIT ? 1 : 0; i < N; ++i)
+            node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
     }
 }
 
 // All n nodes of one rule: the node counts of the paper's rules (App. A, B)
 // get their own compiled loops.
-template <int NP, bool WANT_E, bool INIT>
+template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
 __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
-                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][4]) {
+                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
     switch (n) {
-        case 4: nodes2_n<4, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
-        case 7: nodes2_n<7, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
-        case 12: nodes2_n<12, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
-        case 17: nodes2_n<17, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
-        case 19: nodes2_n<19, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
-        case 33: nodes2_n<33, NP, WANT_E, INIT>(nd, s, u, v, acc); return;
+        case 4: nodes2_n<4, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
+        case 7: nodes2_n<7, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
+        case 12: nodes2_n<12, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
+        case 17: nodes2_n<17, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
+        case 19: nodes2_n<19, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
+        case 33: nodes2_n<33, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
         default: break;
     }
     int i = 0;
     if (INIT) {  // every rule has at least four nodes
-        node2<NP, WANT_E, true>(nd[0], nd[1], s, u, v, acc);
+        node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], s, u, v, acc);
         i = 1;
     }
 #pragma unroll 1
-    for (; i < n; ++i) node2<NP, WANT_E, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+    for (; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
 }
 
 // Shared memory of one warp.
-template <typename R, typename R4, int PT, bool ACC64, bool ATILE = false>
+template <typename R, typename R4, int PT, int NACC, bool ATILE = false>
 struct WarpSmem {
     static constexpr bool kMixed = sizeof(R) == 4;
     // mixed assembly: kc x potential of kAsmGroup elements for the warp's points, written out
@@ -375,9 +407,10 @@ struct WarpSmem {
     float4 pr[kMixed ? 32 * 6 : 1];
 
     R4 nd[2][kMixed ? 2 * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: two)
-    // mixed evaluation: per point pair, component and lane, the running sum as an
-    // unevaluated FP32 pair hi + lo (hi.x, hi.y, lo.x, lo.y)
-    float4 accdf[ACC64 ? (PT / 2) * 4 * 32 : 1];
+    // mixed evaluation (NACC = 4: phi, E) and gradient (NACC = 6): per point pair,
+    // component and lane, the running sum as an unevaluated FP32 pair hi + lo
+    // (hi.x, hi.y, lo.x, lo.y)
+    float4 accdf[NACC ? (PT / 2) * NACC * 32 : 1];
 };
 
 template <typename R>
@@ -391,29 +424,39 @@ template <bool F64, int PT, bool WANT_E, int MODE>
 constexpr size_t far_smem_bytes() {
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
-    constexpr bool ACC64 = !F64 && MODE == 0;
-    return ((sizeof(RuleSmem<R>) + 15) / 16) * 16 + kWarps * sizeof(WarpSmem<R, R4, PT, ACC64, !F64 && MODE == 1>);
+    constexpr int NACC = F64 ? 0 : MODE == 0 ? 4 : MODE == 3 ? 6 : 0;
+    return ((sizeof(RuleSmem<R>) + 15) / 16) * 16 + kWarps * sizeof(WarpSmem<R, R4, PT, NACC, !F64 && MODE == 1>);
 }
 
 // ------------------------------------------------------------ the kernel
 // MODE 0: evaluation (sum over elements); MODE 1: assembly (one value per
 // (point, element) pair written to A, potential only, sigma = 1); MODE 2
-// (FP64 only): field gradient sums.
+// (FP64) and MODE 3 (mixed): field gradient sums.
 // STATS: count pairs per (type, band) into counters[2 + 6 type + band], and
 // into counters[16..18] the (warp, element) pairs that ran one band for the
 // whole warp, those that fell back to per-point bands, and the node
 // evaluations executed (lanes x points x nodes, masked ones included).
+// VAR: 0 constant densities, nodes formed on the fly; 1 the node table
+// (BEM_FLAG_NODE_TABLE); 2 linear / quadratic densities (sigma at every node,
+// formed on the fly).  Each variant carries only its own expansion code: the
+// kernel is large enough for extra code to cost instruction-fetch stalls.
 // CTAs per SM the register allocation must allow (4 x 4 warps)
 #ifndef BEM_MIN_BLOCKS
 #define BEM_MIN_BLOCKS 4
 #endif
-template <bool F64, int PT, bool WANT_E, int MODE, bool STATS, bool PRE>
+template <bool F64, int PT, bool WANT_E, int MODE, bool STATS, int VAR>
 __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK p) {
+    constexpr bool PRE = VAR == 1, VARY = VAR == 2;
     using R = typename std::conditional<F64, double, float>::type;
     using R4 = typename std::conditional<F64, double4, float4>::type;
-    constexpr bool ACC64 = !F64 && MODE == 0;  // running sums in shared memory (mixed evaluation)
+    // running sums in shared memory (mixed evaluation: phi, E; mixed gradient: 6 components)
+    constexpr int NACC = F64 ? 0 : MODE == 0 ? 4 : MODE == 3 ? 6 : 0;
     constexpr bool ATILE = !F64 && MODE == 1;  // mixed assembly: row segments staged in shared memory
-    using WS = WarpSmem<R, R4, PT, ACC64, ATILE>;
+    static_assert(MODE != 3 || !F64, "MODE 3 is the mixed gradient");
+    static_assert(MODE != 2 || F64, "MODE 2 is the FP64 gradient");
+    constexpr bool GRAD3 = MODE == 3;
+    constexpr int NE = GRAD3 ? 7 : 4;  // per-element sums of a point pair (mixed path)
+    using WS = WarpSmem<R, R4, PT, NACC, ATILE>;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RuleSmem<R>& rs = *reinterpret_cast<RuleSmem<R>*>(smem_raw);
@@ -539,7 +582,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         // ---- accumulators
         R acc[F64 ? PT : 1][4];  // FP64 evaluation: the running sums
         R accg[MODE == 2 ? PT : 1][6];  // gradient pass: the running sums
-        float2 acc8[NP][4];      // mixed: FP32 sum of up to 8 element sums (point pairs)
+        constexpr int NA = GRAD3 ? 6 : 4;
+        float2 acc8[NP][NA];  // mixed: FP32 sum of up to 8 element results (point pairs)
         int ncnt[PT];
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
@@ -552,14 +596,14 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 for (int c = 0; c < 6; ++c) accg[q][c] = (R)0;
             }
         }
-        if constexpr (ACC64) {
+        if constexpr (NACC > 0) {
 #pragma unroll
-            for (int k = 0; k < NP * 4; ++k) ws.accdf[k * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int k = 0; k < NP * NACC; ++k) ws.accdf[k * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc8[k][c] = make_float2(0.0f, 0.0f);
+            for (int c = 0; c < NA; ++c) acc8[k][c] = make_float2(0.0f, 0.0f);
 
         const int el0 = chunk * p.chunk_len, el1 = min(p.n_el, el0 + p.chunk_len);
         if constexpr (ATILE) {
@@ -579,8 +623,10 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     const int ty = p.type[j];
                     const double sg = p.sigma ? p.sigma[j] : 1.0;
                     const double area = p.geo[2 * j + 1];
-                    ws.sl[2 * lane] = p.slope ? (R)(p.slope[2 * j] * area) : (R)0;
-                    ws.sl[2 * lane + 1] = p.slope ? (R)(p.slope[2 * j + 1] * area) : (R)0;
+                    if constexpr (VARY) {
+                        ws.sl[2 * lane] = (R)(p.slope[2 * j] * area);
+                        ws.sl[2 * lane + 1] = (R)(p.slope[2 * j + 1] * area);
+                    }
                     R4 c, cl;
                     float th[5];
                     if constexpr (F64) {
@@ -653,10 +699,22 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     auto expand = [&](int r) -> int {
                         const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
                         const R4 a = ws.e0[e], b = ws.e1[e];
+                        R ca = (R)0, cb = (R)0, cc = (R)0;
+                        if (VARY && p.curv) {  // quadratic densities: area x second-order coefficients
+                            const size_t j = (size_t)(b0 + e);
+                            const double ar = p.geo[2 * j + 1];
+                            ca = (R)(p.curv[3 * j] * ar);
+                            cb = (R)(p.curv[3 * j + 1] * ar);
+                            cc = (R)(p.curv[3 * j + 2] * ar);
+                        }
                         for (int i = lane; i < n; i += 32) {
                             const R al = rs.al[st + i], be = rs.be[st + i];
-                            // charge w_i area sigma(Q_i) (linear densities: sigma at the node)
-                            const R qi = fmad(al, ws.sl[2 * e], fmad(be, ws.sl[2 * e + 1], a.w));
+                            // charge w_i area sigma(Q_i) (linear / quadratic densities: sigma at the node)
+                            R qi = a.w;
+                            if constexpr (VARY) {
+                                qi = fmad(al, ws.sl[2 * e], fmad(be, ws.sl[2 * e + 1], qi));
+                                if (p.curv) qi = fmad(al, fmad(al, ca, be * cb), fmad(be * be, cc, qi));
+                            }
                             ws.nd[par][i] = R4{fmad(al, a.x, be * b.x), fmad(al, a.y, be * b.y),
                                                fmad(al, a.z, be * b.z), rs.w[st + i] * qi};
                         }
@@ -761,18 +819,30 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             vv[k] = add2(v, v);
                         }
                     }
-                    float2 eacc[NP][4];  // this element's sums (started by its first rule pass)
+                    float2 eacc[NP][NE];  // this element's sums (started by its first rule pass)
                     // expand rule r of element e into the free node buffer (lane i: node i)
                     auto expand = [&](int r) -> int {
                         const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
                         const float4 f0 = ws.e0[e], f1 = ws.e1[e];
+                        float ca = 0.0f, cb = 0.0f, cc = 0.0f;
+                        if (VARY && p.curv) {  // quadratic densities: area x second-order coefficients
+                            const size_t j = (size_t)(b0 + e);
+                            const double ar = p.geo[2 * j + 1];
+                            ca = (float)(p.curv[3 * j] * ar);
+                            cb = (float)(p.curv[3 * j + 1] * ar);
+                            cc = (float)(p.curv[3 * j + 2] * ar);
+                        }
                         for (int i = lane; i < n; i += 32) {
                             const float al = rs.al[st + i], be = rs.be[st + i];
                             const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y),
                                         oz = fmaf(al, f0.z, be * f1.z);
                             const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
-                            // charge w_i area sigma(Q_i) (linear densities: sigma at the node)
-                            const float qi = fmaf(al, ws.sl[2 * e], fmaf(be, ws.sl[2 * e + 1], f0.w));
+                            // charge w_i area sigma(Q_i) (linear / quadratic densities: sigma at the node)
+                            float qi = f0.w;
+                            if constexpr (VARY) {
+                                qi = fmaf(al, ws.sl[2 * e], fmaf(be, ws.sl[2 * e + 1], qi));
+                                if (p.curv) qi = fmaf(al, fmaf(al, ca, be * cb), fmaf(be * be, cc, qi));
+                            }
                             const float am = -al, bm = -be, wq = rs.w[st + i] * qi;
                             ws.nd[par][2 * i] = make_float4(am, am, bm, bm);
                             ws.nd[par][2 * i + 1] = make_float4(oo, oo, wq, wq);
@@ -811,7 +881,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         } else {
                             n = expand(band_rule(cd));
                         }
-                        nodes2<NP, WANT_E, true>(ws.nd[par], n, sv, uv, vv, eacc);
+                        nodes2<NP, WANT_E, GRAD3, true>(ws.nd[par], n, sv, uv, vv, eacc);
                         par ^= 1;
                         if (STATS && lane == 0) {
                             atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -841,7 +911,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
                         for (int k = 0; k < NP; ++k)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) eacc[k][j] = make_float2(0.0f, 0.0f);  // near-only points
+                            for (int j = 0; j < NE; ++j) eacc[k][j] = make_float2(0.0f, 0.0f);  // near-only points
 #pragma unroll 1
                         for (int band = 1; band <= 5; ++band) {
                             if (!(mask & (1u << band))) continue;
@@ -860,7 +930,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             } else {
                                 n = expand(band_rule(band));
                             }
-                            nodes2<NP, WANT_E, false>(ws.nd[par], n, sm, uv, vv, eacc);
+                            nodes2<NP, WANT_E, GRAD3, false>(ws.nd[par], n, sm, uv, vv, eacc);
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                         }
@@ -907,6 +977,57 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
                                 for (int j = 0; j < 4; ++j) {
                                     float4& slot = ws.accdf[(k * 4 + j) * 32 + lane];
+                                    const float4 v = slot;
+                                    float2 hi = make_float2(v.x, v.y), lo = make_float2(v.z, v.w);
+                                    two_sum_add(hi, lo, acc8[k][j]);
+                                    slot = make_float4(hi.x, hi.y, lo.x, lo.y);
+                                    acc8[k][j] = make_float2(0.0f, 0.0f);
+                                }
+                        }
+                    }
+                    if constexpr (GRAD3) {
+                        // the element's gradient sum q (I / r^3 - 3 r r^T / r^5), r = d - alpha e0 -
+                        // beta e1: with M = C0 d + Ca e0 + Cb e1, N0 = Ca d + Caa e0 + Cab e1,
+                        // N1 = Cb d + Cab e0 + Cbb e1 (C the sums of node2, Ca = -sum c alpha, ...)
+                        // it is B I - 3 (M d^T + N0 e0^T + N1 e1^T)
+                        const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
+                        const float2 h0x = lo2(r3), h0y = hi2(r3), h0z = lo2(r4);
+                        const float2 h1x = hi2(r4), h1y = lo2(r5), h1z = hi2(r5);
+                        const float2 m3 = make_float2(-3.0f, -3.0f);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) {
+                            float2 dx, dy, dz;
+                            diff(k, dx, dy, dz);
+                            const float2* c = eacc[k];
+                            const float2 mx = fma2(c[1], dx, fma2(c[2], h0x, mul2(c[3], h1x)));
+                            const float2 my = fma2(c[1], dy, fma2(c[2], h0y, mul2(c[3], h1y)));
+                            const float2 mz = fma2(c[1], dz, fma2(c[2], h0z, mul2(c[3], h1z)));
+                            const float2 ax = fma2(c[2], dx, fma2(c[4], h0x, mul2(c[5], h1x)));
+                            const float2 ay = fma2(c[2], dy, fma2(c[4], h0y, mul2(c[5], h1y)));
+                            const float2 az = fma2(c[2], dz, fma2(c[4], h0z, mul2(c[5], h1z)));
+                            const float2 bx = fma2(c[3], dx, fma2(c[5], h0x, mul2(c[6], h1x)));
+                            const float2 by = fma2(c[3], dy, fma2(c[5], h0y, mul2(c[6], h1y)));
+                            const float2 bz = fma2(c[3], dz, fma2(c[5], h0z, mul2(c[6], h1z)));
+                            // (xx, yy, zz, xy, xz, yz)
+                            const float2 txx = fma2(mx, dx, fma2(ax, h0x, mul2(bx, h1x)));
+                            const float2 tyy = fma2(my, dy, fma2(ay, h0y, mul2(by, h1y)));
+                            const float2 tzz = fma2(mz, dz, fma2(az, h0z, mul2(bz, h1z)));
+                            const float2 txy = fma2(mx, dy, fma2(ax, h0y, mul2(bx, h1y)));
+                            const float2 txz = fma2(mx, dz, fma2(ax, h0z, mul2(bx, h1z)));
+                            const float2 tyz = fma2(my, dz, fma2(ay, h0z, mul2(by, h1z)));
+                            acc8[k][0] = add2(acc8[k][0], fma2(m3, txx, c[0]));
+                            acc8[k][1] = add2(acc8[k][1], fma2(m3, tyy, c[0]));
+                            acc8[k][2] = add2(acc8[k][2], fma2(m3, tzz, c[0]));
+                            acc8[k][3] = fma2(m3, txy, acc8[k][3]);
+                            acc8[k][4] = fma2(m3, txz, acc8[k][4]);
+                            acc8[k][5] = fma2(m3, tyz, acc8[k][5]);
+                        }
+                        if (((b0 + e) & (kFlush - 1)) == kFlush - 1 || e == nb - 1) {
+#pragma unroll
+                            for (int k = 0; k < NP; ++k)
+#pragma unroll
+                                for (int j = 0; j < 6; ++j) {
+                                    float4& slot = ws.accdf[(k * 6 + j) * 32 + lane];
                                     const float4 v = slot;
                                     float2 hi = make_float2(v.x, v.y), lo = make_float2(v.z, v.w);
                                     two_sum_add(hi, lo, acc8[k][j]);
@@ -965,13 +1086,23 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 p.near_cnt[slot] = ncnt[q];
             }
         }
-        if constexpr (MODE == 2) {
+        if constexpr (MODE == 2 || MODE == 3) {
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
                 if (!valid[q]) continue;
+                double g6[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    if constexpr (MODE == 2) {
+                        g6[j] = accg[q][j];
+                    } else {
+                        const float4 v = ws.accdf[((q >> 1) * 6 + j) * 32 + lane];
+                        g6[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+                    }
+                }
                 const size_t slot = (size_t)sidx[q] * p.n_chunks + chunk;
-                p.part_g[2 * slot] = make_double4(accg[q][0], accg[q][1], accg[q][2], accg[q][3]);
-                p.part_g[2 * slot + 1] = make_double4(accg[q][4], accg[q][5], 0.0, 0.0);
+                p.part_g[2 * slot] = make_double4(g6[0], g6[1], g6[2], g6[3]);
+                p.part_g[2 * slot + 1] = make_double4(g6[4], g6[5], 0.0, 0.0);
                 p.near_cnt[slot] = ncnt[q];
             }
         }
@@ -1046,10 +1177,10 @@ int upload_rules(int dev) {
     return BEM_OK;
 }
 
-template <bool F64, int PT, bool WANT_E, int MODE, bool STATS, bool PRE>
+template <bool F64, int PT, bool WANT_E, int MODE, bool STATS, int VAR>
 int launch_one(const FarK& k, cudaStream_t s) {
     constexpr size_t sm = far_smem_bytes<F64, PT, WANT_E, MODE>();
-    auto fn = k_far<F64, PT, WANT_E, MODE, STATS, PRE>;
+    auto fn = k_far<F64, PT, WANT_E, MODE, STATS, VAR>;
     static int per_sm = 0, sms = 0;  // per instantiation
     if (!per_sm) {
         BEM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1070,13 +1201,18 @@ int launch_one(const FarK& k, cudaStream_t s) {
 
 template <bool F64, int PT, bool WANT_E, int MODE>
 int launch_stats(const FarK& k, cudaStream_t s, bool stats) {
-    if constexpr (!F64) {
+    if constexpr (!F64 && MODE != 3) {
         if (k.nodes)
-            return stats ? launch_one<F64, PT, WANT_E, MODE, true, true>(k, s)
-                         : launch_one<F64, PT, WANT_E, MODE, false, true>(k, s);
+            return stats ? launch_one<F64, PT, WANT_E, MODE, true, 1>(k, s)
+                         : launch_one<F64, PT, WANT_E, MODE, false, 1>(k, s);
     }
-    return stats ? launch_one<F64, PT, WANT_E, MODE, true, false>(k, s)
-                 : launch_one<F64, PT, WANT_E, MODE, false, false>(k, s);
+    if constexpr (MODE == 0) {  // linear / quadratic densities: evaluation only
+        if (k.slope)
+            return stats ? launch_one<F64, PT, WANT_E, MODE, true, 2>(k, s)
+                         : launch_one<F64, PT, WANT_E, MODE, false, 2>(k, s);
+    }
+    return stats ? launch_one<F64, PT, WANT_E, MODE, true, 0>(k, s)
+                 : launch_one<F64, PT, WANT_E, MODE, false, 0>(k, s);
 }
 
 // Node records of every rule for every element (BEM_FLAG_NODE_TABLE): thread
@@ -1121,8 +1257,9 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.work = a.work;
     k.chi = m->d.chi; k.clo = m->d.clo; k.e0f = m->d.e0; k.e1f = m->d.e1;
     // the node table's weights carry the element charge as one factor: constant densities only
-    k.nodes = (m->precision == kFP64 || a.slope) ? nullptr : m->d.nodes;
+    k.nodes = (m->precision == kFP64 || a.slope || a.part_g) ? nullptr : m->d.nodes;
     k.slope = a.slope;
+    k.curv = eval_curv(m, a.slope);
     k.cen = m->d.cen; k.fr = m->d.fr; k.geo = m->d.geo;
     k.type = m->d.type;
     k.sigma = a.sigma;
@@ -1144,8 +1281,8 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
             k.tau2d[t][i] = m->limits[t][i] * m->limits[t][i];
             k.tau2f[t][i] = (float)k.tau2d[t][i];
         }
-    const bool f64 = m->precision == kFP64 || a.part_g;  // gradients: always the FP64 kernel
-    const int tile = far_points_per_tile(f64 ? kFP64 : kMixed);
+    const bool f64 = m->precision == kFP64;
+    const int tile = (a.part_g && !f64) ? 32 * kPtGradMixed : far_points_per_tile(f64 ? kFP64 : kMixed);
     const int n_tiles = (a.n_pts + tile - 1) / tile;
     if (a.A) {
         // assembly has no reduction over elements: cut them finely enough to fill the GPU
@@ -1161,7 +1298,10 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.n_items = n_tiles * k.n_chunks;
     k.tile_pts = tile;
     const bool st = a.stats != 0;
-    if (a.part_g) return launch_stats<true, kPtFp64, true, 2>(k, s, st);
+    if (a.part_g) {  // field gradient: the mesh's precision
+        if (f64) return launch_stats<true, kPtFp64, true, 2>(k, s, st);
+        return launch_stats<false, kPtGradMixed, true, 3>(k, s, st);
+    }
     if (a.A) {
         if (f64) return launch_stats<true, kPtFp64, false, 1>(k, s, st);
         return launch_stats<false, kPtMixed, false, 1>(k, s, st);

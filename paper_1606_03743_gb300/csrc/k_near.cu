@@ -246,12 +246,103 @@ __device__ void polygon_field_lin(int nv, const double* __restrict__ V, D3 P, do
     out[3] = fma(sP, f0[3], fma(-h * nrm.z, hsum, ec.z));
 }
 
+// x^T H y for the symmetric H stored as (xx, yy, zz, xy, xz, yz)
+__device__ __forceinline__ double hform(const double* H, D3 x, D3 y) {
+    return x.x * (H[0] * y.x + H[3] * y.y + H[4] * y.z) + x.y * (H[3] * y.x + H[1] * y.y + H[5] * y.z) +
+           x.z * (H[4] * y.x + H[5] * y.y + H[2] * y.z);
+}
+__device__ __forceinline__ D3 hmul(const double* H, D3 x) {
+    return D3{H[0] * x.x + H[3] * x.y + H[4] * x.z, H[3] * x.x + H[1] * x.y + H[5] * x.z,
+              H[4] * x.x + H[5] * x.y + H[2] * x.z};
+}
+
+// phi and E (without 1/(4 pi eps0)) of the polygon with the quadratic density
+// sigma(Q) = sc + g.(Q - C) + (Q - C)^T H (Q - C) / 2 (g and H in the element
+// plane).  About the foot P' of P (w = Q - P'): sigma = sP + gP.w + w^T H w / 2
+// with gP = g + H (P' - C).  Beyond the linear terms, per edge e (J_e =
+// int_e R ds = (s2 R2 - s1 R1 + rho_e^2 l_e) / 2):
+//   H : int w w^T / R dA   = sum_e (d_e J_e m^T H m + (R2^3 - R1^3)/3 t^T H m) - tr(H) int R dA,
+//                            int R dA = (sum_e d_e J_e + h^2 I0) / 3
+//   H : int w w^T / R^3 dA = tr(H) I0 - sum_e (d_e l_e m^T H m + (R2 - R1) t^T H m)
+//   int (w^T H w) w / R^3 dA = 2 H int w / R dA - sum_e m_e q_e,
+//   q_e = int_e w^T H w / R ds = d_e^2 m^T H m l_e + 2 d_e m^T H t (R2 - R1)
+//         + t^T H t (s2 R2 - s1 R1 - rho_e^2 l_e) / 2
+// (the in-plane divergence theorem on w R, w w^T / R and (w^T H w) / R, with
+// w = d_e m_e + s t_e on the edge); then
+//   phi = sP I0 + gP . int w / R dA + (H : int w w^T / R dA) / 2
+//   E   = sP E0 + [linear terms with gP] + [h n (H : int w w^T / R^3 dA) - int (w^T H w) w / R^3 dA] / 2.
+__device__ void polygon_field_quad(int nv, const double* __restrict__ V, D3 P, double sc, D3 g, const double* H, D3 C,
+                                   double out[4]) {
+    double f0[4];
+    polygon_field(nv, V, P, f0);
+    D3 c[4];
+    for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
+    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
+    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    const double h = -dot(c[0], nrm);
+    const D3 dl = sub(sub(P, scale(nrm, h)), C);
+    const D3 Hd = hmul(H, dl);
+    const double sP = sc + dot(g, dl) + 0.5 * dot(dl, Hd);
+    const D3 gP{g.x + Hd.x, g.y + Hd.y, g.z + Hd.z};
+    const double trH = H[0] + H[1] + H[2];
+    double r[4];
+    for (int k = 0; k < nv; ++k) r[k] = sqrt(dot(c[k], c[k]));
+    D3 i1{0.0, 0.0, 0.0}, ec = scale(gP, -f0[0]), qm{0.0, 0.0, 0.0};
+    double hsum = 0.0, sdj = 0.0, hi2 = 0.0, hk2 = trH * f0[0];
+    for (int k = 0; k < nv; ++k) {
+        const int k2 = (k + 1 == nv) ? 0 : k + 1;
+        D3 t = sub(c[k2], c[k]);
+        t = scale(t, 1.0 / sqrt(dot(t, t)));
+        const D3 m = cross(t, nrm);
+        const double s1 = dot(c[k], t), s2 = dot(c[k2], t);
+        const double d = dot(c[k], m);
+        const double rho2 = fma(d, d, h * h);
+        double num, den;
+        if (s1 >= 0.0) {
+            num = r[k2] + s2;
+            den = r[k] + s1;
+        } else if (s2 <= 0.0) {
+            num = r[k] - s1;
+            den = r[k2] - s2;
+        } else {
+            num = (r[k2] + s2) * (r[k] - s1);
+            den = rho2;
+        }
+        const double l = den == 0.0 ? 0.0 : log(num / den);
+        const double sr = s2 * r[k2] - s1 * r[k];
+        const double J = 0.5 * fma(rho2, l, sr);
+        const double dR = r[k2] - r[k];
+        const double cub = (r[k2] * r[k2] * r[k2] - r[k] * r[k] * r[k]) / 3.0;
+        const double mHm = hform(H, m, m), tHm = hform(H, t, m), tHt = hform(H, t, t);
+        i1 = D3{fma(m.x, J, i1.x), fma(m.y, J, i1.y), fma(m.z, J, i1.z)};
+        sdj = fma(d, J, sdj);
+        hi2 += d * J * mHm + cub * tHm;
+        hk2 -= d * l * mHm + dR * tHm;
+        const double q = d * d * mHm * l + 2.0 * d * tHm * dR + 0.5 * tHt * fma(-rho2, l, sr);
+        qm = D3{fma(m.x, q, qm.x), fma(m.y, q, qm.y), fma(m.z, q, qm.z)};
+        const double gm = dot(gP, m);
+        hsum = fma(gm, l, hsum);
+        const double a = gm * d * l, b = gm * dR;
+        ec = D3{ec.x + a * m.x + b * t.x, ec.y + a * m.y + b * t.y, ec.z + a * m.z + b * t.z};
+    }
+    hi2 -= trH * (sdj + h * h * f0[0]) / 3.0;
+    const D3 Hi1 = hmul(H, i1);
+    // (h n hk2 - (2 H I1 - qm)) / 2
+    const D3 qt{0.5 * (h * nrm.x * hk2 + qm.x) - Hi1.x, 0.5 * (h * nrm.y * hk2 + qm.y) - Hi1.y,
+                0.5 * (h * nrm.z * hk2 + qm.z) - Hi1.z};
+    out[0] = fma(sP, f0[0], dot(gP, i1) + 0.5 * hi2);
+    out[1] = fma(sP, f0[1], fma(-h * nrm.x, hsum, ec.x) + qt.x);
+    out[2] = fma(sP, f0[2], fma(-h * nrm.y, hsum, ec.y) + qt.y);
+    out[3] = fma(sP, f0[3], fma(-h * nrm.z, hsum, ec.z) + qt.z);
+}
+
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
                             const double* __restrict__ verts, const double* __restrict__ sigma,
-                            const double* __restrict__ slope, const double* __restrict__ fr,
-                            const double* __restrict__ cen, double4* __restrict__ val) {
+                            const double* __restrict__ slope, const double* __restrict__ curv,
+                            const double* __restrict__ fr, const double* __restrict__ cen,
+                            double4* __restrict__ val) {
     const unsigned long long n = min(counters[0], cap);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -270,8 +361,27 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
             const double sa = slope[2 * (size_t)r.y] / det, sb = slope[2 * (size_t)r.y + 1] / det;
             const double c0 = sa * g11 - sb * g01, c1 = sb * g00 - sa * g01;
             const D3 g{c0 * e0.x + c1 * e1.x, c0 * e0.y + c1 * e1.y, c0 * e0.z + c1 * e1.z};
-            polygon_field_lin(nv, verts + 12 * (size_t)r.y, P, sg, g,
-                              D3{cen[3 * (size_t)r.y], cen[3 * (size_t)r.y + 1], cen[3 * (size_t)r.y + 2]}, f);
+            const D3 C{cen[3 * (size_t)r.y], cen[3 * (size_t)r.y + 1], cen[3 * (size_t)r.y + 2]};
+            if (curv) {
+                // quadratic density: H = 2 c3 d0 d0^T + c4 (d0 d1^T + d1 d0^T) + 2 c5 d1 d1^T with
+                // d0 = grad(alpha), d1 = grad(beta)
+                const double ig = 1.0 / det;
+                const D3 d0{(g11 * e0.x - g01 * e1.x) * ig, (g11 * e0.y - g01 * e1.y) * ig,
+                            (g11 * e0.z - g01 * e1.z) * ig};
+                const D3 d1{(g00 * e1.x - g01 * e0.x) * ig, (g00 * e1.y - g01 * e0.y) * ig,
+                            (g00 * e1.z - g01 * e0.z) * ig};
+                const double* cq = curv + 3 * (size_t)r.y;
+                const double a2 = 2.0 * cq[0], ab = cq[1], b2 = 2.0 * cq[2];
+                const double H[6] = {a2 * d0.x * d0.x + 2.0 * ab * d0.x * d1.x + b2 * d1.x * d1.x,
+                                     a2 * d0.y * d0.y + 2.0 * ab * d0.y * d1.y + b2 * d1.y * d1.y,
+                                     a2 * d0.z * d0.z + 2.0 * ab * d0.z * d1.z + b2 * d1.z * d1.z,
+                                     a2 * d0.x * d0.y + ab * (d0.x * d1.y + d1.x * d0.y) + b2 * d1.x * d1.y,
+                                     a2 * d0.x * d0.z + ab * (d0.x * d1.z + d1.x * d0.z) + b2 * d1.x * d1.z,
+                                     a2 * d0.y * d0.z + ab * (d0.y * d1.z + d1.y * d0.z) + b2 * d1.y * d1.z};
+                polygon_field_quad(nv, verts + 12 * (size_t)r.y, P, sg, g, H, C, f);
+            } else {
+                polygon_field_lin(nv, verts + 12 * (size_t)r.y, P, sg, g, C, f);
+            }
             sg = 1.0;
         } else {
             polygon_field(nv, verts + 12 * (size_t)r.y, P, f);
@@ -371,8 +481,8 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
     (void)n_pts;
     Work& w = m->w;
     k_near_eval<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
-                                        m->n_chunks, m->d.type, m->d.verts, sigma, slope, m->d.fr, m->d.cen,
-                                        w.near_val);
+                                        m->n_chunks, m->d.type, m->d.verts, sigma, slope, eval_curv(m, slope),
+                                        m->d.fr, m->d.cen, w.near_val);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
