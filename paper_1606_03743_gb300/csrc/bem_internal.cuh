@@ -159,7 +159,6 @@ struct FarArgs {
 };
 // Far-field cubature + near-pair compaction (k_far.cu).
 int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s);
-int far_points_per_tile(int precision);
 // Analytic near field over the compacted list and the per-point finalisation (k_near.cu).
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
                      unsigned long long n_near, cudaStream_t s, const double* slope = nullptr);

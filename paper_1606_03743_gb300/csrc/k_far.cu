@@ -72,12 +72,25 @@ constexpr int kPtMixed = BEM_MIXED_PT, kPtFp64 = BEM_FP64_PT;
 #define BEM_GRAD_PT 2
 #endif
 constexpr int kPtGradMixed = BEM_GRAD_PT;  // mixed gradient: seven sums per point pair and node
+// mixed potential-only passes (assembly rows; matvec and phi-only evaluation)
+#ifndef BEM_ASM_PT
+#define BEM_ASM_PT BEM_MIXED_PT
+#endif
+#ifndef BEM_PHI_PT
+#define BEM_PHI_PT BEM_MIXED_PT
+#endif
+constexpr int kPtAsm = BEM_ASM_PT, kPtPhi = BEM_PHI_PT;
 // node-loop unroll depth
 #ifndef BEM_NODE_UNROLL
 #define BEM_NODE_UNROLL 4
 #endif
 constexpr int kNodeUnroll = BEM_NODE_UNROLL;
 // rules with at most this many nodes get fully unrolled node loops
+// 1: a one-band element's first node starts its sums (its own compiled node
+// loops); 0: the sums are zeroed and every pass shares one set of loops
+#ifndef BEM_INIT_PASS
+#define BEM_INIT_PASS 1
+#endif
 #ifndef BEM_FULL_UNROLL_MAX
 #define BEM_FULL_UNROLL_MAX 12
 #endif
@@ -881,7 +894,15 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         } else {
                             n = expand(band_rule(cd));
                         }
-                        nodes2<NP, WANT_E, GRAD3, true>(ws.nd[par], n, sv, uv, vv, eacc);
+                        if constexpr (BEM_INIT_PASS) {
+                            nodes2<NP, WANT_E, GRAD3, true>(ws.nd[par], n, sv, uv, vv, eacc);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < NP; ++k)
+#pragma unroll
+                                for (int j = 0; j < NE; ++j) eacc[k][j] = make_float2(0.0f, 0.0f);
+                            nodes2<NP, WANT_E, GRAD3, false>(ws.nd[par], n, sv, uv, vv, eacc);
+                        }
                         par ^= 1;
                         if (STATS && lane == 0) {
                             atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -1244,7 +1265,6 @@ int launch_fill_nodes(bem_mesh* m, cudaStream_t s) {
     return BEM_OK;
 }
 
-int far_points_per_tile(int precision) { return 32 * (precision == kFP64 ? kPtFp64 : kPtMixed); }
 
 int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     int rc = upload_rules(m->device);
@@ -1282,7 +1302,8 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
             k.tau2f[t][i] = (float)k.tau2d[t][i];
         }
     const bool f64 = m->precision == kFP64;
-    const int tile = (a.part_g && !f64) ? 32 * kPtGradMixed : far_points_per_tile(f64 ? kFP64 : kMixed);
+    const int pt = f64 ? kPtFp64 : a.part_g ? kPtGradMixed : a.A ? kPtAsm : a.want_e ? kPtMixed : kPtPhi;
+    const int tile = 32 * pt;
     const int n_tiles = (a.n_pts + tile - 1) / tile;
     if (a.A) {
         // assembly has no reduction over elements: cut them finely enough to fill the GPU
@@ -1304,14 +1325,14 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     }
     if (a.A) {
         if (f64) return launch_stats<true, kPtFp64, false, 1>(k, s, st);
-        return launch_stats<false, kPtMixed, false, 1>(k, s, st);
+        return launch_stats<false, kPtAsm, false, 1>(k, s, st);
     }
     if (f64) {
         if (a.want_e) return launch_stats<true, kPtFp64, true, 0>(k, s, st);
         return launch_stats<true, kPtFp64, false, 0>(k, s, st);
     }
     if (a.want_e) return launch_stats<false, kPtMixed, true, 0>(k, s, st);
-    return launch_stats<false, kPtMixed, false, 0>(k, s, st);
+    return launch_stats<false, kPtPhi, false, 0>(k, s, st);
 }
 
 }  // namespace bem
