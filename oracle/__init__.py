@@ -78,7 +78,7 @@ def _load():
         lib.oracle_eval_linear.restype = C.c_int
         lib.oracle_element_grad.argtypes = [C.c_int, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
         lib.oracle_element_grad.restype = C.c_int
-        lib.oracle_eval_grad.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, C.c_int]
+        lib.oracle_eval_grad.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d, C.c_int]
         lib.oracle_eval_grad.restype = C.c_int
         _lib = lib
         return lib
@@ -234,22 +234,25 @@ def element_grad(type_: int, verts, P, method: int = METHOD_PAPER, param: int = 
     return out, band.value
 
 
-def eval_grad(types, verts, sigma, pts, limits=None, eps0: float = 0.0, nthreads: int | None = None):
+def eval_grad(types, verts, sigma, pts, limits=None, eps0: float = 0.0, nthreads: int | None = None,
+              return_gsum: bool = False):
     """Field gradient (n, 6) = (xx, yy, zz, xy, xz, yz) of dE_i/dx_j at the
     field points, summed over all elements in index order by the method,
-    including 1/(4 pi eps0)."""
+    including 1/(4 pi eps0).  return_gsum: also the sum over elements of each
+    contribution's largest |component| (the scale of the cancellation in G)."""
     types = np.ascontiguousarray(types, dtype=np.int32)
     verts = _f64(verts, (types.shape[0], 4, 3))
     sigma = _f64(sigma, (types.shape[0],))
     pts = _f64(pts).reshape(-1, 3)
     G = np.zeros((pts.shape[0], 6))
+    gs = np.zeros(pts.shape[0]) if return_gsum else None
     lim = None if limits is None else _f64(limits, (10,))
     rc = _load().oracle_eval_grad(types.shape[0], types.ctypes.data_as(C.POINTER(C.c_int32)), _dp(verts),
-                                  _dp(sigma), _dp(lim), eps0, pts.shape[0], _dp(pts), _dp(G),
+                                  _dp(sigma), _dp(lim), eps0, pts.shape[0], _dp(pts), _dp(G), _dp(gs),
                                   nthreads or max_threads())
     if rc != 0:
         raise ValueError("oracle_eval_grad: bad arguments")
-    return G
+    return (G, gs) if return_gsum else G
 
 
 def element_batch(types, verts, P, method: int = METHOD_PAPER, param: int = 0, limits=None,

@@ -966,8 +966,12 @@ int oracle_element_grad(int type, const double* verts, const double* P, int meth
 /* field gradient at n_pts points, summed over all elements in index order
  * by the method (rule bands, analytic near field), times 1/(4 pi eps0);
  * G is n_pts x 6 (xx, yy, zz, xy, xz, yz) */
+/* gsum (optional, n_pts): the sum over elements of the largest |component|
+ * of each element's contribution, times 1/(4 pi eps0): the scale against
+ * which cancellation in G is measured */
 int oracle_eval_grad(int64_t n_el, const int32_t* type, const double* verts, const double* sigma,
-                     const double* limits, double eps0, int64_t n_pts, const double* pts, double* G, int nthreads)
+                     const double* limits, double eps0, int64_t n_pts, const double* pts, double* G, double* gsum,
+                     int nthreads)
 {
     const double kc = coulomb_k(eps0);
     int64_t p, j;
@@ -979,20 +983,25 @@ int oracle_eval_grad(int64_t n_el, const int32_t* type, const double* verts, con
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
     for (p = 0; p < n_pts; ++p) {
         const double* P = pts + 3 * p;
-        double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
+        double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0}, am = 0.0;
         int64_t jj;
         int k;
         for (jj = 0; jj < n_el; ++jj) {
             elem_t e;
-            double f[6];
+            double f[6], mx = 0.0;
             int band;
             elem_setup(&e, type[jj], verts + 12 * jj);
             band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], NULL);
             if (band == 0) analytic_grad(&e, P, f);
             else cubature_grad(&e, band - 1, P, f);
-            for (k = 0; k < 6; ++k) nsum_add(&s[k], &c[k], sigma[jj] * f[k]);
+            for (k = 0; k < 6; ++k) {
+                nsum_add(&s[k], &c[k], sigma[jj] * f[k]);
+                if (fabs(sigma[jj] * f[k]) > mx) mx = fabs(sigma[jj] * f[k]);
+            }
+            am += mx;
         }
         for (k = 0; k < 6; ++k) G[6 * p + k] = kc * (s[k] + c[k]);
+        if (gsum) gsum[p] = kc * am;
     }
     return 0;
 }

@@ -135,3 +135,15 @@ def test_field_sum_traceless_on_plate():
     pts = synth.plate_points(seed=1, n=64)
     G = oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, pts)
     assert np.abs(G[:, 0] + G[:, 1] + G[:, 2]).max() <= 1e-12 * np.abs(G).max()
+
+
+def test_gsum_bounds_the_gradient():
+    """The element-scale sum is the triangle-inequality bound of the largest
+    component, and equals it for a single element."""
+    mesh = synth.plate_mesh(seed=1, n=4)
+    pts = synth.plate_points(seed=2, n=64)
+    G, gs = oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, pts, return_gsum=True)
+    assert np.array_equal(G, oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, pts))
+    assert (np.abs(G).max(axis=1) <= gs * (1 + 1e-12)).all()
+    G1, gs1 = oracle.eval_grad(mesh.types[:1], mesh.verts[:1], mesh.sigma[:1], pts, return_gsum=True)
+    assert np.allclose(np.abs(G1).max(axis=1), gs1, rtol=1e-15, atol=0)
