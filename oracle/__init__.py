@@ -68,6 +68,10 @@ def _load():
         lib.oracle_max_threads.restype = C.c_int
         lib.oracle_element_batch.argtypes = [C.c_int64, i32, d, d, C.c_int, C.c_int, d, d, i32, C.c_int]
         lib.oracle_element_batch.restype = C.c_int
+        lib.oracle_element_grad_var.argtypes = [C.c_int, d, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
+        lib.oracle_element_grad_var.restype = C.c_int
+        lib.oracle_eval_grad_var.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d, C.c_int]
+        lib.oracle_eval_grad_var.restype = C.c_int
         lib.oracle_element_quad.argtypes = [C.c_int, d, d, d, C.c_int, C.c_int, d, d, C.POINTER(C.c_int)]
         lib.oracle_element_quad.restype = C.c_int
         lib.oracle_eval_quad.argtypes = [C.c_int64, i32, d, d, d, C.c_double, C.c_int64, d, d, d, C.c_int]
@@ -216,6 +220,50 @@ def eval_quad(types, verts, coef, pts, limits=None, eps0: float = 0.0, nthreads:
     if rc != 0:
         raise ValueError("oracle_eval_quad: bad arguments")
     return phi, E
+
+
+def _coef6(coef, n):
+    c = np.asarray(coef, float).reshape(n, -1)
+    if c.shape[1] == 3:
+        c = np.concatenate([c, np.zeros((n, 3))], axis=1)
+    return _f64(c, (n, 6))
+
+
+def element_grad_var(type_: int, verts, coef, P, method: int = METHOD_PAPER, param: int = 0, limits=None):
+    """Field gradient (6,) of one element with a linear (3 coefficients) or
+    quadratic (6) density, WITHOUT 1/(4 pi eps0); returns (g, band)."""
+    v = np.zeros((4, 3))
+    vv = np.asarray(verts, float).reshape(-1, 3)
+    v[: vv.shape[0]] = vv
+    cf = _coef6(coef, 1)[0].copy()
+    P = _f64(P, (3,))
+    lim = None if limits is None else _f64(limits, (10,))
+    out = np.zeros(6)
+    band = C.c_int(-1)
+    rc = _load().oracle_element_grad_var(type_, _dp(v), _dp(cf), _dp(P), method, param, _dp(lim), _dp(out),
+                                         C.byref(band))
+    if rc != 0:
+        raise ValueError("oracle_element_grad_var: bad arguments")
+    return out, band.value
+
+
+def eval_grad_var(types, verts, coef, pts, limits=None, eps0: float = 0.0, nthreads: int | None = None,
+                  return_gsum: bool = False):
+    """Field gradient (n, 6) for elements with linear (n_el, 3) or quadratic
+    (n_el, 6) densities, by the method, including 1/(4 pi eps0)."""
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    verts = _f64(verts, (types.shape[0], 4, 3))
+    cf = _coef6(coef, types.shape[0])
+    pts = _f64(pts).reshape(-1, 3)
+    G = np.zeros((pts.shape[0], 6))
+    gs = np.zeros(pts.shape[0]) if return_gsum else None
+    lim = None if limits is None else _f64(limits, (10,))
+    rc = _load().oracle_eval_grad_var(types.shape[0], types.ctypes.data_as(C.POINTER(C.c_int32)), _dp(verts),
+                                      _dp(cf), _dp(lim), eps0, pts.shape[0], _dp(pts), _dp(G), _dp(gs),
+                                      nthreads or max_threads())
+    if rc != 0:
+        raise ValueError("oracle_eval_grad_var: bad arguments")
+    return (G, gs) if return_gsum else G
 
 
 def element_grad(type_: int, verts, P, method: int = METHOD_PAPER, param: int = 0, limits=None):

@@ -1501,3 +1501,235 @@ int oracle_eval_quad(int64_t n_el, const int32_t* type, const double* verts, con
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Field gradient for linear and quadratic densities.                   */
+/*                                                                      */
+/* The cubature branch takes q_i = w_i area sigma(Q_i) in the point-     */
+/* charge derivative above.  The analytic branch moves the derivative   */
+/* along an in-plane unit vector tau from the field point onto the      */
+/* density (dK(P - Q)/dP = -dK(P - Q)/dQ for K(x) = x / |x|^3, then the  */
+/* divergence theorem in the plane):                                    */
+/*   dE/dtau = E[d sigma / dtau] - sum_e (tau·m_e) int_e sigma (P - Q) / R^3 ds */
+/* where E[d sigma / dtau] is the field of the density d sigma / dtau    */
+/* (constant for a linear sigma, linear for a quadratic one).  On an     */
+/* edge, sigma = b0 + b1 s + b2 s^2 in the coordinate s along t_e from   */
+/* the foot F of the perpendicular from P (P - Q = (P - F) - s t_e), so  */
+/* the edge integral is                                                 */
+/*   (P - F) (b0 M0 + b1 M1 + b2 M2) - t_e (b0 M1 + b1 M2 + b2 M3),     */
+/*   M_k = int s^k / R^3 ds:  M0 = [s / (rho^2 R)], M1 = [-1/R],         */
+/*   M2 = [ln(s + R) - s / R] = l_e - rho^2 M0, M3 = [R + rho^2 / R]     */
+/* (rho = |P - F|).  The two in-plane columns of G follow; the normal    */
+/* column from the symmetry of G and Laplace's equation (zero trace).    */
+/* ------------------------------------------------------------------ */
+static void cubature_grad_var(const elem_t* e, int rule, const double P[3], const lin_t* s, double g[6])
+{
+    const rule_t* r = e->type == 0 ? &TRI[rule] : &RECT[rule];
+    int i;
+    for (i = 0; i < 6; ++i) g[i] = 0.0;
+    for (i = 0; i < r->n; ++i) {
+        double Q[3], d[3];
+        rule_node(e, r, i, Q);
+        sub3(P, Q, d);
+        charge_grad(r->w[i] * e->area * lin_sigma(s, Q), d, g);
+    }
+}
+
+static void gl2_grad_var(const elem_t* e, int n, const double P[3], const lin_t* s, double g[6])
+{
+    double x[NGL_MAX], w[NGL_MAX];
+    int i, j, k;
+    gauss_legendre(n, x, w);
+    for (k = 0; k < 6; ++k) g[k] = 0.0;
+    for (i = 0; i < n; ++i) {
+        for (j = 0; j < n; ++j) {
+            double Q[3], d[3], wt;
+            if (e->type == 1) {
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->cen[k] + 0.5 * e->a * x[i] * e->ux[k] + 0.5 * e->b * x[j] * e->uy[k];
+                wt = w[i] * w[j] * e->a * e->b / 4.0;
+            } else {
+                const double u = 0.5 * (x[i] + 1.0), v = 0.5 * (x[j] + 1.0);
+                for (k = 0; k < 3; ++k)
+                    Q[k] = e->v[0][k] + u * (e->v[1][k] - e->v[0][k]) + u * v * (e->v[2][k] - e->v[1][k]);
+                wt = 0.25 * w[i] * w[j] * 2.0 * e->area * u;
+            }
+            sub3(P, Q, d);
+            charge_grad(wt * lin_sigma(s, Q), d, g);
+        }
+    }
+}
+
+/* int over the edge V1 -> V2 of sigma(Q) (P - Q) / R^3 ds for the density s */
+static void edge_density_field(const double V1[3], const double V2[3], const double P[3], const lin_t* s,
+                               double L[3])
+{
+    double t[3], r1[3], r2[3], rho[3], F[3], dF[3], gF[3], len, u1, u2, R1, R2, rho2, M0, M1, M2, M3, l, b0, b1, b2;
+    int k, a;
+    sub3(V2, V1, t);
+    len = norm3(t);
+    for (k = 0; k < 3; ++k) t[k] /= len;
+    sub3(V1, P, r1);
+    sub3(V2, P, r2);
+    u1 = dot3(r1, t);
+    u2 = dot3(r2, t);
+    R1 = norm3(r1);
+    R2 = norm3(r2);
+    for (k = 0; k < 3; ++k) rho[k] = r1[k] - u1 * t[k]; /* F - P */
+    rho2 = dot3(rho, rho);
+    L[0] = L[1] = L[2] = 0.0;
+    if (R1 == 0.0 || R2 == 0.0) return;
+    if (u1 >= 0.0) {
+        M0 = (u2 - u1) * (u2 + u1) / (R1 * R2 * (u2 * R1 + u1 * R2));
+    } else if (u2 <= 0.0) {
+        M0 = (u1 - u2) * (u1 + u2) / (R1 * R2 * (-u1 * R2 - u2 * R1));
+    } else {
+        if (rho2 == 0.0) return; /* on the closed edge */
+        M0 = (u2 / R2 - u1 / R1) / rho2;
+    }
+    M1 = (u2 - u1) * (u2 + u1) / (R1 * R2 * (R1 + R2)); /* 1/R1 - 1/R2 */
+    l = edge_log(u1, u2, R1, R2, rho2);
+    M2 = l - rho2 * M0;
+    M3 = (u2 - u1) * (u2 + u1) / (R1 + R2) - rho2 * M1; /* (R2 - R1) + rho^2 (1/R2 - 1/R1) */
+    /* sigma along the edge about the foot F */
+    for (k = 0; k < 3; ++k) F[k] = P[k] + rho[k];
+    sub3(F, s->C, dF);
+    for (a = 0; a < 3; ++a) {
+        gF[a] = s->g[a];
+        for (k = 0; k < 3; ++k) gF[a] += s->H[a][k] * dF[k];
+    }
+    b0 = lin_sigma(s, F);
+    b1 = dot3(gF, t);
+    b2 = 0.5 * quad_form(s->H, t, t);
+    for (k = 0; k < 3; ++k)
+        L[k] = -rho[k] * (b0 * M0 + b1 * M1 + b2 * M2) - t[k] * (b0 * M1 + b1 * M2 + b2 * M3);
+}
+
+static void analytic_grad_var(const elem_t* e, const double P[3], const lin_t* s, double g[6])
+{
+    const int nv = e->type == 0 ? 3 : 4;
+    double n[3], e1[3], e2[3], nl, tau[2][3], col[3][3], G[3][3];
+    int j, a, b, c;
+    sub3(e->v[1], e->v[0], e1);
+    sub3(e->v[2], e->v[0], e2);
+    cross3(e1, e2, n);
+    nl = norm3(n);
+    for (a = 0; a < 3; ++a) n[a] /= nl;
+    for (a = 0; a < 3; ++a) tau[0][a] = e1[a] / norm3(e1);
+    cross3(n, tau[0], tau[1]);
+    for (c = 0; c < 2; ++c) {
+        /* E of the density d sigma / d tau = tau·g + (H tau)·(Q - C) */
+        lin_t ds;
+        double f[4];
+        ds.sc = dot3(tau[c], s->g);
+        for (a = 0; a < 3; ++a) {
+            ds.g[a] = 0.0;
+            for (b = 0; b < 3; ++b) ds.g[a] += s->H[a][b] * tau[c][b];
+            ds.C[a] = s->C[a];
+        }
+        memset(ds.H, 0, sizeof ds.H);
+        analytic_field_lin(e, P, &ds, f);
+        for (a = 0; a < 3; ++a) col[c][a] = f[a + 1];
+        for (j = 0; j < nv; ++j) {
+            const double* V1 = e->v[j];
+            const double* V2 = e->v[(j + 1) % nv];
+            double t[3], m[3], L[3], len, tm;
+            sub3(V2, V1, t);
+            len = norm3(t);
+            for (a = 0; a < 3; ++a) t[a] /= len;
+            cross3(t, n, m);
+            tm = dot3(tau[c], m);
+            edge_density_field(V1, V2, P, s, L);
+            for (a = 0; a < 3; ++a) col[c][a] -= tm * L[a];
+        }
+    }
+    /* normal column: tau_k·(G n) = n·(G tau_k), n·(G n) = -(tau_1·G tau_1 + tau_2·G tau_2) */
+    {
+        const double c0 = dot3(n, col[0]), c1 = dot3(n, col[1]);
+        const double nn = -(dot3(tau[0], col[0]) + dot3(tau[1], col[1]));
+        for (a = 0; a < 3; ++a) col[2][a] = c0 * tau[0][a] + c1 * tau[1][a] + nn * n[a];
+    }
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b) G[a][b] = col[0][a] * tau[0][b] + col[1][a] * tau[1][b] + col[2][a] * n[b];
+    g[0] = G[0][0]; g[1] = G[1][1]; g[2] = G[2][2];
+    g[3] = 0.5 * (G[0][1] + G[1][0]);
+    g[4] = 0.5 * (G[0][2] + G[2][0]);
+    g[5] = 0.5 * (G[1][2] + G[2][1]);
+}
+
+/* gradient of ONE element with the quadratic density coef = (c0 .. c5)
+ * (linear: c3 = c4 = c5 = 0), without 1/(4 pi eps0); methods PAPER, GL2,
+ * ANALYTIC, RULE as oracle_element_grad */
+int oracle_element_grad_var(int type, const double* verts, const double* coef, const double* P, int method,
+                            int param, const double* limits, double* out /* 6 */, int* band_out)
+{
+    elem_t e;
+    lin_t s;
+    int band = -1;
+    build_rules();
+    elem_setup(&e, type, verts);
+    quadratic_density(&e, coef, &s);
+    switch (method) {
+    case OR_METHOD_PAPER:
+        band = choose_band(&e, P, limits ? limits + 5 * type : DEFAULT_LIMITS[type], NULL);
+        if (band == 0) analytic_grad_var(&e, P, &s, out);
+        else cubature_grad_var(&e, band - 1, P, &s, out);
+        break;
+    case OR_METHOD_GL2:
+        if (param < 1 || param > NGL_MAX) return -1;
+        gl2_grad_var(&e, param, P, &s, out);
+        break;
+    case OR_METHOD_ANALYTIC:
+        analytic_grad_var(&e, P, &s, out);
+        break;
+    case OR_METHOD_RULE:
+        if (param < 0 || param > 4) return -1;
+        cubature_grad_var(&e, param, P, &s, out);
+        break;
+    default:
+        return -1;
+    }
+    if (band_out) *band_out = band;
+    return 0;
+}
+
+/* field gradient at n_pts points for elements with quadratic densities
+ * coef (n_el x 6), by the method, summed in index order, times 1/(4 pi eps0) */
+int oracle_eval_grad_var(int64_t n_el, const int32_t* type, const double* verts, const double* coef,
+                         const double* limits, double eps0, int64_t n_pts, const double* pts, double* G,
+                         double* gsum, int nthreads)
+{
+    const double kc = coulomb_k(eps0);
+    int64_t p, j;
+    build_rules();
+    if (n_el < 0 || n_pts < 0) return -1;
+    for (j = 0; j < n_el; ++j)
+        if (type[j] != 0 && type[j] != 1) return -1;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (p = 0; p < n_pts; ++p) {
+        const double* P = pts + 3 * p;
+        double sm[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0}, am = 0.0;
+        int64_t jj;
+        int k;
+        for (jj = 0; jj < n_el; ++jj) {
+            elem_t e;
+            lin_t s;
+            double f[6], mx = 0.0;
+            int band;
+            elem_setup(&e, type[jj], verts + 12 * jj);
+            quadratic_density(&e, coef + 6 * jj, &s);
+            band = choose_band(&e, P, limits ? limits + 5 * type[jj] : DEFAULT_LIMITS[type[jj]], NULL);
+            if (band == 0) analytic_grad_var(&e, P, &s, f);
+            else cubature_grad_var(&e, band - 1, P, &s, f);
+            for (k = 0; k < 6; ++k) {
+                nsum_add(&sm[k], &c[k], f[k]);
+                if (fabs(f[k]) > mx) mx = fabs(f[k]);
+            }
+            am += mx;
+        }
+        for (k = 0; k < 6; ++k) G[6 * p + k] = kc * (sm[k] + c[k]);
+        if (gsum) gsum[p] = kc * am;
+    }
+    return 0;
+}
