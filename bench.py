@@ -426,6 +426,10 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     far = mdr[:nlo] >= 3
     kap = (esum / np.linalg.norm(rE, axis=1))[:nlo]
     sel = far & (kap <= 100)
+    ngv = min(a.grad_points_mixed, a.points)
+    pgv = torch.from_numpy(pts[:ngv]).to(dev)
+    Gv = torch.empty((ngv, 6), dtype=torch.float64, device=dev)
+    nvo = 256
     for key, coef, setter, ref_fn, desc in varying:
         setter(coef)
         bem.bem_eval(m.handle, p_all, lphi, lE, stream=stream.cuda_stream)
@@ -434,7 +438,18 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
         t1.record(stream)
         torch.cuda.synchronize()
         msl = t0.elapsed_time(t1)
+        # the field gradient with the same densities
+        bem.bem_eval_grad(m.handle, pgv, Gv, stream=stream.cuda_stream)
+        t0.record(stream)
+        bem.bem_eval_grad(m.handle, pgv, Gv, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        msg_v = t0.elapsed_time(t1)
         m.set_sigma(mesh.sigma)
+        Gvr, gsv = oracle.eval_grad_var(mesh.types, mesh.verts, coef, pts[:nvo], nthreads=nt, return_gsum=True)
+        Gvg = Gv[:nvo].cpu().numpy()
+        gverr = np.abs(Gvg - Gvr).max(axis=1) / np.abs(Gvr).max(axis=1)
+        gvsel = (mdr[:nvo] >= 3) & (gsv / np.abs(Gvr).max(axis=1) <= 100)
         lref_phi, lref_E = ref_fn(mesh.types, mesh.verts, coef, pts[:nlo], nthreads=nt)
         gl_phi, gl_E = lphi[:nlo].cpu().numpy(), lE[:nlo].cpu().numpy()
         out[key] = {
@@ -443,7 +458,10 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
             "max_rel_phi_vs_oracle": float((np.abs(gl_phi - lref_phi) / np.abs(lref_phi))[sel].max()),
             "max_rel_E_vs_oracle": float((np.linalg.norm(gl_E - lref_E, axis=1)
                                           / np.linalg.norm(lref_E, axis=1))[sel].max()),
-            "oracle_points": nlo, "gate_points": "min DR >= 3 and kappa (constant density) <= 100"}
+            "oracle_points": nlo, "gate_points": "min DR >= 3 and kappa (constant density) <= 100",
+            "field_gradient": {"value": ngv * mesh.n / (msg_v * 1e-3), "unit": UNIT, "n_points": ngv, "ms": msg_v,
+                               "max_rel_err_vs_oracle": float(gverr[gvsel].max()), "oracle_points": nvo,
+                               "gate_points": "min DR >= 3 and kappa_G <= 100"}}
 
     out["accuracy_vs_oracle"] = accuracy_report(gphi, gE, g64phi[:k], g64E[:k], rphi, rE, mdr, esum)
     out["accuracy_vs_oracle"]["run_precision"] = a.precision

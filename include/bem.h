@@ -137,7 +137,7 @@ int bem_set_sigma(bem_mesh* mesh, const double* sigma, void* stream);
  * of margin: ~1e-11 relative at the band edges instead of ~1e-15), the near
  * field by the analytic integral of the linear density.  bem_set_sigma
  * returns the mesh to constant densities.  bem_assemble and bem_matvec keep
- * their constant unit / x densities; bem_eval_grad rejects a linear mesh.
+ * their constant unit / x densities; bem_eval_grad uses the linear ones.
  *   coef [n_el][3], host or device
  */
 int bem_set_sigma_linear(bem_mesh* mesh, const double* coef, void* stream);
@@ -152,7 +152,8 @@ int bem_set_sigma_linear(bem_mesh* mesh, const double* coef, void* stream);
  * now lose two polynomial degrees of margin: up to ~1e-8 relative in E at the
  * edge of the 4-point rule's band), the near field the analytic integral of the
  * quadratic density.  bem_set_sigma or bem_set_sigma_linear replaces it;
- * bem_assemble, bem_matvec and bem_eval_grad behave as for a linear mesh.
+ * bem_assemble and bem_matvec keep their constant densities, bem_eval_grad
+ * uses the quadratic ones.
  *   coef [n_el][6], host or device
  */
 int bem_set_sigma_quadratic(bem_mesh* mesh, const double* coef, void* stream);
@@ -183,6 +184,11 @@ int bem_eval(bem_mesh* mesh, const double* points, int64_t n, double* phi, doubl
  * sums b, c, c alpha, c beta, c alpha^2, c alpha beta, c beta^2 (b = q_i / r^3,
  * c = q_i / r^5) from which the element's tensor is formed, summed as FP32
  * hi + lo pairs (~1e-6 relative, as the mixed field); near pairs are FP64.
+ * Linear and quadratic densities (bem_set_sigma_linear / _quadratic): the
+ * node charges carry sigma(Q_i); near pairs move the in-plane derivative
+ * onto the density (divergence theorem in the plane: the field of
+ * d sigma / d tau minus edge integrals of sigma (P - Q) / R^3, in closed
+ * form), the normal column from symmetry and zero trace.
  *   points [n][3]
  *   G      [n][6]  (dEx/dx, dEy/dy, dEz/dz, dEx/dy, dEx/dz, dEy/dz) in V/m^2;
  *                  the tensor is symmetric and, off the elements, traceless

@@ -642,6 +642,7 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         a.perm = w.perm;
         a.n_pts = (int)n;
         a.sigma = m->d.sigma;
+        a.slope = eval_slope(m, m->d.sigma);
         a.part = w.part;
         a.part_g = part_g.p;
         a.near_cnt = w.near_cnt;
@@ -663,7 +664,8 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         }
         Scratch<double4> gval;
         if ((rc = gval.alloc(2 * (size_t)n_near))) return rc;
-        if ((rc = launch_near_grad(m, dpts, w.perm, m->d.sigma, gval.p, n_near, s))) return rc;
+        if ((rc = launch_near_grad(m, dpts, w.perm, m->d.sigma, gval.p, n_near, s, eval_slope(m, m->d.sigma))))
+            return rc;
         if ((rc = launch_finalize_grad(m, w.perm, (int)n, part_g.p, gval.p, n_near, dG, s))) return rc;
         if (!g_dev) BEM_CUDA_TRY(cudaMemcpyAsync(G, dG, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -680,10 +682,6 @@ extern "C" {
 int bem_eval_grad(bem_mesh* m, const double* points, int64_t n, double* G, void* stream) {
     int rc = check_mesh(m, "bem_eval_grad");
     if (rc) return rc;
-    if (m->linear) {
-        set_error("bem_eval_grad: gradients are provided for constant densities only (bem_set_sigma)");
-        return BEM_ERR_INVALID;
-    }
     if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && (!points || !G))) {
         set_error("bem_eval_grad: bad arguments (n = %lld)", (long long)n);
         return BEM_ERR_INVALID;

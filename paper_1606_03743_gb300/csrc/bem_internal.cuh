@@ -176,7 +176,7 @@ int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double
 int launch_fill_nodes(bem_mesh* m, cudaStream_t s);
 // field gradient over the compacted near list and its per-point finalisation (k_near.cu)
 int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
-                     unsigned long long gcap, cudaStream_t s);
+                     unsigned long long gcap, cudaStream_t s, const double* slope = nullptr);
 int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* part_g, const double4* gval,
                          unsigned long long gcap, double* G, cudaStream_t s);
 // kc x potential of each element at its own centroid (sigma = 1): the diagonal of the

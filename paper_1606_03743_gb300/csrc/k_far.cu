@@ -1227,7 +1227,7 @@ int launch_stats(const FarK& k, cudaStream_t s, bool stats) {
             return stats ? launch_one<F64, PT, WANT_E, MODE, true, 1>(k, s)
                          : launch_one<F64, PT, WANT_E, MODE, false, 1>(k, s);
     }
-    if constexpr (MODE == 0) {  // linear / quadratic densities: evaluation only
+    if constexpr (MODE != 1) {  // linear / quadratic densities: evaluation and gradients
         if (k.slope)
             return stats ? launch_one<F64, PT, WANT_E, MODE, true, 2>(k, s)
                          : launch_one<F64, PT, WANT_E, MODE, false, 2>(k, s);

@@ -141,30 +141,6 @@ __device__ void polygon_grad(int nv, const double* __restrict__ V, D3 P, double 
     out[5] = G[1][2];
 }
 
-// Gradient of each compacted near pair, times sigma, at the pair's slot (two double4).
-__global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
-                            unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
-                            const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
-                            const double* __restrict__ verts, const double* __restrict__ sigma,
-                            double4* __restrict__ gval) {
-    const unsigned long long n = min(counters[0], cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int4 r = rec[i];
-        const int src = perm[r.x];
-        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
-        double f[6];
-        polygon_grad(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
-        const double sg = sigma[r.y];
-        const unsigned long long slot =
-            (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
-        if (slot < gcap) {
-            gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
-            gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
-        }
-    }
-}
-
 // far gradient sums of the chunks in chunk order + near pairs in element
 // order, times 1/(4 pi eps0), written at the point's original position.
 __global__ void k_finalize_grad(int n, int n_chunks, const int* __restrict__ perm, const double4* __restrict__ part_g,
@@ -336,6 +312,176 @@ __device__ void polygon_field_quad(int nv, const double* __restrict__ V, D3 P, d
     out[3] = fma(sP, f0[3], fma(-h * nrm.z, hsum, ec.z) + qt.z);
 }
 
+// The density of element j in space: sigma(Q) = sc + g.(Q - C) + (Q - C)^T H (Q - C) / 2
+// from its frame coefficients: g = s_a grad(alpha) + s_b grad(beta) and H = 2 c3 d0 d0^T +
+// c4 (d0 d1^T + d1 d0^T) + 2 c5 d1 d1^T, with d0 = grad(alpha), d1 = grad(beta) the in-plane
+// duals of the frame vectors e0, e1 (H = 0 for a linear density).
+struct Density {
+    double sc;
+    D3 g, C;
+    double H[6];  // xx, yy, zz, xy, xz, yz
+};
+__device__ void element_density(int j, double sc, const double* __restrict__ slope, const double* __restrict__ curv,
+                                const double* __restrict__ fr, const double* __restrict__ cen, Density& dn) {
+    const double* F = fr + 6 * (size_t)j;
+    const D3 e0{F[0], F[1], F[2]}, e1{F[3], F[4], F[5]};
+    const double g00 = dot(e0, e0), g01 = dot(e0, e1), g11 = dot(e1, e1);
+    const double det = g00 * g11 - g01 * g01;
+    const double sa = slope[2 * (size_t)j] / det, sb = slope[2 * (size_t)j + 1] / det;
+    const double c0 = sa * g11 - sb * g01, c1 = sb * g00 - sa * g01;
+    dn.sc = sc;
+    dn.g = D3{c0 * e0.x + c1 * e1.x, c0 * e0.y + c1 * e1.y, c0 * e0.z + c1 * e1.z};
+    dn.C = D3{cen[3 * (size_t)j], cen[3 * (size_t)j + 1], cen[3 * (size_t)j + 2]};
+    for (int k = 0; k < 6; ++k) dn.H[k] = 0.0;
+    if (curv) {
+        const double ig = 1.0 / det;
+        const D3 d0{(g11 * e0.x - g01 * e1.x) * ig, (g11 * e0.y - g01 * e1.y) * ig, (g11 * e0.z - g01 * e1.z) * ig};
+        const D3 d1{(g00 * e1.x - g01 * e0.x) * ig, (g00 * e1.y - g01 * e0.y) * ig, (g00 * e1.z - g01 * e0.z) * ig};
+        const double* cq = curv + 3 * (size_t)j;
+        const double a2 = 2.0 * cq[0], ab = cq[1], b2 = 2.0 * cq[2];
+        dn.H[0] = a2 * d0.x * d0.x + 2.0 * ab * d0.x * d1.x + b2 * d1.x * d1.x;
+        dn.H[1] = a2 * d0.y * d0.y + 2.0 * ab * d0.y * d1.y + b2 * d1.y * d1.y;
+        dn.H[2] = a2 * d0.z * d0.z + 2.0 * ab * d0.z * d1.z + b2 * d1.z * d1.z;
+        dn.H[3] = a2 * d0.x * d0.y + ab * (d0.x * d1.y + d1.x * d0.y) + b2 * d1.x * d1.y;
+        dn.H[4] = a2 * d0.x * d0.z + ab * (d0.x * d1.z + d1.x * d0.z) + b2 * d1.x * d1.z;
+        dn.H[5] = a2 * d0.y * d0.z + ab * (d0.y * d1.z + d1.y * d0.z) + b2 * d1.y * d1.z;
+    }
+}
+
+// Line integral over the edge c1 -> c2 (corners relative to P) of sigma(Q) (P - Q) / R^3 ds.
+// With F the foot of the perpendicular from P on the edge line, s the coordinate along t
+// from F and rho = |F - P|, sigma = b0 + b1 s + b2 s^2 on the edge and
+//   int = -(F - P) (b0 M0 + b1 M1 + b2 M2) - t (b0 M1 + b1 M2 + b2 M3),
+//   M0 = [s / (rho^2 R)], M1 = [-1/R], M2 = [ln(s + R) - s/R] = l - rho^2 M0,
+//   M3 = [R + rho^2 / R] = (R2 - R1) - rho^2 M1
+// (the brackets differences between the edge ends; M0 and M1 in cancellation-free
+// quotient forms).  A point on the closed edge gives 0.
+__device__ D3 edge_density_field(D3 c1, D3 c2, D3 P, const Density& dn) {
+    D3 t = sub(c2, c1);
+    t = scale(t, 1.0 / sqrt(dot(t, t)));
+    const double u1 = dot(c1, t), u2 = dot(c2, t);
+    const double R1 = sqrt(dot(c1, c1)), R2 = sqrt(dot(c2, c2));
+    const D3 rho = sub(c1, scale(t, u1));  // F - P
+    const double rho2 = dot(rho, rho);
+    if (R1 == 0.0 || R2 == 0.0) return D3{0.0, 0.0, 0.0};
+    double M0;
+    if (u1 >= 0.0) M0 = (u2 - u1) * (u2 + u1) / (R1 * R2 * (u2 * R1 + u1 * R2));
+    else if (u2 <= 0.0) M0 = (u1 - u2) * (u1 + u2) / (R1 * R2 * (-u1 * R2 - u2 * R1));
+    else if (rho2 > 0.0) M0 = (u2 / R2 - u1 / R1) / rho2;
+    else return D3{0.0, 0.0, 0.0};
+    const double M1 = (u2 - u1) * (u2 + u1) / (R1 * R2 * (R1 + R2));
+    double num, den;
+    if (u1 >= 0.0) {
+        num = R2 + u2;
+        den = R1 + u1;
+    } else if (u2 <= 0.0) {
+        num = R1 - u1;
+        den = R2 - u2;
+    } else {
+        num = (R2 + u2) * (R1 - u1);
+        den = rho2;
+    }
+    const double l = den == 0.0 ? 0.0 : log(num / den);
+    const double M2 = l - rho2 * M0;
+    const double M3 = (u2 - u1) * (u2 + u1) / (R1 + R2) - rho2 * M1;
+    // sigma, its slope along t and half its curvature along t at the foot
+    const D3 dF = sub(D3{P.x + rho.x, P.y + rho.y, P.z + rho.z}, dn.C);
+    const D3 HdF = hmul(dn.H, dF);
+    const double b0 = dn.sc + dot(dn.g, dF) + 0.5 * dot(dF, HdF);
+    const double b1 = dot(dn.g, t) + dot(HdF, t);
+    const double b2 = 0.5 * hform(dn.H, t, t);
+    const double a = fma(b0, M0, fma(b1, M1, b2 * M2)), b = fma(b0, M1, fma(b1, M2, b2 * M3));
+    return D3{-rho.x * a - t.x * b, -rho.y * a - t.y * b, -rho.z * a - t.z * b};
+}
+
+// Field gradient (xx, yy, zz, xy, xz, yz; without 1/(4 pi eps0)) of the polygon with the
+// density dn at P.  For an in-plane unit vector tau the derivative moves from P onto the
+// density (dK(P - Q)/dP = -dK(P - Q)/dQ for K(x) = x / |x|^3, then the divergence theorem
+// in the plane):
+//   dE/dtau = E[d sigma / dtau] - sum_e (tau.m_e) int_e sigma (P - Q) / R^3 ds,
+// with E[d sigma / dtau] the field of the linear density tau.g + (H tau).(Q - C).  The
+// normal column follows from the symmetry of the tensor and its zero trace off the element.
+__device__ void polygon_grad_var(int nv, const double* __restrict__ V, D3 P, const Density& dn, double out[6]) {
+    D3 c[4];
+    for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
+    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
+    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    D3 tau[2];
+    tau[0] = sub(c[1], c[0]);
+    tau[0] = scale(tau[0], 1.0 / sqrt(dot(tau[0], tau[0])));
+    tau[1] = cross(nrm, tau[0]);
+    D3 col[3];
+    for (int q = 0; q < 2; ++q) {
+        double f[4];
+        polygon_field_lin(nv, V, P, dot(tau[q], dn.g), hmul(dn.H, tau[q]), dn.C, f);
+        D3 v{f[1], f[2], f[3]};
+        for (int k = 0; k < nv; ++k) {
+            const int k2 = (k + 1 == nv) ? 0 : k + 1;
+            D3 t = sub(c[k2], c[k]);
+            t = scale(t, 1.0 / sqrt(dot(t, t)));
+            const double tm = dot(tau[q], cross(t, nrm));
+            const D3 L = edge_density_field(c[k], c[k2], P, dn);
+            v = D3{fma(-tm, L.x, v.x), fma(-tm, L.y, v.y), fma(-tm, L.z, v.z)};
+        }
+        col[q] = v;
+    }
+    const double n0 = dot(nrm, col[0]), n1 = dot(nrm, col[1]);
+    const double nn = -(dot(tau[0], col[0]) + dot(tau[1], col[1]));
+    col[2] = D3{n0 * tau[0].x + n1 * tau[1].x + nn * nrm.x, n0 * tau[0].y + n1 * tau[1].y + nn * nrm.y,
+                n0 * tau[0].z + n1 * tau[1].z + nn * nrm.z};
+    // G = col_0 tau_0^T + col_1 tau_1^T + col_2 n^T, symmetrised
+    auto Gab = [&](int a, int b) {
+        const double ca[3] = {a == 0 ? col[0].x : a == 1 ? col[0].y : col[0].z,
+                              a == 0 ? col[1].x : a == 1 ? col[1].y : col[1].z,
+                              a == 0 ? col[2].x : a == 1 ? col[2].y : col[2].z};
+        const double rb[3] = {b == 0 ? tau[0].x : b == 1 ? tau[0].y : tau[0].z,
+                              b == 0 ? tau[1].x : b == 1 ? tau[1].y : tau[1].z,
+                              b == 0 ? nrm.x : b == 1 ? nrm.y : nrm.z};
+        return ca[0] * rb[0] + ca[1] * rb[1] + ca[2] * rb[2];
+    };
+    out[0] = Gab(0, 0);
+    out[1] = Gab(1, 1);
+    out[2] = Gab(2, 2);
+    out[3] = 0.5 * (Gab(0, 1) + Gab(1, 0));
+    out[4] = 0.5 * (Gab(0, 2) + Gab(2, 0));
+    out[5] = 0.5 * (Gab(1, 2) + Gab(2, 1));
+}
+
+// Gradient of each compacted near pair, times sigma, at the pair's slot (two double4);
+// linear / quadratic densities (slope set) by polygon_grad_var.
+__global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
+                            unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
+                            const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
+                            const double* __restrict__ verts, const double* __restrict__ sigma,
+                            const double* __restrict__ slope, const double* __restrict__ curv,
+                            const double* __restrict__ fr, const double* __restrict__ cen,
+                            double4* __restrict__ gval) {
+    const unsigned long long n = min(counters[0], cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int4 r = rec[i];
+        const int src = perm[r.x];
+        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
+        const int nv = type[r.y] == BEM_RECTANGLE ? 4 : 3;
+        double f[6];
+        double sg = sigma[r.y];
+        if (slope) {
+            Density dn;
+            element_density(r.y, sg, slope, curv, fr, cen, dn);
+            polygon_grad_var(nv, verts + 12 * (size_t)r.y, P, dn, f);
+            sg = 1.0;
+        } else {
+            polygon_grad(nv, verts + 12 * (size_t)r.y, P, f);
+        }
+        const unsigned long long slot =
+            (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
+        if (slot < gcap) {
+            gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
+            gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
+        }
+    }
+}
+
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
@@ -353,35 +499,10 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
         const int nv = type[r.y] == BEM_RECTANGLE ? 4 : 3;
         double sg = sigma[r.y];
         if (slope) {
-            // linear density: g = s_a grad(alpha) + s_b grad(beta), the in-plane duals of e0, e1
-            const double* F = fr + 6 * (size_t)r.y;
-            const D3 e0{F[0], F[1], F[2]}, e1{F[3], F[4], F[5]};
-            const double g00 = dot(e0, e0), g01 = dot(e0, e1), g11 = dot(e1, e1);
-            const double det = g00 * g11 - g01 * g01;
-            const double sa = slope[2 * (size_t)r.y] / det, sb = slope[2 * (size_t)r.y + 1] / det;
-            const double c0 = sa * g11 - sb * g01, c1 = sb * g00 - sa * g01;
-            const D3 g{c0 * e0.x + c1 * e1.x, c0 * e0.y + c1 * e1.y, c0 * e0.z + c1 * e1.z};
-            const D3 C{cen[3 * (size_t)r.y], cen[3 * (size_t)r.y + 1], cen[3 * (size_t)r.y + 2]};
-            if (curv) {
-                // quadratic density: H = 2 c3 d0 d0^T + c4 (d0 d1^T + d1 d0^T) + 2 c5 d1 d1^T with
-                // d0 = grad(alpha), d1 = grad(beta)
-                const double ig = 1.0 / det;
-                const D3 d0{(g11 * e0.x - g01 * e1.x) * ig, (g11 * e0.y - g01 * e1.y) * ig,
-                            (g11 * e0.z - g01 * e1.z) * ig};
-                const D3 d1{(g00 * e1.x - g01 * e0.x) * ig, (g00 * e1.y - g01 * e0.y) * ig,
-                            (g00 * e1.z - g01 * e0.z) * ig};
-                const double* cq = curv + 3 * (size_t)r.y;
-                const double a2 = 2.0 * cq[0], ab = cq[1], b2 = 2.0 * cq[2];
-                const double H[6] = {a2 * d0.x * d0.x + 2.0 * ab * d0.x * d1.x + b2 * d1.x * d1.x,
-                                     a2 * d0.y * d0.y + 2.0 * ab * d0.y * d1.y + b2 * d1.y * d1.y,
-                                     a2 * d0.z * d0.z + 2.0 * ab * d0.z * d1.z + b2 * d1.z * d1.z,
-                                     a2 * d0.x * d0.y + ab * (d0.x * d1.y + d1.x * d0.y) + b2 * d1.x * d1.y,
-                                     a2 * d0.x * d0.z + ab * (d0.x * d1.z + d1.x * d0.z) + b2 * d1.x * d1.z,
-                                     a2 * d0.y * d0.z + ab * (d0.y * d1.z + d1.y * d0.z) + b2 * d1.y * d1.z};
-                polygon_field_quad(nv, verts + 12 * (size_t)r.y, P, sg, g, H, C, f);
-            } else {
-                polygon_field_lin(nv, verts + 12 * (size_t)r.y, P, sg, g, C, f);
-            }
+            Density dn;
+            element_density(r.y, sg, slope, curv, fr, cen, dn);
+            if (curv) polygon_field_quad(nv, verts + 12 * (size_t)r.y, P, dn.sc, dn.g, dn.H, dn.C, f);
+            else polygon_field_lin(nv, verts + 12 * (size_t)r.y, P, dn.sc, dn.g, dn.C, f);
             sg = 1.0;
         } else {
             polygon_field(nv, verts + 12 * (size_t)r.y, P, f);
@@ -500,10 +621,11 @@ int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double
 }
 
 int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
-                     unsigned long long gcap, cudaStream_t s) {
+                     unsigned long long gcap, cudaStream_t s, const double* slope) {
     Work& w = m->w;
     k_near_grad<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, gcap, pts, perm,
-                                        w.near_off, m->n_chunks, m->d.type, m->d.verts, sigma, gval);
+                                        w.near_off, m->n_chunks, m->d.type, m->d.verts, sigma, slope,
+                                        eval_curv(m, slope), m->d.fr, m->d.cen, gval);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;

@@ -102,9 +102,18 @@ def test_noalloc_and_server_use_linear_density(bem, case):
         assert np.array_equal(sphi, phi[:500]) and np.array_equal(sE, E[:500])
 
 
-def test_gradient_rejects_linear_mesh(bem, case):
-    mesh, coef, pts, *_ = case
-    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=0) as m:
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-6)])
+def test_gradient_of_linear_density(bem, case, prec, tol):
+    """bem_eval_grad on a linear mesh against the oracle's gradient for the
+    linear density (largest component error over the largest component)."""
+    mesh, coef, pts, _, _, mdr = case
+    sub = np.concatenate([np.where(mdr < 3)[0], np.arange(0, len(pts), 5)])
+    P = pts[sub]
+    ref = oracle.eval_grad_var(mesh.types, mesh.verts, coef, P)
+    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=prec) as m:
         m.set_sigma_linear(coef)
-        with pytest.raises(bem.BemError):
-            m.eval_grad(pts[:10])
+        G = m.eval_grad(P)
+    err = np.abs(G - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    far = mdr[sub] >= 3
+    assert err[far].max() <= tol
+    assert err[~far].max() <= (1e-11 if prec == 0 else 1e-5)

@@ -118,7 +118,7 @@ def test_noalloc_and_server_use_quadratic_density(bem, case):
         assert np.array_equal(sphi, phi[:500]) and np.array_equal(sE, E[:500])
 
 
-def test_device_coefficients_and_gradient_rejected(bem, case):
+def test_device_coefficients(bem, case):
     import torch
     mesh, coef, pts, *_ = case
     with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=0) as m:
@@ -128,5 +128,40 @@ def test_device_coefficients_and_gradient_rejected(bem, case):
         m.set_sigma_quadratic(torch.from_numpy(coef).cuda())
         phi2, E2 = m.eval(pts[:300])
         assert np.array_equal(phi, phi2) and np.array_equal(E, E2)
-        with pytest.raises(bem.BemError):
-            m.eval_grad(pts[:10])
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-6)])
+def test_gradient_of_quadratic_density(bem, case, prec, tol):
+    """bem_eval_grad on a quadratic mesh against the oracle's gradient for the
+    quadratic density, near points included."""
+    mesh, coef, pts, _, _, mdr = case
+    sub = np.concatenate([np.where(mdr < 3)[0], np.arange(0, len(pts), 5)])
+    P = pts[sub]
+    ref = oracle.eval_grad_var(mesh.types, mesh.verts, coef, P)
+    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=prec) as m:
+        m.set_sigma_quadratic(coef)
+        G = m.eval_grad(P)
+        m.set_sigma(mesh.sigma)
+        G0 = m.eval_grad(P)
+    err = np.abs(G - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    far = mdr[sub] >= 3
+    assert err[far].max() <= tol
+    assert err[~far].max() <= (1e-11 if prec == 0 else 1e-5)
+    # back to constant densities: the constant gradient again
+    ref0 = oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, P)
+    assert (np.abs(G0 - ref0).max(axis=1) / np.abs(ref0).max(axis=1))[far].max() <= tol
+
+
+def test_gradient_every_band_quadratic(bem):
+    """Quadratic densities, points from DR 0.02 to 700, FP64 kernel."""
+    mesh = synth.plate_mesh(seed=2, n=4)
+    rng = np.random.default_rng(5)
+    pts = synth.random_directions(1500, seed=5) * np.geomspace(0.02, 700.0, 1500)[:, None]
+    pts += rng.uniform(-0.5, 0.5, (1500, 3)) * [1, 1, 0]
+    pts[np.abs(pts[:, 2]) < 0.01, 2] = 0.01
+    coef = rng.normal(size=(mesh.n, 6)) * 0.2 + [1.0, 0, 0, 0, 0, 0]
+    ref = oracle.eval_grad_var(mesh.types, mesh.verts, coef, pts)
+    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=bem.FP64) as m:
+        m.set_sigma_quadratic(coef)
+        G = m.eval_grad(pts)
+    assert (np.abs(G - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() <= 1e-11
