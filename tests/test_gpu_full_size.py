@@ -113,3 +113,58 @@ def test_degenerate_thin_elements(bem, prec, tol):
     assert rel_phi(phi, rphi)[far].max() <= tol and rel_E(E, rE)[far].max() <= tol
     near_tol = tol if prec == 0 else 1e-5
     assert rel_phi(phi, rphi)[~far].max() <= near_tol and rel_E(E, rE)[~far].max() <= near_tol
+
+
+def test_coax_150k_gradient_mixed(bem):
+    """The mixed gradient at the size bench.py times it (262 144 points of the
+    150 000-element mesh), sampled against the oracle.  Its bar: FP32 rounding
+    of each element's tensor, |dG| <= 1e-7 sum_j max|G_j| at every sampled
+    point, and <= 2e-6 max|G| where min DR >= 3 and kappa_G <= 100."""
+    import torch
+    mesh = synth.coax_mesh(seed=2)
+    pts = synth.coax_points(seed=2, n=1_000_000)[:262_144]
+    dev = torch.device("cuda")
+    with bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                  torch.from_numpy(mesh.sigma).to(dev), precision=bem.MIXED) as m:
+        p_d = torch.from_numpy(pts).to(dev)
+        G = torch.empty((len(pts), 6), dtype=torch.float64, device=dev)
+        bem.bem_eval_grad(m.handle, p_d, G)
+        torch.cuda.synchronize()
+        G = G.cpu().numpy()
+    idx = np.random.default_rng(14).choice(len(pts), 32, replace=False)
+    ref, gsum = oracle.eval_grad(mesh.types, mesh.verts, mesh.sigma, pts[idx], return_gsum=True)
+    _, _, mdr = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[idx], return_min_dr=True)
+    d = np.abs(G[idx] - ref).max(axis=1)
+    assert (d / gsum).max() <= 1e-7
+    kap = gsum / np.abs(ref).max(axis=1)
+    gate = (mdr >= 3) & (kap <= 100)
+    assert gate.sum() >= 16
+    assert (d / np.abs(ref).max(axis=1))[gate].max() <= 2e-6
+
+
+def test_coax_150k_1M_quadratic(bem):
+    """Quadratic densities on the full 150 000 x 1 000 000 workload, sampled."""
+    import torch
+    mesh = synth.coax_mesh(seed=2)
+    pts = synth.coax_points(seed=2, n=1_000_000)
+    rng = np.random.default_rng(31)
+    coef = np.concatenate([mesh.sigma[:, None], (rng.normal(0.0, 0.15, (2, mesh.n)) * mesh.sigma).T,
+                           (rng.normal(0.0, 0.05, (3, mesh.n)) * mesh.sigma).T], axis=1)
+    dev = torch.device("cuda")
+    with bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                  torch.from_numpy(mesh.sigma).to(dev), precision=bem.MIXED) as m:
+        m.set_sigma_quadratic(coef)
+        p_d = torch.from_numpy(pts).to(dev)
+        phi = torch.empty(len(pts), dtype=torch.float64, device=dev)
+        E = torch.empty((len(pts), 3), dtype=torch.float64, device=dev)
+        bem.bem_eval(m.handle, p_d, phi, E)
+        torch.cuda.synchronize()
+        phi, E = phi.cpu().numpy(), E.cpu().numpy()
+    idx = np.random.default_rng(15).choice(len(pts), 32, replace=False)
+    rphi, rE = oracle.eval_quad(mesh.types, mesh.verts, coef, pts[idx])
+    _, cE, mdr, esum = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[idx], return_min_dr=True,
+                                         return_esum=True)
+    gate = (mdr >= 3) & (esum / np.linalg.norm(cE, axis=1) <= 100)
+    assert gate.sum() >= 16
+    assert rel_phi(phi[idx], rphi)[gate].max() <= 1e-6
+    assert rel_E(E[idx], rE)[gate].max() <= 1e-6

@@ -165,3 +165,16 @@ def test_gradient_every_band_quadratic(bem):
         m.set_sigma_quadratic(coef)
         G = m.eval_grad(pts)
     assert (np.abs(G - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() <= 1e-11
+
+
+def test_node_table_mesh_takes_varying_densities(bem, case):
+    """A mesh created with the node table (constant densities only) evaluates
+    quadratic densities by the on-the-fly expansion: the same results as a
+    mesh without the table."""
+    mesh, coef, pts, *_ = case
+    out = []
+    for nt in (False, True):
+        with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=bem.MIXED, node_table=nt) as m:
+            m.set_sigma_quadratic(coef)
+            out.append(m.eval(pts[:1000]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
