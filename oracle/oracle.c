@@ -404,9 +404,11 @@ static void analytic_field(const elem_t* e, const double P[3], double out[4])
         phi += d * l;
         for (k = 0; k < 3; ++k) E[k] += m[k] * l;
     }
-    if (h == 0.0) {
-        /* field point in the element plane: h * Omega = 0; on the element
-         * the normal field jumps, and the mean of both sides (0) is used */
+    if (fabs(h) <= 1e-12 * e->L) {
+        /* field point in the element plane (to 1e-12 of the mean side, so
+         * that a point computed to lie on the element, such as its centroid,
+         * counts as on it whatever the rounding of h): h * Omega = 0; on the
+         * element the normal field jumps, and the mean of both sides (0) is used */
         omega = 0.0;
     } else {
         omega = tri_solid_angle(e->v[0], e->v[1], e->v[2], P);

@@ -351,3 +351,21 @@ def test_esum_is_sum_of_element_field_norms():
                   for j in range(mesh.n))
         assert es[p] == pytest.approx(k * ref, rel=1e-13)
         assert es[p] >= np.linalg.norm(E[p]) * (1 - 1e-12)  # triangle inequality
+
+
+@pytest.mark.parametrize("t", [0, 1])
+def test_centroid_of_a_tilted_element_takes_the_mean_of_both_sides(t):
+    """The centroid of an element in general position lies on it only up to the
+    rounding of its coordinates (h of order 1e-17): it still counts as on the
+    element, so its normal field is the mean of the two one-sided limits."""
+    for k, v in enumerate(synth.random_elements(t, 4, seed=470 + t)):
+        g = oracle.element_geometry(t, v)
+        C = g["centroid"]
+        n = np.cross(v[1] - v[0], v[2] - v[0])
+        n /= np.linalg.norm(n)
+        delta = 1e-8 * g["L"]
+        on = oracle.element(t, v, C, oracle.METHOD_ANALYTIC)[0]
+        up = oracle.element(t, v, C + delta * n, oracle.METHOD_ANALYTIC)[0]
+        dn = oracle.element(t, v, C - delta * n, oracle.METHOD_ANALYTIC)[0]
+        assert abs(up[1:] @ n - dn[1:] @ n) == pytest.approx(4 * math.pi, rel=1e-6)  # the jump
+        assert np.abs(on[1:] - 0.5 * (up[1:] + dn[1:])).max() <= 1e-6 * np.abs(up[1:]).max()
