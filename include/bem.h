@@ -166,8 +166,8 @@ int bem_set_sigma_quadratic(bem_mesh* mesh, const double* coef, void* stream);
  *   E      [n][3]  field (V/m), or NULL to skip it
  * n = 0 is a no-op.  Each result depends only on its own field point and
  * the mesh: it is the same whatever other points share the call.  On a
- * field point that lies on an element the normal field is taken as the
- * mean of both sides (zero contribution).
+ * field point that lies on an element (to 1e-12 of its mean side length)
+ * the normal field is taken as the mean of both sides (zero contribution).
  */
 int bem_eval(bem_mesh* mesh, const double* points, int64_t n, double* phi, double* E, void* stream);
 

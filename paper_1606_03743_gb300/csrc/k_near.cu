@@ -46,13 +46,15 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double
     D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
     nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
     const double h = -dot(c[0], nrm);  // (P - V0)·n
-    double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0, perim = 0.0;
     double r[4];
     for (int k = 0; k < nv; ++k) r[k] = sqrt(dot(c[k], c[k]));
     for (int k = 0; k < nv; ++k) {
         const int k2 = (k + 1 == nv) ? 0 : k + 1;
         D3 t = sub(c[k2], c[k]);
-        t = scale(t, 1.0 / sqrt(dot(t, t)));
+        const double len = sqrt(dot(t, t));
+        perim += len;
+        t = scale(t, 1.0 / len);
         const D3 m = cross(t, nrm);
         const double s1 = dot(c[k], t), s2 = dot(c[k2], t);
         const double d = dot(c[k], m);
@@ -75,8 +77,11 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double
         ey = fma(m.y, l, ey);
         ez = fma(m.z, l, ez);
     }
+    // in the element plane to 1e-12 of the mean side (a point computed to lie on the element,
+    // such as its centroid, counts as on it whatever the rounding of h): h Omega = 0, and on the
+    // element the mean of both sides of the normal-field jump (0)
     double om = 0.0;
-    if (h != 0.0) {
+    if (fabs(h) > 1e-12 * (perim / nv)) {
         if (nv == 3) om = solid_angle(c[0], c[1], c[2]);
         else om = solid_angle(c[0], c[1], c[3]) + solid_angle(c[1], c[2], c[3]);
     }

@@ -168,3 +168,38 @@ def test_coax_150k_1M_quadratic(bem):
     assert gate.sum() >= 16
     assert rel_phi(phi[idx], rphi)[gate].max() <= 1e-6
     assert rel_E(E[idx], rE)[gate].max() <= 1e-6
+
+
+def test_sphere_cylinder_20k_assembly_matvec_solve(bem):
+    """The 20 000-element collocation workload bench.py times: the dense
+    20 000 x 20 000 matrix (both precisions) on sampled rows, the matrix-free
+    product on the same rows, and the refined and mixed solves checked by the
+    oracle's own rows."""
+    import torch
+    mesh = synth.sphere_cylinder_mesh(seed=3)
+    col = synth.collocation_points(mesh)
+    dev = torch.device("cuda")
+    rows = [0, 9_999, 17_999, 18_000, 19_999]
+    ref = np.concatenate([oracle.assemble(mesh.types, mesh.verts, col, rows=(r, r + 1)) for r in rows])
+    x = mesh.sigma
+    rhs = np.where(mesh.types == 0, 1.0, 0.0)
+    for prec, tol in ((bem.FP64, 1e-12), (bem.MIXED, 1e-6)):
+        with bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                      torch.from_numpy(mesh.sigma).to(dev), precision=prec) as m:
+            A = torch.empty((mesh.n, mesh.n), dtype=torch.float64, device=dev)
+            bem.bem_assemble(m.handle, torch.from_numpy(col).to(dev), A)
+            torch.cuda.synchronize()
+            Ar = A[rows].cpu().numpy()
+            del A
+            assert (np.abs(Ar - ref) / np.abs(ref)).max() <= tol
+            y = m.matvec(x)
+            assert (np.abs(y[rows] - ref @ x) / np.abs(ref @ x)).max() <= tol
+            if prec == bem.FP64:
+                sig, info = m.solve(rhs, refine=True)
+                bar = 1e-9  # relative residual ~1e-12 of |rhs| = 134, plus the FP64 parity of the rows
+            else:
+                sig, info = m.solve(rhs)
+                bar = 2e-4  # relative residual 1e-6 of |rhs|, plus 1e-6 of each row's terms
+            assert info["converged"]
+            # the oracle's rows of A sigma reproduce the prescribed potentials
+            assert np.abs(ref @ sig - rhs[rows]).max() <= bar

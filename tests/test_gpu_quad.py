@@ -178,3 +178,24 @@ def test_node_table_mesh_takes_varying_densities(bem, case):
             m.set_sigma_quadratic(coef)
             out.append(m.eval(pts[:1000]))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_points_on_the_elements(bem, prec):
+    """Field and gradient at the element centroids (points on the elements: the
+    normal field of the element itself taken as the mean of both sides) with
+    quadratic densities, against the oracle's same convention."""
+    mesh = synth.sphere_cylinder_mesh(seed=3, freq=4, n_phi=8, n_z=6)
+    coef = np.random.default_rng(460).normal(size=(mesh.n, 6)) * 0.2 + [1.0, 0, 0, 0, 0, 0]
+    cen = synth.collocation_points(mesh)
+    rphi, rE = oracle.eval_quad(mesh.types, mesh.verts, coef, cen)
+    rG = oracle.eval_grad_var(mesh.types, mesh.verts, coef, cen)
+    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma, precision=prec) as m:
+        m.set_sigma_quadratic(coef)
+        phi, E = m.eval(cen)
+        G = m.eval_grad(cen)
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert np.isfinite(phi).all() and np.isfinite(E).all() and np.isfinite(G).all()
+    assert rel_phi(phi, rphi).max() <= tol
+    assert (np.abs(E - rE).max(axis=1) / np.abs(rE).max(axis=1)).max() <= tol
+    assert (np.abs(G - rG).max(axis=1) / np.abs(rG).max(axis=1)).max() <= (1e-11 if prec == 0 else 1e-5)
