@@ -65,7 +65,8 @@ extern "C" {
  * streams them into its node buffers with asynchronous copies, one element
  * ahead, instead of computing them per (warp, element).  Results agree with
  * the on-the-fly path to FP32 rounding (the charge scales the element sums
- * instead of each node's weight). */
+ * instead of each node's weight).  Linear and quadratic densities and the
+ * field gradient use the on-the-fly expansion whatever the flag. */
 #define BEM_FLAG_NODE_TABLE 1
 
 typedef struct bem_mesh bem_mesh;
