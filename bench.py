@@ -37,7 +37,7 @@ import synth  # noqa: E402
 
 METRIC = "pair interactions/s (phi+E) at stated rel. error vs FP64; p50/p99 query latency"
 UNIT = "pairs/s"
-SM_COUNT, FP32_LANES, MUFU_LANES = 152, 128, 16  # per SM
+FP32_LANES = 128  # FP32 lanes per SM (nominal; the measured rate is the denominator)
 WORKLOAD = ("coaxial cylinders r=1.0/1.2 len 4: 2 x 200x250 flat rectangles + 2 end caps of 25000 triangles "
             "(150000 elements, sigma~N(1,0.2)); 1000000 field points uniform in r<0.95, |z|<1.9")
 
@@ -142,6 +142,63 @@ def far_traffic_from_profile():
     return float(m_b.group(1))
 
 
+def measured_peaks(bem, sms: int) -> dict:
+    """Throughput of the pipes that bound the far-field kernel, measured on
+    this GPU by the library's own microbenchmark kernels (bem_peak_rate: every
+    SM full of independent FFMA, FFMA2, MUFU.RSQ or DFMA chains, best of three
+    launches timed with CUDA events, the SM clock read in the kernel).  The
+    FP32 pipe peak is the better of the scalar and packed FMA rates (lane
+    operations: an FMA counts once)."""
+    kinds = {"ffma": bem.PEAK_FFMA, "ffma2": bem.PEAK_FFMA2, "rsqrt": bem.PEAK_RSQRT, "dfma": bem.PEAK_DFMA}
+    out = {}
+    for name, k in kinds.items():
+        r = bem.bem_peak_rate(k)
+        out[name] = {"tops": r["ops_per_s"] / 1e12, "ms": r["ms"], "sm_mhz": r["sm_mhz"],
+                     "lanes_per_sm_per_clock": r["ops_per_s"] / (sms * r["sm_mhz"] * 1e6) if r["sm_mhz"] else None}
+    out["fp32_tops"] = max(out["ffma"]["tops"], out["ffma2"]["tops"])
+    out["sms"] = sms
+    out["how"] = ("bem_peak_rate: 2048 threads per SM, 8 independent chains of one instruction per thread, "
+                  "~50 ms launches, best of 3 (CUDA events); SM MHz from clock64 over %globaltimer")
+    return out
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def measured_hbm_gbs() -> tuple[float, str]:
+    """HBM copy bandwidth from MEASURED_PEAKS.json beside this file, else the
+    fallback figure of an earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, an earlier GB300 measurement)"
+
+
+def algorithmic_work_phi(stats: np.ndarray) -> float:
+    """FP-pipe operations of potential-only far pairs (assembly rows, matvec):
+    per pair 8 to classify it, per node 8 (r_i: 3, r^2: 3, q_i / r: 1, sum: 1)
+    plus one rsqrt."""
+    nodes = {0: [0, 33, 19, 12, 7, 4], 1: [0, 33, 17, 12, 7, 4]}
+    return sum(float(stats[6 * t + b]) * (8 + 8 * nodes[t][b]) for t in (0, 1) for b in range(1, 6))
+
+
 def algorithmic_work(stats: np.ndarray) -> tuple[float, float, float]:
     """Work the method needs for the far pairs of one step, from the pair
     counts per distance-ratio band.  FP32-pipe operations (an FMA is one
@@ -191,7 +248,7 @@ def run_reference(a, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_elements": mesh.n, "n_points": a.points,
                        "step": f"{n_sample} of the {a.points} points against all elements (bounded CPU sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle", "cpu_model": cpu_model(),
                              "sample": f"{n_sample} points x {mesh.n} elements per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -237,11 +294,13 @@ def main():
     def step():
         bem.bem_eval(m.handle, p_d, phi, E, stream=stream.cuda_stream)
 
-    # band statistics of this workload (outside the timed region)
+    # band statistics of this workload and the pipe peaks (outside the timed region)
     m.set_stats(True)
     step()
     stats = m.last_stats()
     m.set_stats(False)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks(bem, sms)
     m.set_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -272,13 +331,13 @@ def main():
     value = shard.job_rate(world * pairs_step * a.steps, ms)
 
     # roofline of the dominant kernel (far-field cubature), from its own events:
-    # the FP32 pipe's issue rate bounds it (152 SMs x 128 lanes x 2070 MHz
-    # operations per second), the MUFU pipe's rsqrt rate second
+    # the FP32 pipe bounds it (measured FMA rate), the MUFU pipe's rsqrt rate second
     ops, rsq, flops = algorithmic_work(stats)
     far_avg = statistics.mean(far_ms)
-    peak_ops = SM_COUNT * FP32_LANES * 2070e6 / 1e12  # T FP32-pipe ops/s at the maximum SM clock
+    peak_ops = peaks["fp32_tops"]  # T FP32-pipe lane ops/s, measured
+    derived_ops = sms * FP32_LANES * 2070e6 / 1e12  # unit counts x maximum SM clock
     achieved = ops / (far_avg * 1e-3) / 1e12
-    mufu_frac = rsq / (far_avg * 1e-3) / (SM_COUNT * MUFU_LANES * 2070e6)
+    mufu_frac = rsq / (far_avg * 1e-3) / (peaks["rsqrt"]["tops"] * 1e12)
     flop_frac = flops / (far_avg * 1e-3) / (2 * peak_ops * 1e12)
     traffic = far_traffic_from_profile()
 
@@ -292,12 +351,16 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
                          "kernel": "k_far (far-field cubature)", "kernel_ms": far_avg,
-                         "peak_note": ("FP32 pipe issue rate: 152 SMs x 128 lanes x 2070 MHz, one op per lane "
-                                       "per clock (an FMA is one op); derived from unit counts and the maximum "
-                                       "SM clock"),
+                         "peak_note": ("FP32 pipe, measured (of measured): the better of the FFMA and FFMA2 "
+                                       "microbenchmark rates in lane operations per second (an FMA is one op)"),
+                         "frac_of_derived_peak": achieved / derived_ops, "derived_peak": derived_ops,
+                         "derived_peak_note": f"{sms} SMs x {FP32_LANES} lanes x 2070 MHz",
                          "work_note": "algorithmic FP32 ops per far pair: 8 + 13 x nodes of its rule",
-                         "mufu_frac": mufu_frac, "mufu_peak_note": "MUFU rsqrt: 152 SMs x MUFU_LANES x 2070 MHz",
+                         "mufu_frac": mufu_frac,
+                         "mufu_peak_note": ("MUFU rsqrt, measured: %.2f T/s = %.1f lanes per SM per clock"
+                                            % (peaks["rsqrt"]["tops"], peaks["rsqrt"]["lanes_per_sm_per_clock"] or 0)),
                          "flop_frac_fma2": flop_frac},
+            "peaks_measured": peaks,
             "band_pairs": {"triangle": [int(x) for x in stats[0:6]], "rectangle": [int(x) for x in stats[6:12]],
                            "order": "analytic, 33, 19|17, 12, 7, 4 points"},
             "far_kernel_work": {"warp_element_uniform": int(stats[13]), "warp_element_mixed": int(stats[14]),
@@ -310,15 +373,16 @@ def main():
     if not a.no_extras:
         line["e2e"] = end_to_end(a, bem, torch, m, mesh, pts, stream, dist, dev, world, barrier)
     if rank == 0 and world == 1 and not a.no_extras:
-        line.update(extras(a, bem, torch, m, mesh, pts, prec, stream, phi, E))
+        line.update(extras(a, bem, torch, m, mesh, pts, prec, stream, phi, E, peaks))
     if rank == 0 and world == 1 and not a.no_serving:
         line["serving"] = serving(a, bem, torch)
         lat = line["serving"]["mixed"]
         line["latency"] = {"p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "workload": line["serving"]["workload"]}
     if rank == 0 and world == 1 and not a.no_assembly:
-        line["assembly"] = assembly(a, bem, torch)
+        line["assembly"] = assembly(a, bem, torch, peaks)
     if rank == 0 and world == 1 and not a.no_extras:
-        line["node_table_ablation"] = node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_avg, ops)
+        line["node_table_ablation"] = node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_avg, ops,
+                                                          peak_ops)
     if rank == 0 and world == 1 and not a.no_large:
         line["large_mixed_vs_fp64"] = large_mixed_vs_fp64(a, bem, torch)
     if rank == 0:
@@ -350,7 +414,7 @@ def end_to_end(a, bem, torch, m, mesh, pts, stream, dist, dev, world, barrier):
             "ms_per_step": e2e_ms, "timing": "host clock around the call, median of 3, slowest rank"}
 
 
-def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
+def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d, peaks):
     """End-to-end (host buffers), FP64-path comparison, CPU oracle baseline and accuracy."""
     out = {}
     # ---- the plain FP64 kernel on the same GPU (smaller batch: it is ~50x slower)
@@ -361,14 +425,33 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     p64 = torch.from_numpy(pts[:n64]).to(dev)
     f64phi = torch.empty(n64, dtype=torch.float64, device=dev)
     f64E = torch.empty((n64, 3), dtype=torch.float64, device=dev)
+    m64.set_stats(True)  # band counts of this batch (untimed)
     bem.bem_eval(m64.handle, p64, f64phi, f64E, stream=stream.cuda_stream)
+    stats64 = m64.last_stats()
+    m64.set_stats(False)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    bem.bem_eval(m64.handle, p64, f64phi, f64E, stream=stream.cuda_stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = t0.elapsed_time(t1)
+    m64.set_timing(True)
+    calls, far64 = [], []
+    for _ in range(3):
+        t0.record(stream)
+        bem.bem_eval(m64.handle, p64, f64phi, f64E, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        calls.append(t0.elapsed_time(t1))
+        far64.append(float(m64.last_times()[1]))
+    m64.set_timing(False)
+    ms64 = statistics.median(calls)
+    ops64, _, _ = algorithmic_work(stats64)
+    far64_ms = statistics.median(far64)
+    fp64_roof = {"bound": "alu", "kernel": "k_far (FP64 path)", "kernel_ms": far64_ms,
+                 "achieved": ops64 / (far64_ms * 1e-3) / 1e12, "peak": peaks["dfma"]["tops"], "unit": "Tops/s",
+                 "frac": ops64 / (far64_ms * 1e-3) / 1e12 / peaks["dfma"]["tops"],
+                 "peak_note": "FP64 pipe, measured DFMA rate (of measured)",
+                 "work_note": ("the same algorithmic count as the mixed path (8 + 13 x nodes per far pair) on the "
+                               "FP64 pipe; the FP64 reciprocal square root is a multi-instruction sequence, so "
+                               "the kernel issues more FP64 operations than this count"),
+                 "timing": "median of 3 calls, kernel time from the library's CUDA events"}
     mix_rate = None
     # same batch on the mixed mesh for a like-for-like ratio
     if prec == bem.MIXED:
@@ -381,6 +464,7 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
         torch.cuda.synchronize()
         mix_rate = n64 * mesh.n / (t0.elapsed_time(t1) * 1e-3)
     out["fp64_path"] = {"value": n64 * mesh.n / (ms64 * 1e-3), "unit": UNIT, "n_points": n64, "ms": ms64,
+                        "roofline": fp64_roof,
                         "mixed_same_batch": mix_rate,
                         "mixed_over_fp64": (mix_rate / (n64 * mesh.n / (ms64 * 1e-3))) if mix_rate else None}
 
@@ -394,6 +478,7 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
                                             return_min_dr=True, return_esum=True)
     cpu_s = time.perf_counter() - t0c
     out["cpu_baseline"] = {"value": ns * mesh.n / cpu_s, "unit": UNIT, "cores": nt, "kind": "oracle",
+                           "cpu_model": cpu_model(),
                            "sample": f"first {ns} of the {a.points} points x all {mesh.n} elements ({cpu_s:.1f} s)"}
     gphi = phi_d[:ns].cpu().numpy()
     gE = E_d[:ns].cpu().numpy()
@@ -496,7 +581,7 @@ def extras(a, bem, torch, m, mesh, pts, prec, stream, phi_d, E_d):
     return out
 
 
-def node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_ms_fly, ops):
+def node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_ms_fly, ops, peak):
     """The same workload with the nodes precomputed per element (the paper's
     Sec. 6 / Table 4 comparison) against the on-the-fly kernel timed above."""
     dev = p_d.device
@@ -517,7 +602,6 @@ def node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_ms_fly, op
     d_phi = ((phi2 - phi).abs() / phi.abs()).max().item()
     d_E = ((E2 - E).norm(dim=1) / E.norm(dim=1)).max().item()
     ms = statistics.mean(far)
-    peak = SM_COUNT * FP32_LANES * 2070e6 / 1e12
     out = {"far_kernel_ms_on_the_fly": far_ms_fly, "far_kernel_ms_node_table": ms,
            "frac_node_table": ops / (ms * 1e-3) / 1e12 / peak,
            "table_bytes": int(mesh.n * 75 * 32),
@@ -529,10 +613,10 @@ def node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_ms_fly, op
 def accuracy_report(gphi, gE, g64phi, g64E, rphi, rE, mdr, esum):
     """Relative errors of phi, of the vector E and of |E| against the oracle,
     grouped by the distance-ratio band of each point's nearest element
-    (triangle limits of the paper's Sec. 4 reading: near < 3 <= 33-point < 12
+    (the default triangle limits, Sec. 4 reading: near < 4.5 <= 33-point < 12
     <= 19-point < 30 <= 12-point < 120 <= 7-point < 2250 <= 4-point), plus the
-    points outside the near band whose field does not cancel by more than
-    100 (kappa = sum_j |E_j| / |E|)."""
+    points at DR >= 3 from every element whose field does not cancel by more
+    than 100 (kappa = sum_j |E_j| / |E|)."""
     kappa = esum / np.linalg.norm(rE, axis=1)
 
     def errs(p, e, sel):
@@ -551,8 +635,9 @@ def accuracy_report(gphi, gE, g64phi, g64E, rphi, rE, mdr, esum):
                 "mean_rel_E": float(eE[sel].mean()), "max_E_over_sum_abs_Ej": float(eEc[sel].max()),
                 "n": int(sel.sum())}
 
-    edges = [0, 3, 12, 30, 120, 2250, np.inf]
-    names = ["near (<3)", "33-pt [3,12)", "19-pt [12,30)", "12-pt [30,120)", "7-pt [120,2250)", "4-pt (>=2250)"]
+    edges = [0, 4.5, 12, 30, 120, 2250, np.inf]
+    names = ["near (<4.5)", "33-pt [4.5,12)", "19-pt [12,30)", "12-pt [30,120)", "7-pt [120,2250)",
+             "4-pt (>=2250)"]
     groups = {"min_DR>=3,kappa<=100": (mdr >= 3) & (kappa <= 100), "min_DR>=3": mdr >= 3}
     for lo, hi, nm in zip(edges[:-1], edges[1:], names):
         groups["min_DR " + nm] = (mdr >= lo) & (mdr < hi)
@@ -672,7 +757,7 @@ def serving(a, bem, torch):
     return out
 
 
-def assembly(a, bem, torch):
+def assembly(a, bem, torch, peaks):
     """Collocation assembly: 20000 elements (geodesic sphere + inner
     cylinder), the dense 20000 x 20000 FP64 matrix on the device, plus the
     matrix-free product."""
@@ -685,15 +770,24 @@ def assembly(a, bem, torch):
     A = torch.empty((mesh.n, mesh.n), dtype=torch.float64, device=dev)
     x = torch.from_numpy(mesh.sigma).to(dev)
     y = torch.empty(mesh.n, dtype=torch.float64, device=dev)
+    hbm, hbm_note = measured_hbm_gbs()
     for prec, name in ((bem.FP64, "fp64"), (bem.MIXED, "mixed")):
         m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
                      torch.from_numpy(mesh.sigma).to(dev), precision=prec)
+        m.set_stats(True)  # band counts (untimed)
         bem.bem_assemble(m.handle, c_d, A)
+        st = m.last_stats()
+        m.set_stats(False)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bem.bem_assemble(m.handle, c_d, A)
-        torch.cuda.synchronize()
-        ta = time.perf_counter() - t0
+        tas = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            bem.bem_assemble(m.handle, c_d, A)
+            torch.cuda.synchronize()
+            tas.append(time.perf_counter() - t0)
+        ta = statistics.median(tas)
+        ops_a = algorithmic_work_phi(st)
+        pipe = peaks["dfma"]["tops"] if prec == bem.FP64 else peaks["fp32_tops"]
         bem.bem_matvec(m.handle, x, y)
         t0 = time.perf_counter()
         bem.bem_matvec(m.handle, x, y)
@@ -701,8 +795,14 @@ def assembly(a, bem, torch):
         tm = time.perf_counter() - t0
         nbytes = 8.0 * mesh.n * mesh.n
         out[name] = {"assemble_ms": ta * 1e3, "matrix_write_GBps": nbytes / ta / 1e9,
+                     "hbm_frac": nbytes / ta / 1e9 / hbm, "hbm_peak_gbs": hbm, "hbm_peak_note": hbm_note,
+                     "pipe_frac": ops_a / ta / 1e12 / pipe,
+                     "pipe_note": ("algorithmic ops (8 per far pair + 8 per node, potential only) over the whole "
+                                   "call's time, against the measured " +
+                                   ("DFMA" if prec == bem.FP64 else "FP32 FMA") + " rate"),
                      "entries_per_s": mesh.n * mesh.n / ta, "matvec_ms": tm * 1e3,
-                     "matvec_pairs_per_s": mesh.n * mesh.n / tm}
+                     "matvec_pairs_per_s": mesh.n * mesh.n / tm,
+                     "timing": "median of 3 calls, host clock with a device synchronize"}
         # the electrode problem: sphere (triangles) at 1 V, inner cylinder at 0 V
         rhs = torch.from_numpy(np.where(mesh.types == 0, 1.0, 0.0)).to(dev)
         sig = torch.empty(mesh.n, dtype=torch.float64, device=dev)

@@ -6,8 +6,9 @@
  * The method (Sec. 4, Eq. 4.1): every element is replaced by the point
  * charges q_i = w_i sigma A of one of the paper's cubature rules (App. A for
  * triangles, App. B for rectangles), chosen by the distance ratio
- * DR = |P - Q_cen| / L (Sec. 2); below the near-field limit (DR < 3 by
- * default, Sec. 4) the element is integrated analytically.  phi and E at a
+ * DR = |P - Q_cen| / L (Sec. 2); below the near-field limit (DR < 4.5 for
+ * triangles, 6 for rectangles by default, Sec. 4; see bem_default_limits)
+ * the element is integrated analytically.  phi and E at a
  * field point are the sums over all elements (Sec. 5), times 1/(4 pi eps0).
  *
  * Conventions for every entry point:
@@ -81,9 +82,10 @@ typedef struct {
                                  rule bands (Sec. 4): DR < limits[0] is
                                  integrated analytically, limits[0] <= DR <
                                  limits[1] uses the 33-point rule, ... and
-                                 DR >= limits[4] the 4-point rule.  Default:
-                                 triangles {3, 12, 30, 120, 2250}, rectangles
-                                 {3, 18, 45, 160, 2800}. */
+                                 DR >= limits[4] the 4-point rule.  Default
+                                 (bem_default_limits): triangles {4.5, 12,
+                                 30, 120, 2250}, rectangles {6, 18, 45, 160,
+                                 2800}. */
     double eps0;              /* vacuum permittivity; <= 0: 8.8541878128e-12 F/m */
     size_t device_mem_budget; /* upper bound in bytes on the scratch memory the
                                  mesh may hold (work lists, sort buffers);
@@ -112,6 +114,22 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
 
 /* Release the mesh and every device buffer it owns.  NULL is a no-op. */
 void bem_destroy(bem_mesh* mesh);
+
+/*
+ * bem_default_limits -- the default DR band limits of bem_options.limits
+ * (10 host doubles, triangles then rectangles, in that field's layout).
+ * Sec. 4 prints limits for the triangle potential at a 2e-15 relative error
+ * (analytic below DR 3, then 33, 19, 12, 7, 4 points from DR 3, 8, 20, 80,
+ * 1500) and notes that the field needs slightly higher ones, which then
+ * serve potential and field together; it prints none for rectangles.  The
+ * defaults repeat the paper's experiment (random unit-cube elements, the
+ * 16 x 16 Gauss-Legendre reference, mean relative errors) for phi and E
+ * together and take, per rule, the smallest DR from which both stay at or
+ * below 2e-15, rounded up -- the near limit included: the 33-point rule
+ * reaches 2e-15 for the triangle potential at DR 3, as printed, and for the
+ * field at DR 4.1 (triangles) and 5.3 (rectangles).  Host only.
+ */
+int bem_default_limits(double* out /* 10 */);
 
 /* Number of elements of the mesh (0 for NULL). */
 int64_t bem_num_elements(const bem_mesh* mesh);
@@ -142,6 +160,23 @@ int bem_set_sigma(bem_mesh* mesh, const double* sigma, void* stream);
  *   coef [n_el][3], host or device
  */
 int bem_set_sigma_linear(bem_mesh* mesh, const double* coef, void* stream);
+
+/*
+ * bem_linear_coef_from_corners -- the coefficients of bem_set_sigma_linear
+ * from density values at the corners of each element (Sec. 7's densities
+ * that vary over the element, given where meshes usually carry them).  The
+ * frame coordinates are those of Eq. 3.2 / Eq. 3.3 (see bem_rule):
+ *   triangle (sA, sB, sC): the linear interpolant, coef = (m, sA - m, sB - m)
+ *     with m = (sA + sB + sC) / 3;
+ *   rectangle (s0, s1, s2, s3) at P0..P3 = natural coordinates (-1,-1),
+ *     (1,-1), (1,1), (-1,1): the least-squares plane, ((s0+s1+s2+s3)/4,
+ *     (s1+s2-s0-s3)/4, (s2+s3-s0-s1)/4), exact when s0 + s2 = s1 + s3.
+ *   types  [n]     host
+ *   values [n][4]  host; a triangle's fourth value is ignored
+ *   coef   [n][3]  host, out
+ * Host only; no device needed.  BEM_ERR_INVALID for an unknown type.
+ */
+int bem_linear_coef_from_corners(const int32_t* types, const double* values, int64_t n, double* coef);
 
 /*
  * bem_set_sigma_quadratic -- charge densities that vary quadratically over
@@ -301,6 +336,28 @@ int bem_last_times(const bem_mesh* mesh, double* out /* 4 */);
 /* Total number of CUDA kernels this library has launched in this process
  * (all meshes, all devices). */
 int64_t bem_kernel_launches(void);
+
+/*
+ * bem_peak_rate -- measured throughput of one arithmetic pipe of the current
+ * device, the denominator of the far-field kernel's roofline fraction.  The
+ * paper has no counterpart (it reports times, not pipe rates); the cubature
+ * sum of Eq. 4.1 is bound by FP32 fused multiply-adds plus one reciprocal
+ * square root per node (mixed path) or by FP64 arithmetic (FP64 path).
+ *   kind  BEM_PEAK_FFMA (scalar FP32 FMA), BEM_PEAK_FFMA2 (packed f32x2 FMA),
+ *         BEM_PEAK_RSQRT (MUFU reciprocal square root), BEM_PEAK_DFMA (FP64 FMA)
+ *   out   [3] host: out[0] lane operations per second (an FMA counts as one
+ *         operation, a packed FFMA2 as two), out[1] duration of the best of
+ *         three timed launches in ms (CUDA events), out[2] the SM clock in
+ *         MHz during the run (clock64 over the global timer on one block)
+ * Every SM runs 2048 threads, each with eight independent chains of the
+ * instruction; a launch lasts about 50 ms.  Allocates a few bytes of device
+ * memory and a stream for the call.  BEM_ERR_INVALID for an unknown kind.
+ */
+#define BEM_PEAK_FFMA 0
+#define BEM_PEAK_FFMA2 1
+#define BEM_PEAK_RSQRT 2
+#define BEM_PEAK_DFMA 3
+int bem_peak_rate(int32_t kind, double* out /* 3 */);
 
 /*
  * bem_eval_noalloc -- bem_eval that allocates no device memory.

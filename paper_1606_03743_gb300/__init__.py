@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = ["Mesh", "BemError", "load_library", "bem_create", "bem_destroy", "bem_eval", "bem_assemble",
            "bem_matvec", "bem_set_sigma", "bem_centroids", "bem_rule", "bem_num_elements", "bem_last_error",
            "bem_version", "bem_set_stats", "bem_last_stats", "bem_set_timing", "bem_last_times",
-           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "bem_set_sigma_linear", "bem_set_sigma_quadratic", "linear_coef_from_corner_values", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
+           "bem_kernel_launches", "bem_eval_noalloc", "bem_solve", "bem_eval_grad", "bem_set_sigma_linear", "bem_set_sigma_quadratic", "linear_coef_from_corner_values", "bem_peak_rate", "bem_default_limits", "PEAK_FFMA", "PEAK_FFMA2", "PEAK_RSQRT", "PEAK_DFMA", "SOLVE_X0", "SOLVE_REFINE", "FLAG_NODE_TABLE", "NOALLOC_MAX_POINTS", "NOALLOC_MAX_NEAR", "Server", "FP64", "MIXED", "TRIANGLE", "RECTANGLE"]
 
 FP64, MIXED = 0, 1
 TRIANGLE, RECTANGLE = 0, 1
@@ -103,6 +103,12 @@ def load_library(build_if_missing: bool = True):
     lib.bem_eval_grad.restype = C.c_int
     lib.bem_solve.argtypes = [vp, vp, vp, C.POINTER(bem_solve_options), d, vp]
     lib.bem_solve.restype = C.c_int
+    lib.bem_linear_coef_from_corners.argtypes = [vp, vp, C.c_int64, vp]
+    lib.bem_linear_coef_from_corners.restype = C.c_int
+    lib.bem_default_limits.argtypes = [d]
+    lib.bem_default_limits.restype = C.c_int
+    lib.bem_peak_rate.argtypes = [C.c_int32, d]
+    lib.bem_peak_rate.restype = C.c_int
     for name in ("bem_server_create", "bem_submit", "bem_poll", "bem_wait", "bem_cancel", "bem_server_pause",
                  "bem_server_stats"):
         getattr(lib, name).restype = C.c_int
@@ -186,6 +192,13 @@ def bem_rule(type_: int, r: int) -> np.ndarray:
     return out[:n].copy()
 
 
+def bem_default_limits() -> np.ndarray:
+    """(2, 5) default DR band limits (triangles, rectangles) of bem_create."""
+    out = np.zeros(10)
+    _check(load_library().bem_default_limits(out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out.reshape(2, 5)
+
+
 def bem_create(types, verts, sigma, precision: int = FP64, limits=None, eps0: float = 0.0,
                device_mem_budget: int = 0, stream=None, flags: int = 0) -> int:
     lib = load_library()
@@ -220,9 +233,27 @@ def bem_set_sigma(mesh: int, sigma, stream=None) -> None:
     _check(load_library().bem_set_sigma(mesh, sp, _stream(stream)))
 
 
+def _check_out(name: str, x, n: int, per: int) -> None:
+    """An output array the library writes n * per doubles into: float64,
+    contiguous and large enough (a short array would get writes past its end)."""
+    if x is None:
+        return
+    if _is_torch(x):
+        t = _torch()
+        ok_type, ok_contig, size = x.dtype == t.float64, x.is_contiguous(), x.numel()
+    else:
+        ok_type, ok_contig, size = x.dtype == np.float64, x.flags["C_CONTIGUOUS"], x.size
+    if not ok_type or not ok_contig:
+        raise ValueError(f"{name} must be a contiguous float64 array")
+    if size < n * per:
+        raise ValueError(f"{name} holds {size} doubles; {n * per} are written")
+
+
 def bem_eval(mesh: int, points, phi=None, E=None, stream=None) -> None:
     p, pp = _prep(points, np.float64)
     n = p.numel() // 3 if _is_torch(p) else p.size // 3
+    _check_out("phi", phi, n, 1)
+    _check_out("E", E, n, 3)
     _check(load_library().bem_eval(mesh, pp, n, _ptr(phi) if phi is not None else None,
                                    _ptr(E) if E is not None else None, _stream(stream)))
 
@@ -237,6 +268,8 @@ def bem_eval_noalloc(mesh: int, points, phi=None, E=None, stream=None) -> None:
     points, phi and E must be CUDA tensors, at most NOALLOC_MAX_POINTS points."""
     p, pp = _prep(points, np.float64)
     n = p.numel() // 3 if _is_torch(p) else p.size // 3
+    _check_out("phi", phi, n, 1)
+    _check_out("E", E, n, 3)
     _check(load_library().bem_eval_noalloc(mesh, pp, n, _ptr(phi) if phi is not None else None,
                                            _ptr(E) if E is not None else None, _stream(stream)))
 
@@ -244,11 +277,13 @@ def bem_eval_noalloc(mesh: int, points, phi=None, E=None, stream=None) -> None:
 def bem_assemble(mesh: int, colloc, A, stream=None) -> None:
     p, pp = _prep(colloc, np.float64)
     m = p.numel() // 3 if _is_torch(p) else p.size // 3
+    _check_out("A", A, m, bem_num_elements(mesh))
     _check(load_library().bem_assemble(mesh, pp, m, _ptr(A), _stream(stream)))
 
 
 def bem_matvec(mesh: int, x, y, stream=None) -> None:
     xx, xp = _prep(x, np.float64, (bem_num_elements(mesh),))
+    _check_out("y", y, bem_num_elements(mesh), 1)
     _check(load_library().bem_matvec(mesh, xp, _ptr(y), _stream(stream)))
 
 
@@ -267,25 +302,35 @@ def bem_set_sigma_quadratic(mesh: int, coef, stream=None) -> None:
 
 def linear_coef_from_corner_values(types, values):
     """(n, 3) coefficients of bem_set_sigma_linear from density values at the
-    corners: triangles (sA, sB, sC) interpolated linearly; rectangles the linear
-    least-squares fit of the four corner values (exact when they lie on a plane:
-    s0 + s2 = s1 + s3)."""
-    types = np.asarray(types)
-    v = np.asarray(values, np.float64).reshape(len(types), -1)
-    out = np.zeros((len(types), 3))
-    tri = types == TRIANGLE
-    m = v[tri, :3].mean(axis=1)
-    out[tri] = np.stack([m, v[tri, 0] - m, v[tri, 1] - m], axis=1)
-    r = ~tri
-    s0, s1, s2, s3 = v[r, 0], v[r, 1], v[r, 2], v[r, 3]  # corners at (x, y) = (-1,-1), (1,-1), (1,1), (-1,1)
-    out[r] = np.stack([(s0 + s1 + s2 + s3) / 4, (s1 + s2 - s0 - s3) / 4, (s2 + s3 - s0 - s1) / 4], axis=1)
+    corners (n, 3 or 4): bem_linear_coef_from_corners (host arrays; a
+    triangle's fourth value is ignored)."""
+    t = np.ascontiguousarray(np.asarray(types), dtype=np.int32)
+    n = int(t.shape[0])
+    v = np.asarray(values, np.float64).reshape(n, -1)
+    v4 = np.zeros((n, 4))
+    v4[:, : v.shape[1]] = v
+    out = np.zeros((n, 3))
+    _check(load_library().bem_linear_coef_from_corners(t.ctypes.data, v4.ctypes.data, n, out.ctypes.data))
     return out
+
+
+# arithmetic pipes of bem_peak_rate
+PEAK_FFMA, PEAK_FFMA2, PEAK_RSQRT, PEAK_DFMA = 0, 1, 2, 3
+
+
+def bem_peak_rate(kind: int) -> dict:
+    """Measured throughput of one arithmetic pipe of the current device:
+    {ops_per_s (lane operations, an FMA counts once), ms, sm_mhz}."""
+    out = np.zeros(3)
+    _check(load_library().bem_peak_rate(int(kind), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return {"ops_per_s": float(out[0]), "ms": float(out[1]), "sm_mhz": float(out[2])}
 
 
 def bem_eval_grad(mesh: int, points, G, stream=None) -> None:
     """Field gradient (n, 6) = (dEx/dx, dEy/dy, dEz/dz, dEx/dy, dEx/dz, dEy/dz) at the points."""
     pp, ptr = _prep(points, np.float64)
     n = (pp.numel() if _is_torch(pp) else pp.size) // 3
+    _check_out("G", G, n, 6)
     _check(load_library().bem_eval_grad(mesh, ptr, n, _ptr(G), _stream(stream)))
 
 
@@ -512,3 +557,4 @@ class Server:
         _check(load_library().bem_server_stats(self._h, 1 if reset else 0,
                                                out.ctypes.data_as(C.POINTER(C.c_double))))
         return dict(zip(SERVER_STAT_NAMES, out.tolist()))
+

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The far-field kernel's FP32 values (squared distances >= ~1e-6, charges,
 # sums) are nowhere near the FP32 denormal range, so it flushes denormals:
 # rsqrtf then maps to the bare MUFU reciprocal square root.
-PER_FILE_FLAGS = {"k_far.cu": ["-ftz=true"]}
+PER_FILE_FLAGS = {"k_far.cu": ["-ftz=true"], "peaks.cu": ["-ftz=true"]}
 
 
 def nvcc() -> str:

@@ -9,13 +9,16 @@
 #include <string>
 
 #include "bem_internal.cuh"
+#include "bem_test.h"
 
 namespace bem {
 
 namespace {
 thread_local std::string g_err;
 std::atomic<int64_t> g_launches{0};
-const double kDefaultLimits[2][5] = {{3.0, 12.0, 30.0, 120.0, 2250.0}, {3.0, 18.0, 45.0, 160.0, 2800.0}};
+// DR band limits (Sec. 4) for phi and E together: per type the smallest DR from which the
+// next rule's mean relative errors of phi and E stay at or below 2e-15, rounded up
+const double kDefaultLimits[2][5] = {{4.5, 12.0, 30.0, 120.0, 2250.0}, {6.0, 18.0, 45.0, 160.0, 2800.0}};
 constexpr double kEps0SI = 8.8541878128e-12;
 constexpr int kMaxCellBits = 7;  // must match the key width of k_sort.cu
 constexpr size_t kCells = size_t(1) << (3 * kMaxCellBits);
@@ -33,22 +36,70 @@ void set_error(const char* fmt, ...) {
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+namespace {
+std::atomic<int64_t> g_alloc_left{-1};  // allocations before injected failures (< 0: none injected)
+std::atomic<int64_t> g_alloc_count{0};  // allocations attempted, process-wide
+
+// true if this allocation is to fail (the test hook's budget is spent)
+bool injected_failure() {
+    g_alloc_count.fetch_add(1, std::memory_order_relaxed);
+    int64_t left = g_alloc_left.load();
+    while (left >= 0) {
+        if (left == 0) return true;
+        if (g_alloc_left.compare_exchange_weak(left, left - 1)) return false;
+    }
+    return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_malloc(void** p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
     set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
     return e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA;
 }
 
-namespace {
-
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+PtrLoc ptr_location(const void* p, int dev) {
+    if (!p) return kPtrHost;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();  // clear the sticky-free error of an unknown host pointer
-        return false;
+        return kPtrHost;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return kPtrDevice;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? kPtrDevice : kPtrOtherDevice;
+    return kPtrHost;
 }
+
+int reject_other_device(const char* fn, int dev, const void* const* ptrs, const char* const* names, int n) {
+    for (int i = 0; i < n; ++i) {
+        if (ptrs[i] && ptr_location(ptrs[i], dev) == kPtrOtherDevice) {
+            set_error("%s: %s is in the memory of another GPU than the mesh's device %d", fn, names[i], dev);
+            return BEM_ERR_INVALID;
+        }
+    }
+    return BEM_OK;
+}
+
+namespace {
+
+// the array is device memory the mesh's kernels can use directly (callers have
+// already rejected arrays on another device)
+bool is_device_ptr(const void* p, int dev) { return p && ptr_location(p, dev) == kPtrDevice; }
 
 template <typename T>
 int dalloc(bem_mesh* m, T** p, size_t count) {
@@ -58,7 +109,7 @@ int dalloc(bem_mesh* m, T** p, size_t count) {
                   m->w.bytes);
         return BEM_ERR_OOM;
     }
-    cudaError_t e = cudaMalloc((void**)p, bytes > 0 ? bytes : 16);
+    cudaError_t e = dev_malloc((void**)p, bytes > 0 ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -166,8 +217,8 @@ void free_mesh(bem_mesh* m) {
 }
 
 // Stage an input array of `bytes` onto the device if it is a host array.
-int stage_in(const void* src, size_t bytes, void* dev_buf, const void** out, cudaStream_t s) {
-    if (is_device_ptr(src)) {
+int stage_in(const void* src, size_t bytes, void* dev_buf, const void** out, cudaStream_t s, int dev) {
+    if (is_device_ptr(src, dev)) {
         *out = src;
         return BEM_OK;
     }
@@ -323,7 +374,7 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     const size_t nn = (size_t)n;
 #define BEM_ALLOC(ptr, count)                                                              \
     if (!rc) {                                                                             \
-        cudaError_t e_ = cudaMalloc((void**)&(ptr), sizeof(*(ptr)) * (count));             \
+        cudaError_t e_ = dev_malloc((void**)&(ptr), sizeof(*(ptr)) * (count));             \
         if (e_ != cudaSuccess) {                                                           \
             cudaGetLastError();                                                            \
             set_error("bem_create: cudaMalloc failed: %s", cudaGetErrorString(e_));        \
@@ -352,9 +403,9 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     // stage the raw input (host or device) into scratch, then preprocess
     int* dtypes = nullptr;
     double *dverts = nullptr, *dsig = nullptr;
-    ce = cudaMalloc((void**)&dtypes, sizeof(int) * nn);
-    if (ce == cudaSuccess) ce = cudaMalloc((void**)&dverts, sizeof(double) * 12 * nn);
-    if (ce == cudaSuccess) ce = cudaMalloc((void**)&dsig, sizeof(double) * nn);
+    ce = dev_malloc((void**)&dtypes, sizeof(int) * nn);
+    if (ce == cudaSuccess) ce = dev_malloc((void**)&dverts, sizeof(double) * 12 * nn);
+    if (ce == cudaSuccess) ce = dev_malloc((void**)&dsig, sizeof(double) * nn);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(dtypes, types, sizeof(int) * nn, cudaMemcpyDefault, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(dverts, verts, sizeof(double) * 12 * nn, cudaMemcpyDefault, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(dsig, sigma, sizeof(double) * nn, cudaMemcpyDefault, s);
@@ -373,7 +424,7 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
         return rc;
     }
     if (opt && (opt->flags & BEM_FLAG_NODE_TABLE) && m->precision == kMixed) {
-        cudaError_t e = cudaMalloc((void**)&d.nodes, sizeof(float4) * 2 * kTableSlots * nn);
+        cudaError_t e = dev_malloc((void**)&d.nodes, sizeof(float4) * 2 * kTableSlots * nn);
         if (e != cudaSuccess) {
             cudaGetLastError();
             set_error("bem_create: cudaMalloc of the node table (%zu bytes) failed: %s",
@@ -429,7 +480,7 @@ int bem_set_sigma_linear(bem_mesh* m, const double* coef, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     BEM_CUDA_TRY(cudaSetDevice(m->device));
     if (!m->d.slope) {
-        const cudaError_t e = cudaMalloc((void**)&m->d.slope, sizeof(double) * 2 * n);
+        const cudaError_t e = dev_malloc((void**)&m->d.slope, sizeof(double) * 2 * n);
         if (e != cudaSuccess) {
             cudaGetLastError();
             m->d.slope = nullptr;
@@ -463,7 +514,7 @@ int bem_set_sigma_quadratic(bem_mesh* m, const double* coef, void* stream) {
     const size_t cols[2] = {2, 3};
     for (int b = 0; b < 2; ++b) {
         if (*bufs[b]) continue;
-        const cudaError_t e = cudaMalloc((void**)bufs[b], sizeof(double) * cols[b] * n);
+        const cudaError_t e = dev_malloc((void**)bufs[b], sizeof(double) * cols[b] * n);
         if (e != cudaSuccess) {
             cudaGetLastError();
             *bufs[b] = nullptr;
@@ -526,6 +577,54 @@ int bem_last_times(const bem_mesh* m, double* out) {
 
 int64_t bem_kernel_launches(void) { return g_launches.load(); }
 
+int bem_test_fail_alloc_after(int64_t n) {
+    g_alloc_left.store(n < 0 ? -1 : n);
+    return BEM_OK;
+}
+
+int64_t bem_test_alloc_count(void) { return g_alloc_count.load(); }
+
+int32_t bem_test_ptr_location(const void* p, int32_t dev) { return (int32_t)ptr_location(p, dev); }
+
+int bem_default_limits(double* out) {
+    if (!out) {
+        set_error("bem_default_limits: out is NULL");
+        return BEM_ERR_INVALID;
+    }
+    for (int t = 0; t < 2; ++t)
+        for (int k = 0; k < 5; ++k) out[5 * t + k] = kDefaultLimits[t][k];
+    return BEM_OK;
+}
+
+int bem_linear_coef_from_corners(const int32_t* types, const double* values, int64_t n, double* coef) {
+    if (n < 0 || (n > 0 && (!types || !values || !coef))) {
+        set_error("bem_linear_coef_from_corners: bad arguments (n = %lld)", (long long)n);
+        return BEM_ERR_INVALID;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        const double* v = values + 4 * j;
+        double* c = coef + 3 * j;
+        if (types[j] == BEM_TRIANGLE) {
+            // sigma = m + (sA - m) alpha + (sB - m) beta: at A (alpha, beta) = (1, 0), at B (0, 1),
+            // at C (-1, -1), which gives 3 m - sA - sB = sC
+            const double mean = (v[0] + v[1] + v[2]) / 3.0;
+            c[0] = mean;
+            c[1] = v[0] - mean;
+            c[2] = v[1] - mean;
+        } else if (types[j] == BEM_RECTANGLE) {
+            // corners P0..P3 at natural coordinates (-1,-1), (1,-1), (1,1), (-1,1):
+            // the least-squares plane through the four values (exact if they are planar)
+            c[0] = (v[0] + v[1] + v[2] + v[3]) / 4.0;
+            c[1] = (v[1] + v[2] - v[0] - v[3]) / 4.0;
+            c[2] = (v[2] + v[3] - v[0] - v[1]) / 4.0;
+        } else {
+            set_error("bem_linear_coef_from_corners: element %lld has unknown type %d", (long long)j, (int)types[j]);
+            return BEM_ERR_INVALID;
+        }
+    }
+    return BEM_OK;
+}
+
 int bem_centroids(bem_mesh* m, double* out, void* stream) {
     int rc = check_mesh(m, "bem_centroids");
     if (rc) return rc;
@@ -547,8 +646,8 @@ int eval_slice(bem_mesh* m, const double* points, int64_t n, double* phi, double
     if ((rc = ensure_points(m, (size_t)n))) return rc;
     Work& w = m->w;
     const double* dpts;
-    if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s))) return rc;
-    const bool phi_dev = phi && is_device_ptr(phi), E_dev = E && is_device_ptr(E);
+    if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s, m->device))) return rc;
+    const bool phi_dev = is_device_ptr(phi, m->device), E_dev = is_device_ptr(E, m->device);
     const bool phi_host = phi && !phi_dev, E_host = E && !E_dev;
     if ((phi_dev && E_host) || (phi_host && E_dev)) {
         set_error("bem_eval: phi and E must both be host or both be device arrays");
@@ -582,6 +681,11 @@ int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* 
     if (n == 0) return BEM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     BEM_CUDA_TRY(cudaSetDevice(m->device));
+    {
+        const void* ptrs[3] = {points, phi, E};
+        const char* names[3] = {"points", "phi", "E"};
+        if ((rc = reject_other_device("bem_eval", m->device, ptrs, names, 3))) return rc;
+    }
     for (int64_t off = 0; off < n; off += kEvalSlice) {
         const int64_t k = std::min(kEvalSlice, n - off);
         rc = eval_slice(m, points + 3 * off, k, phi ? phi + off : nullptr, E ? E + 3 * off : nullptr, s);
@@ -602,7 +706,7 @@ struct Scratch {
         if (p) cudaFree(p);
     }
     int alloc(size_t count) {
-        const cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * (count > 0 ? count : 1));
+        const cudaError_t e = dev_malloc((void**)&p, sizeof(T) * (count > 0 ? count : 1));
         if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -620,11 +724,11 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
     if ((rc = ensure_points(m, (size_t)n))) return rc;
     Work& w = m->w;
     const double* dpts;
-    if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s))) return rc;
+    if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s, m->device))) return rc;
     if ((rc = launch_sort_points(m, dpts, (int)n, s))) return rc;
     if ((rc = check_points(m, "bem_eval_grad", s))) return rc;
     const size_t np = (size_t)n * (size_t)m->n_chunks;
-    const bool g_dev = is_device_ptr(G);
+    const bool g_dev = is_device_ptr(G, m->device);
     const size_t need = sizeof(double4) * 2 * np + (g_dev ? 0 : sizeof(double) * 6 * (size_t)n);
     if (m->w.bytes + need > m->budget) {
         set_error("bem_eval_grad: needs %zu bytes beyond the %zu in use (budget %zu)", need, m->w.bytes, m->budget);
@@ -689,6 +793,11 @@ int bem_eval_grad(bem_mesh* m, const double* points, int64_t n, double* G, void*
     if (n == 0) return BEM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     BEM_CUDA_TRY(cudaSetDevice(m->device));
+    {
+        const void* ptrs[2] = {points, G};
+        const char* names[2] = {"points", "G"};
+        if ((rc = reject_other_device("bem_eval_grad", m->device, ptrs, names, 2))) return rc;
+    }
     for (int64_t off = 0; off < n; off += kEvalSlice) {
         const int64_t k = std::min(kEvalSlice, n - off);
         if ((rc = grad_slice(m, points + 3 * off, k, G + 6 * off, s))) return rc;
@@ -705,15 +814,20 @@ int bem_matvec(bem_mesh* m, const double* x, double* y, void* stream) {
     }
     cudaStream_t s = (cudaStream_t)stream;
     BEM_CUDA_TRY(cudaSetDevice(m->device));
+    {
+        const void* ptrs[2] = {x, y};
+        const char* names[2] = {"x", "y"};
+        if ((rc = reject_other_device("bem_matvec", m->device, ptrs, names, 2))) return rc;
+    }
     const int n = m->d.n;
     if ((rc = ensure_points(m, (size_t)n))) return rc;
     Work& w = m->w;
     // x is staged into the first n doubles of the (otherwise unused) points buffer
     const double* dx;
-    if ((rc = stage_in(x, sizeof(double) * n, w.pts, (const void**)&dx, s))) return rc;
+    if ((rc = stage_in(x, sizeof(double) * n, w.pts, (const void**)&dx, s, m->device))) return rc;
     if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[0], s));
     if ((rc = launch_sort_points(m, m->d.cen, n, s))) return rc;
-    const bool y_dev = is_device_ptr(y);
+    const bool y_dev = is_device_ptr(y, m->device);
     double* dy = y_dev ? y : w.out;
     if ((rc = run_eval(m, m->d.cen, n, dx, dy, nullptr, 0, false, s))) return rc;
     if (!y_dev) {
@@ -733,12 +847,17 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
     if (mrows == 0) return BEM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     BEM_CUDA_TRY(cudaSetDevice(m->device));
+    {
+        const void* ptrs[2] = {colloc, A};
+        const char* names[2] = {"colloc", "A"};
+        if ((rc = reject_other_device("bem_assemble", m->device, ptrs, names, 2))) return rc;
+    }
     if ((rc = ensure_points(m, (size_t)mrows))) return rc;
     Work& w = m->w;
     const double* dpts;
-    if ((rc = stage_in(colloc, sizeof(double) * 3 * mrows, w.pts, (const void**)&dpts, s))) return rc;
+    if ((rc = stage_in(colloc, sizeof(double) * 3 * mrows, w.pts, (const void**)&dpts, s, m->device))) return rc;
     const size_t abytes = sizeof(double) * (size_t)mrows * (size_t)m->d.n;
-    const bool a_dev = is_device_ptr(A);
+    const bool a_dev = is_device_ptr(A, m->device);
     double* dA = A;
     if (!a_dev) {
         if ((rc = dalloc(m, &dA, (size_t)mrows * (size_t)m->d.n))) return rc;

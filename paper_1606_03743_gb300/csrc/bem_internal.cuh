@@ -115,6 +115,23 @@ struct bem_mesh {
 namespace bem {
 
 // ---------------------------------------------------------------- helpers
+// Where a caller's array lives relative to the mesh's device `dev`: host
+// memory (staged by the library), memory the kernels on `dev` can use
+// directly (that device's memory or managed memory), or another GPU's memory
+// (rejected: a kernel on `dev` must not dereference it).
+enum PtrLoc { kPtrHost = 0, kPtrDevice = 1, kPtrOtherDevice = 2 };
+PtrLoc ptr_location(const void* p, int dev);
+// BEM_ERR_INVALID (with a message naming fn and the argument) if any of the
+// n arrays lives on another device; NULL entries are skipped.
+int reject_other_device(const char* fn, int dev, const void* const* ptrs, const char* const* names, int n);
+
+// Every device (and pinned host) allocation of the library goes through
+// these: cudaMalloc / cudaMallocHost, except that the test hook
+// bem_test_fail_alloc_after (include/bem_test.h) can make them fail with
+// cudaErrorMemoryAllocation without calling the runtime.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t pinned_malloc(void** p, size_t bytes);
+
 void set_error(const char* fmt, ...);
 void count_launches(int n);  // adds n to the process-wide kernel launch counter
 int cuda_fail(cudaError_t e, const char* what);
@@ -131,6 +148,14 @@ int cuda_fail(cudaError_t e, const char* what);
 int launch_prep(bem_mesh* m, const int* types, const double* verts, const double* sigma, cudaStream_t s,
                 int64_t* bad, int* bad_code, double* coord_max);
 
+// Bits per axis of the spatial sort's cells for n points: about one point per
+// cell (1..7 bits per axis), so the Z-order curve orders the points finely and
+// 32 x PT consecutive points are compact.  The sort uses 2^(3 b) cells.
+constexpr int sort_cell_bits(size_t n) {
+    int b = 1;
+    while (b < 7 && (size_t(1) << (3 * b)) < n) ++b;
+    return b;
+}
 // Spatial sort of field points (k_sort.cu): perm = points in cell order.
 int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s, const int* n_dev = nullptr);
 // Exclusive scan of n ints (k_sort.cu); tmp needs scan_tmp_ints(n) ints.

@@ -99,6 +99,16 @@ constexpr int kNodeUnroll = BEM_NODE_UNROLL;
 #define BEM_FLUSH 8
 #endif
 constexpr int kFlush = BEM_FLUSH;
+// mixed path: 1 keeps each point pair's d = P - C in shared memory for the
+// element's field rebuild; 0 forms it again there
+#ifndef BEM_D_SMEM
+#define BEM_D_SMEM 0
+#endif
+// 1: the per-band (masked) passes of straddling elements run one generic node
+// loop instead of loops compiled per rule size (less code)
+#ifndef BEM_MASKED_GENERIC
+#define BEM_MASKED_GENERIC 0
+#endif
 static_assert((kFlush & (kFlush - 1)) == 0 && kFlush <= 32, "flush interval: a power of two up to 32");
 
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
@@ -383,6 +393,11 @@ __device__ __forceinline__ void nodes2_n(const float4* __restrict__ nd, const fl
 template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
 __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
                                        const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
+    if constexpr (!INIT && BEM_MASKED_GENERIC) {
+#pragma unroll 2
+        for (int i = 0; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+        return;
+    }
     switch (n) {
         case 4: nodes2_n<4, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
         case 7: nodes2_n<7, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
@@ -424,6 +439,8 @@ struct WarpSmem {
     // component and lane, the running sum as an unevaluated FP32 pair hi + lo
     // (hi.x, hi.y, lo.x, lo.y)
     float4 accdf[NACC ? (PT / 2) * NACC * 32 : 1];
+    // mixed evaluation / gradient with BEM_D_SMEM: d of each point pair of a lane
+    float2 dd[(NACC && BEM_D_SMEM) ? (PT / 2) * 3 * 32 : 1];
 };
 
 template <typename R>
@@ -825,6 +842,11 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
                             diff(k, dx, dy, dz);
+                            if constexpr (BEM_D_SMEM && NACC > 0 && (WANT_E || GRAD3)) {
+                                ws.dd[(3 * k) * 32 + lane] = dx;
+                                ws.dd[(3 * k + 1) * 32 + lane] = dy;
+                                ws.dd[(3 * k + 2) * 32 + lane] = dz;
+                            }
                             sv[k] = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
                             const float2 u = fma2(dx, lo2(r3), fma2(dy, hi2(r3), mul2(dz, lo2(r4))));
                             const float2 v = fma2(dx, hi2(r4), fma2(dy, lo2(r5), mul2(dz, hi2(r5))));
@@ -985,8 +1007,14 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int k = 0; k < NP; ++k) {
                             acc8[k][0] = add2(acc8[k][0], eacc[k][0]);
                             if (WANT_E) {
-                                float2 dx, dy, dz;  // formed again rather than held through the node loop
-                                diff(k, dx, dy, dz);
+                                float2 dx, dy, dz;  // not held in registers through the node loop
+                                if constexpr (BEM_D_SMEM) {
+                                    dx = ws.dd[(3 * k) * 32 + lane];
+                                    dy = ws.dd[(3 * k + 1) * 32 + lane];
+                                    dz = ws.dd[(3 * k + 2) * 32 + lane];
+                                } else {
+                                    diff(k, dx, dy, dz);
+                                }
                                 acc8[k][1] = fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], fma2(h1x, eacc[k][3], acc8[k][1])));
                                 acc8[k][2] = fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], fma2(h1y, eacc[k][3], acc8[k][2])));
                                 acc8[k][3] = fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], fma2(h1z, eacc[k][3], acc8[k][3])));
@@ -1018,7 +1046,13 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
-                            diff(k, dx, dy, dz);
+                            if constexpr (BEM_D_SMEM) {
+                                dx = ws.dd[(3 * k) * 32 + lane];
+                                dy = ws.dd[(3 * k + 1) * 32 + lane];
+                                dz = ws.dd[(3 * k + 2) * 32 + lane];
+                            } else {
+                                diff(k, dx, dy, dz);
+                            }
                             const float2* c = eacc[k];
                             const float2 mx = fma2(c[1], dx, fma2(c[2], h0x, mul2(c[3], h1x)));
                             const float2 my = fma2(c[1], dy, fma2(c[2], h0y, mul2(c[3], h1y)));

@@ -1,8 +1,9 @@
 // k_near.cu -- analytic near field (FP64) over the compacted near-pair list,
 // and the per-point finalisation.
 //
-// Below the near limit (DR < 3 by default, Sec. 4) the paper integrates the
-// element analytically; it cites the formulas without printing them.  For a
+// Below the near limit (by default DR < 4.5 for triangles and 6 for
+// rectangles, Sec. 4) the element is integrated analytically; the paper
+// cites the formulas without printing them.  For a
 // uniformly charged planar polygon with unit normal n (corners counter-
 // clockwise about n) and field point P at signed height h = (P - V)·n:
 //   int dA / R         = sum_e d_e l_e - h Omega

@@ -143,13 +143,6 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
     if (i < n) out[i] += offs[i / kScanTile];
 }
 
-int bits_for(int n) {
-    // about one point per cell (1..7 bits per axis): the Z-order curve then
-    // orders the points finely, so 32 x PT consecutive points are compact
-    int b = 1;
-    while (b < 7 && (1 << (3 * b)) < n) ++b;
-    return b;
-}
 
 }  // namespace
 
@@ -188,7 +181,7 @@ int launch_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t
 int launch_sort_points(bem_mesh* m, const double* pts, int n, cudaStream_t s, const int* n_dev) {
     Work& w = m->w;
     BEM_CUDA_TRY(cudaMemsetAsync(w.counters + 15, 0, sizeof(unsigned long long), s));
-    const int bits = bits_for(n);
+    const int bits = sort_cell_bits((size_t)n);
     const int ncell = 1 << (3 * bits);
     unsigned* bb = reinterpret_cast<unsigned*>(w.bbox);
     k_bbox_init<<<1, 32, 0, s>>>(bb);

@@ -26,7 +26,8 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 constexpr size_t kMaxPts = BEM_NOALLOC_MAX_POINTS;
 constexpr size_t kMaxNear = BEM_NOALLOC_MAX_NEAR;
 constexpr size_t kChunksCap = kMaxChunks;  // element chunks of the far-field pass (at most kMaxChunks per mesh)
-constexpr size_t kCellsMax = 32768;    // the sort uses at most 2^(3*5) cells for <= 2^14 points
+// cells of the spatial sort for at most kMaxPts points (the sort's own rule)
+constexpr size_t kCellsMax = size_t(1) << (3 * sort_cell_bits(kMaxPts));
 constexpr size_t kScanInts = 16384;    // block sums of every scan level, with room to spare
 
 // byte offsets of the scratch areas inside the array
@@ -72,14 +73,6 @@ int scratch_base(int dev, unsigned char** out) {
     return BEM_OK;
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 }  // namespace
 }  // namespace bem
@@ -100,7 +93,15 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     if (n == 0) return BEM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     BEM_CUDA_TRY(cudaSetDevice(m->device));
-    if (!points || !on_device(points) || (phi && !on_device(phi)) || (E && !on_device(E))) {
+    {
+        const void* ptrs[3] = {points, phi, E};
+        const char* names[3] = {"points", "phi", "E"};
+        int rc0 = reject_other_device("bem_eval_noalloc", m->device, ptrs, names, 3);
+        if (rc0) return rc0;
+    }
+    const int dev = m->device;
+    if (!points || ptr_location(points, dev) != kPtrDevice || (phi && ptr_location(phi, dev) != kPtrDevice) ||
+        (E && ptr_location(E, dev) != kPtrDevice)) {
         set_error("bem_eval_noalloc: points, phi and E must be device arrays (no staging buffers are used)");
         return BEM_ERR_INVALID;
     }

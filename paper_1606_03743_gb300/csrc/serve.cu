@@ -98,7 +98,7 @@ constexpr size_t kCountersN = 24;
 
 template <typename T>
 int slot_alloc(bem_server* sv, Slot& sl, T** p, size_t count) {
-    const cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+    const cudaError_t e = dev_malloc((void**)p, sizeof(T) * (count ? count : 1));
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("bem_server_create: cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
@@ -165,11 +165,11 @@ int slot_setup(bem_server* sv, Slot& sl) {
         return rc;
     w.cap_pts = cap;
     w.cap_near = sv->near_cap;
-    BEM_CUDA_TRY(cudaMallocHost((void**)&sl.h_pts, sizeof(double) * 3 * cap));
-    BEM_CUDA_TRY(cudaMallocHost((void**)&sl.h_phi, sizeof(double) * cap));
-    BEM_CUDA_TRY(cudaMallocHost((void**)&sl.h_E, sizeof(double) * 3 * cap));
-    BEM_CUDA_TRY(cudaMallocHost((void**)&sl.h_n, sizeof(int)));
-    BEM_CUDA_TRY(cudaMallocHost((void**)&sl.h_near, sizeof(unsigned long long)));
+    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_pts, sizeof(double) * 3 * cap));
+    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_phi, sizeof(double) * cap));
+    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_E, sizeof(double) * 3 * cap));
+    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_n, sizeof(int)));
+    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_near, sizeof(unsigned long long)));
     BEM_CUDA_TRY(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
     BEM_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
 

@@ -104,7 +104,7 @@ struct Buffers {
         for (void* p : ptrs) cudaFree(p);
     }
     int get(double** p, size_t count) {
-        const cudaError_t e = cudaMalloc((void**)p, (count > 0 ? count : 1) * sizeof(double));
+        const cudaError_t e = dev_malloc((void**)p, (count > 0 ? count : 1) * sizeof(double));
         if (e != cudaSuccess) {
             cudaGetLastError();
             *p = nullptr;
@@ -116,14 +116,9 @@ struct Buffers {
     }
 };
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// rhs and sigma are only copied (never read by a kernel), so any array the
+// runtime can copy is accepted: host memory or any GPU's memory
+bool on_device(const void* p, int dev) { return ptr_location(p, dev) != kPtrHost; }
 
 struct Ctx {
     bem_mesh* m;
@@ -344,11 +339,11 @@ extern "C" int bem_solve(bem_mesh* m, const double* rhs, double* sigma, const be
     sv.y.assign(restart, 0.0);
     sv.col.assign(2 * (restart + 2), 0.0);
 
-    const bool rhs_dev = on_device(rhs), sig_dev = on_device(sigma);
-    BEM_CUDA_TRY(cudaMemcpyAsync(b, rhs, sizeof(double) * n, rhs_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    const bool rhs_dev = on_device(rhs, m->device), sig_dev = on_device(sigma, m->device);
+    BEM_CUDA_TRY(cudaMemcpyAsync(b, rhs, sizeof(double) * n, rhs_dev ? cudaMemcpyDefault : cudaMemcpyHostToDevice, s));
     if (flags & BEM_SOLVE_X0)
         BEM_CUDA_TRY(cudaMemcpyAsync(x, sigma, sizeof(double) * n,
-                                     sig_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+                                     sig_dev ? cudaMemcpyDefault : cudaMemcpyHostToDevice, s));
     else
         BEM_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     if ((rc = launch_self_potential(m, sv.diag, s))) return rc;
@@ -396,7 +391,7 @@ extern "C" int bem_solve(bem_mesh* m, const double* rhs, double* sigma, const be
             count_launches(1);
         }
     }
-    BEM_CUDA_TRY(cudaMemcpyAsync(sigma, x, sizeof(double) * n, sig_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(sigma, x, sizeof(double) * n, sig_dev ? cudaMemcpyDefault : cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (info) {
         info[0] = (double)products;

@@ -104,3 +104,34 @@ def test_library_rules_match_oracle_tables():
                 o = np.stack([orc[:, 0], orc[:, 1], orc[:, 3]], 1)
             key = lambda a: a[np.lexsort((a[:, 1], a[:, 0]))]
             assert np.allclose(key(lib), key(o), rtol=0, atol=1e-15)
+
+
+def test_library_default_limits_match_oracle():
+    """The library's default DR band limits (bem_default_limits) are the
+    oracle's frozen table, which tests/test_oracle_field.py pins against the
+    2e-15 criterion of Sec. 4."""
+    assert np.array_equal(bem.bem_default_limits(), oracle.default_limits())
+
+
+def test_corner_value_coefficients():
+    """bem_linear_coef_from_corners: a density linear in space, sampled at the
+    corners, is reproduced at every corner by the coefficients in the frame
+    coordinates of Eq. 3.2 / Eq. 3.3; a triangle takes the mean of its three
+    values at its centroid; an unknown type is rejected."""
+    import synth
+    mesh = synth.plate_mesh(seed=1, n=3)
+    rng = np.random.default_rng(5)
+    a, c0 = rng.normal(size=3), 1.3
+    vals = c0 + mesh.verts @ a
+    coef = bem.linear_coef_from_corner_values(mesh.types, vals)
+    for t, cf, val in zip(mesh.types, coef, vals):
+        if t == bem.TRIANGLE:  # (alpha, beta) at A, B, C = (1, 0), (0, 1), (-1, -1)
+            ab, want = np.array([[1, 0], [0, 1], [-1, -1]]), val[:3]
+        else:  # natural coordinates of P0..P3
+            ab, want = np.array([[-1, -1], [1, -1], [1, 1], [-1, 1]]), val
+        assert np.allclose(cf[0] + ab @ cf[1:], want, rtol=1e-14, atol=1e-14)
+    one = bem.linear_coef_from_corner_values(np.array([0], np.int32), np.array([[0.3, 1.9, -0.4, 0.0]]))
+    m = (0.3 + 1.9 - 0.4) / 3
+    assert np.allclose(one, [[m, 0.3 - m, 1.9 - m]], rtol=1e-15)
+    with pytest.raises(bem.BemError):
+        bem.linear_coef_from_corner_values(np.array([2], np.int32), np.zeros((1, 4)))

@@ -2,8 +2,10 @@
 
 Tolerances (stated by the method's targets): FP64 path 1e-12 relative in phi
 and |E|; mixed path 1e-6 relative for field points whose distance ratio to
-every element is at least the near limit 3 (min DR >= 3), and 1e-5 for the
-rest (their far-field share is still FP32).
+every element is at least 3 (min DR >= 3: the paper's near limit for the
+potential; the defaults for potential and field together, 4.5 and 6, treat
+more pairs analytically in FP64), and 1e-5 for the rest (their far-field
+share is still FP32).
 """
 import numpy as np
 import pytest

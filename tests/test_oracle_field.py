@@ -216,6 +216,46 @@ def test_paper_triangle_bands_reproduced(golden_dir):
         assert below > g["target"], (N, below)
 
 
+TARGET = 2e-15  # Sec. 4: the relative accuracy the printed limits are chosen for
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("type_", [TRI, RECT])
+def test_default_limits_meet_the_field_target(type_):
+    """Sec. 4: with potential and field computed together, each rule serves
+    from the DR at which the field (the stricter of the two) reaches the
+    2e-15 level.  The frozen default table (reading 1) is pinned by the
+    paper's own experiment on fresh random elements: at every limit, the
+    near limit included, the rule of the band above it meets 2e-15 in both
+    mean err(phi) and mean err(E); at 0.7 x the limit it misses in one of
+    them (the limit was not rounded up by more than that)."""
+    from oracle import dr_experiment
+    lim = oracle.default_limits()[type_]
+    for k in range(5):
+        r = 4 - k  # the rule of the band [lim[k], lim[k+1]): 33 points above lim[0] ... 4 above lim[4]
+        at = dr_experiment.errors(type_, float(lim[k]), n_el=2000, seed=901 + k)[r]
+        below = dr_experiment.errors(type_, 0.7 * float(lim[k]), n_el=2000, seed=911 + k)[r]
+        assert at[0] <= TARGET and at[1] <= TARGET, (k, lim[k], at)
+        assert max(below) > TARGET, (k, lim[k], below)
+
+
+@pytest.mark.slow
+def test_potential_only_limits_fail_the_field_target(golden_dir):
+    """The check above catches a table calibrated on the potential alone: the
+    paper's printed triangle-potential limits (Sec. 4) give mean field errors
+    above 2e-15 at their lower ends, while their potential errors meet it."""
+    from oracle import dr_experiment
+    with open(os.path.join(golden_dir, "paper_bands.json")) as f:
+        g = json.load(f)
+    idx = {"4": 0, "7": 1, "12": 2, "19": 3, "33": 4}
+    worst_E = 0.0
+    for N, lim in g["triangle_phi_lower_limit_by_N"].items():
+        e = dr_experiment.errors(TRI, float(lim), n_el=2000, seed=921 + idx[N])[idx[N]]
+        assert e[0] <= 1.5 * TARGET, (N, e)
+        worst_E = max(worst_E, e[1])
+    assert worst_E > 2 * TARGET, worst_E
+
+
 def test_gl2_accurate_above_dr2(golden_dir):
     """Sec. 2: GL2 with 16 x 16 nodes is accurate to ~1e-15 above DR = 2;
     checked against brute-force subdivision."""
