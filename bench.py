@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (latency) measurement")
     ap.add_argument("--no-assembly", action="store_true", help="skip the collocation-assembly measurement")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-tick", type=int, default=32768, help="points per serving tick (larger requests split)")
     ap.add_argument("--no-large", action="store_true", help="skip the 500k-element x 4M-point mixed vs FP64 run")
     ap.add_argument("--grad-points", type=int, default=16384, help="points of the FP64 field-gradient line")
     ap.add_argument("--grad-points-mixed", type=int, default=262144, help="points of the mixed field-gradient line")
@@ -692,11 +693,25 @@ def large_mixed_vs_fp64(a, bem, torch):
     return out
 
 
-def run_server(bem, m, reqs, rate, n_el):
+SIZE_CLASSES = ((1, 1000), (1001, 10000), (10001, 100000))
+
+
+def latency_classes(ms, sizes) -> dict:
+    """p50 / p99 latency per request-size class (points)."""
+    out = {}
+    for lo, hi in SIZE_CLASSES:
+        sel = (sizes >= lo) & (sizes <= hi)
+        if sel.any():
+            out[f"{lo}-{hi}"] = {"n": int(sel.sum()), "p50_ms": float(np.percentile(ms[sel], 50)),
+                                 "p99_ms": float(np.percentile(ms[sel], 99)), "max_ms": float(ms[sel].max())}
+    return out
+
+
+def run_server(bem, m, reqs, rate, n_el, tick):
     """Poisson arrivals at `rate` requests/s into a server on mesh m; returns
     latency statistics (measured by the library, submission to results on
-    the host) and throughput."""
-    srv = bem.Server(m)
+    the host), overall and per request-size class, and throughput."""
+    srv = bem.Server(m, max_points_per_tick=tick)
     rng = np.random.default_rng(55)
     gaps = rng.exponential(1.0 / rate, len(reqs))
     tickets = []
@@ -712,10 +727,12 @@ def run_server(bem, m, reqs, rate, n_el):
         srv.wait(t, timeout=600)
     wall = time.perf_counter() - t0
     st = srv.stats()
+    ms, sizes = srv.latencies()
     srv.close()
     pts = sum(len(r) for r in reqs)
     return {"requests": len(reqs), "points": int(pts), "rate_req_per_s": rate, "p50_ms": st["p50_ms"],
-            "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "ticks": int(st["ticks"]),
+            "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "by_size": latency_classes(ms, sizes),
+            "points_per_tick": int(st["points_per_tick"]), "ticks": int(st["ticks"]),
             "fallback_ticks": int(st["fallback_ticks"]), "graph_launches": int(st["graph_launches"]),
             "throughput_pairs_per_s": pts * n_el / wall, "wall_s": wall}
 
@@ -745,14 +762,14 @@ def serving(a, bem, torch):
             sel = [r for r in reqs if len(r) <= 2000][:20]
         mean_size = float(np.mean([len(r) for r in sel]))
         rate = 0.7 * cap_pts / mean_size
-        out[name] = run_server(bem, m, sel, rate, mesh.n)
+        out[name] = run_server(bem, m, sel, rate, mesh.n, a.serve_tick)
         out[name]["capacity_points_per_s"] = cap_pts
         if prec == bem.FP64:
             # the same capped subset on the mixed path, at the same arrival rate
             m.close()
             m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
                          torch.from_numpy(mesh.sigma).to(dev), precision=bem.MIXED)
-            out["mixed_same_subset_as_fp64"] = run_server(bem, m, sel, rate, mesh.n)
+            out["mixed_same_subset_as_fp64"] = run_server(bem, m, sel, rate, mesh.n, a.serve_tick)
         m.close()
     return out
 

@@ -393,21 +393,29 @@ int bem_eval_noalloc(bem_mesh* mesh, const double* points, int64_t n, double* ph
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of field-point queries on a device-resident
  * mesh (a particle tracker's stream of uneven requests).  A server thread
- * forms ticks: it admits queued requests in arrival order while their
- * points fit one tick's device buffers, copies them in, replays one CUDA
- * graph of the whole evaluation (captured at creation; the persistent
- * far-field kernel walks (point tile x element chunk) work items), and
- * copies the results back.  Two ticks can be in flight, so requests that
- * arrive while one tick runs are admitted into the next and overlap it.
- * Each result equals bem_eval's for the same points bit for bit, whatever
- * other requests shared its tick.  While a server exists it owns the mesh:
- * make no other call on that mesh until bem_server_destroy.
+ * forms ticks of at most max_points_per_tick points: first every waiting
+ * small request (at most 1/8 of a tick) whole, in arrival order, then the
+ * other requests in arrival order, splitting one that does not fit the
+ * space left (its next piece goes into this tick, the rest into later
+ * ticks).  A tick's points are copied in, one CUDA graph of the whole
+ * evaluation (captured at creation; the persistent far-field kernel walks
+ * (point tile x element chunk) work items) is replayed, and the results are
+ * copied back.  Two ticks can be in flight, so requests that arrive while
+ * one tick runs are admitted into the next and overlap it; at most one of
+ * them holds pieces of large requests, so a small request waits behind at
+ * most one tick of large work.  Each result equals bem_eval's for the same
+ * points bit for bit, whatever other requests shared its ticks and however
+ * it was split.  While a server exists it owns the mesh: make no other call
+ * on that mesh until bem_server_destroy.
  * ------------------------------------------------------------------------ */
 typedef struct bem_server bem_server;
 
 typedef struct {
     int64_t max_points_per_tick;     /* points one tick can take (0: 131072); a
-                                        request may not exceed it */
+                                        larger request is split across ticks.
+                                        Smaller ticks finish sooner (lower
+                                        latency for small requests), larger
+                                        ones fill the GPU better */
     int64_t max_near_pairs_per_tick; /* near-field pairs one tick can take (0: 2^21);
                                         a tick that has more evaluates its
                                         requests one by one with bem_eval */
@@ -425,8 +433,8 @@ int bem_server_create(bem_mesh* mesh, const bem_server_options* opt, bem_server*
 void bem_server_destroy(bem_server* server);
 
 /* Queue n field points (host array [n][3], copied) for evaluation; *ticket
- * names the request.  Thread-safe.  BEM_ERR_INVALID for n < 1, n above the
- * tick capacity or a non-finite coordinate. */
+ * names the request.  Thread-safe.  BEM_ERR_INVALID for n < 1 or a
+ * non-finite coordinate; BEM_ERR_OOM if the host copy cannot be made. */
 int bem_submit(bem_server* server, const double* points, int64_t n, uint64_t* ticket);
 
 /* Non-blocking: *done = 1 and the results copied to phi [n] / E [n][3]
@@ -454,6 +462,12 @@ int bem_server_pause(bem_server* server, int32_t paused);
  * to per-request evaluation, out[7] points per tick (capacity), out[8]
  * device bytes held, out[9] graph launches. */
 int bem_server_stats(bem_server* server, int32_t reset, double* out /* 10 */);
+
+/* Latency of every request completed since creation or the last stats reset,
+ * in completion order: ms[i] (submission to results on the host) and
+ * points[i] (its size), for i < min(cap, *count); *count receives the number
+ * of completed requests.  Host arrays of cap entries (cap = 0: count only). */
+int bem_server_latencies(bem_server* server, int64_t cap, double* ms, int64_t* points, int64_t* count);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bem_last_error(void);

@@ -95,6 +95,7 @@ def load_library(build_if_missing: bool = True):
     lib.bem_cancel.argtypes = [vp, C.c_uint64]
     lib.bem_server_pause.argtypes = [vp, C.c_int32]
     lib.bem_server_stats.argtypes = [vp, C.c_int32, d]
+    lib.bem_server_latencies.argtypes = [vp, C.c_int64, d, i64, i64]
     lib.bem_set_sigma_linear.argtypes = [vp, vp, vp]
     lib.bem_set_sigma_linear.restype = C.c_int
     lib.bem_set_sigma_quadratic.argtypes = [vp, vp, vp]
@@ -110,7 +111,7 @@ def load_library(build_if_missing: bool = True):
     lib.bem_peak_rate.argtypes = [C.c_int32, d]
     lib.bem_peak_rate.restype = C.c_int
     for name in ("bem_server_create", "bem_submit", "bem_poll", "bem_wait", "bem_cancel", "bem_server_pause",
-                 "bem_server_stats"):
+                 "bem_server_stats", "bem_server_latencies"):
         getattr(lib, name).restype = C.c_int
     lib.bem_last_error.restype = C.c_char_p
     lib.bem_version.restype = C.c_char_p
@@ -558,3 +559,15 @@ class Server:
                                                out.ctypes.data_as(C.POINTER(C.c_double))))
         return dict(zip(SERVER_STAT_NAMES, out.tolist()))
 
+    def latencies(self):
+        """(ms, points) of every request completed since creation or the last
+        stats reset: latency from submission to results on the host, and size."""
+        lib = load_library()
+        count = C.c_int64()
+        _check(lib.bem_server_latencies(self._h, 0, None, None, C.byref(count)))
+        n = count.value
+        ms, pts = np.zeros(n), np.zeros(n, np.int64)
+        _check(lib.bem_server_latencies(self._h, n, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                        pts.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(count)))
+        k = min(n, count.value)
+        return ms[:k], pts[:k]

@@ -271,13 +271,22 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
         a.stats = m->stats;
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[1], s));
-        int rc = launch_far(m, a, s);
-        if (rc) return rc;
+        int rc;
+        {
+            NvtxRange r("bem.far");
+            if ((rc = launch_far(m, a, s))) return rc;
+        }
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[2], s));
-        if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n * m->n_chunks, w.scan_tmp, s))) return rc;
-        if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s, eval_slope(m, dsigma)))) return rc;
+        {
+            NvtxRange r("bem.near");
+            if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n * m->n_chunks, w.scan_tmp, s))) return rc;
+            if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s, eval_slope(m, dsigma)))) return rc;
+        }
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[3], s));
-        if ((rc = launch_finalize(m, w.perm, n, dphi, dE, stride4, s))) return rc;
+        {
+            NvtxRange r("bem.finalize");
+            if ((rc = launch_finalize(m, w.perm, n, dphi, dE, stride4, s))) return rc;
+        }
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[4], s));
         unsigned long long cnt[kCounters];
         BEM_CUDA_TRY(cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, s));
@@ -654,7 +663,10 @@ int eval_slice(bem_mesh* m, const double* points, int64_t n, double* phi, double
         return BEM_ERR_INVALID;
     }
     if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[0], s));
-    if ((rc = launch_sort_points(m, dpts, (int)n, s))) return rc;
+    {
+        NvtxRange r("bem.sort");
+        if ((rc = launch_sort_points(m, dpts, (int)n, s))) return rc;
+    }
     if ((rc = check_points(m, "bem_eval", s))) return rc;
     if (!phi_host && !E_host) return run_eval(m, dpts, (int)n, m->d.sigma, phi, E, 0, E != nullptr, s);
     // host outputs: finalise into the staging buffer (phi | E), then copy out
@@ -672,6 +684,7 @@ constexpr int64_t kEvalSlice = int64_t(1) << 21;
 }  // namespace
 
 int bem_eval(bem_mesh* m, const double* points, int64_t n, double* phi, double* E, void* stream) {
+    NvtxRange range("bem_eval");
     int rc = check_mesh(m, "bem_eval");
     if (rc) return rc;
     if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && !points)) {
@@ -784,6 +797,7 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
 extern "C" {
 
 int bem_eval_grad(bem_mesh* m, const double* points, int64_t n, double* G, void* stream) {
+    NvtxRange range("bem_eval_grad");
     int rc = check_mesh(m, "bem_eval_grad");
     if (rc) return rc;
     if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && (!points || !G))) {
@@ -806,6 +820,7 @@ int bem_eval_grad(bem_mesh* m, const double* points, int64_t n, double* G, void*
 }
 
 int bem_matvec(bem_mesh* m, const double* x, double* y, void* stream) {
+    NvtxRange range("bem_matvec");
     int rc = check_mesh(m, "bem_matvec");
     if (rc) return rc;
     if (!x || !y) {
@@ -838,6 +853,7 @@ int bem_matvec(bem_mesh* m, const double* x, double* y, void* stream) {
 }
 
 int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, void* stream) {
+    NvtxRange range("bem_assemble");
     int rc = check_mesh(m, "bem_assemble");
     if (rc) return rc;
     if (mrows < 0 || mrows >= (int64_t(1) << 31) || (mrows > 0 && (!colloc || !A))) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -131,6 +132,15 @@ int reject_other_device(const char* fn, int dev, const void* const* ptrs, const 
 // cudaErrorMemoryAllocation without calling the runtime.
 cudaError_t dev_malloc(void** p, size_t bytes);
 cudaError_t pinned_malloc(void** p, size_t bytes);
+
+// A named NVTX range over a phase of host-side work (the launches of one
+// step of the path), visible to Nsight tools; no cost without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void set_error(const char* fmt, ...);
 void count_launches(int n);  // adds n to the process-wide kernel launch counter

@@ -4,8 +4,14 @@
 // A particle tracker asks for phi and E at the successive positions of its
 // tracks, in requests of very uneven size.  The server keeps the mesh on the
 // GPU and runs a host thread that forms "ticks":
-//  * requests wait in a FIFO; a tick admits them from the front while their
-//    points fit the tick's device buffers (the memory admitted per tick);
+//  * requests wait in a queue; a tick takes points up to the capacity of its
+//    device buffers (the memory admitted per tick): first every waiting
+//    small request (at most 1/8 of a tick) in arrival order, whole, then the
+//    other requests in arrival order, a request larger than the space left
+//    being split -- its next piece goes into this tick, the rest into later
+//    ones.  At most one tick holding pieces of large requests is on the GPU
+//    at a time, so a small request never waits behind more than one such
+//    tick;
 //  * the points are packed into pinned host memory, copied to the device,
 //    and one CUDA graph -- the whole evaluation (spatial sort, the persistent
 //    far-field kernel over (point tile x element chunk) work items, the
@@ -49,6 +55,18 @@ struct Req {
     int state = kPending;
     int status = BEM_OK;
     bool cancelled = false;
+    bool queued = true;     // still in the pending queue (points not yet admitted)
+    int64_t next = 0;       // points [0, next) have been admitted into ticks
+    int64_t done_pts = 0;   // points whose results have come back
+    int in_flight = 0;      // pieces on the GPU
+};
+
+// A contiguous run of one request's points inside a tick.
+struct Piece {
+    Req* r;
+    int64_t roff;  // first point within the request
+    int64_t n;     // points
+    int64_t soff;  // first point within the tick
 };
 
 struct Slot {
@@ -62,10 +80,10 @@ struct Slot {
     double *h_pts = nullptr, *h_phi = nullptr, *h_E = nullptr;  // pinned
     int* h_n = nullptr;
     unsigned long long* h_near = nullptr;
-    std::vector<Req*> reqs;
-    std::vector<int64_t> offs;
+    std::vector<Piece> pieces;
     int64_t n = 0;
     bool busy = false;
+    bool large = false;  // holds pieces of requests larger than a small one
     std::vector<void*> dev_allocs;
 };
 
@@ -87,6 +105,7 @@ struct bem_server {
     uint64_t next_ticket = 1;
     bool stop = false, paused = false;
     std::vector<double> lat_ms;
+    std::vector<int64_t> lat_n;  // points of each request in lat_ms
     int64_t ticks = 0, points_done = 0, fallbacks = 0, graph_launches = 0;
     std::string thread_error;
 };
@@ -210,27 +229,75 @@ void slot_free(Slot& sl) {
     cudaFreeHost(sl.h_near);
 }
 
-// Admit requests from the front of the queue into a free slot and launch the
-// tick.  Called with the lock held; returns false if nothing was admitted.
-bool fill_and_launch(bem_server* sv, Slot& sl, std::unique_lock<std::mutex>& lk) {
-    sl.reqs.clear();
-    sl.offs.clear();
-    int64_t n = 0;
-    while (!sv->pending.empty()) {
-        Req* r = sv->pending.front();
-        if (n + r->n > sv->cap) break;
-        sv->pending.pop_front();
-        if (r->cancelled) continue;
-        r->state = kRunning;
-        sl.reqs.push_back(r);
-        sl.offs.push_back(n);
-        n += r->n;
+// Drop a request that is neither queued nor on the GPU.  Lock held.
+void forget(bem_server* sv, Req* r) {
+    sv->reqs.erase(r->ticket);
+    delete r;
+}
+
+// A request has failed: no further piece of it is admitted.  Lock held.
+void fail_request(bem_server* sv, Req* r, int status) {
+    r->state = kFailed;
+    r->status = status;
+    if (r->queued) {
+        sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
+        r->queued = false;
     }
-    if (sl.reqs.empty()) return false;
+}
+
+// Its results are complete, or it failed and nothing of it is left on the GPU.
+bool finished(const Req* r) { return r->state == kDone || (r->state == kFailed && r->in_flight == 0 && !r->queued); }
+
+// Requests of at most this many points are small: admitted whole, ahead of
+// the pieces of larger ones.
+int64_t small_limit(const bem_server* sv) { return std::max<int64_t>(1, sv->cap / 8); }
+
+// Admit points of waiting requests into a free slot and launch the tick
+// (policy at the top of this file).  Called with the lock held; returns false
+// if nothing was admitted.
+bool fill_and_launch(bem_server* sv, Slot& sl, bool allow_large, std::unique_lock<std::mutex>& lk) {
+    sl.pieces.clear();
+    sl.large = false;
+    const int64_t small = small_limit(sv);
+    int64_t n = 0;
+    auto admit = [&](Req* r, int64_t take) {
+        sl.pieces.push_back(Piece{r, r->next, take, n});
+        r->next += take;
+        ++r->in_flight;
+        r->state = kRunning;
+        n += take;
+        if (r->n > small) sl.large = true;
+    };
+    // small requests first, whole, in arrival order
+    for (Req* r : sv->pending) {
+        if (r->cancelled || r->n > small) continue;
+        const int64_t rem = r->n - r->next;
+        if (rem > 0 && n + rem <= sv->cap) admit(r, rem);
+    }
+    // then the rest in arrival order, the last one split to fill the tick
+    if (allow_large) {
+        for (Req* r : sv->pending) {
+            if (n >= sv->cap) break;
+            if (r->cancelled) continue;
+            const int64_t rem = r->n - r->next;
+            if (rem > 0) admit(r, std::min(rem, sv->cap - n));
+        }
+    }
+    // fully admitted requests leave the queue
+    for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+        if ((*it)->next == (*it)->n || (*it)->cancelled) {
+            (*it)->queued = false;
+            it = sv->pending.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (sl.pieces.empty()) return false;
     sl.n = n;
     lk.unlock();
-    for (size_t i = 0; i < sl.reqs.size(); ++i)
-        memcpy(sl.h_pts + 3 * sl.offs[i], sl.reqs[i]->pts.data(), sizeof(double) * 3 * sl.reqs[i]->n);
+    NvtxRange range("bem.tick");
+    for (const Piece& pc : sl.pieces)
+        memcpy(sl.h_pts + 3 * pc.soff, pc.r->pts.data() + 3 * pc.roff, sizeof(double) * 3 * pc.n);
     *sl.h_n = (int)n;
     cudaError_t e = cudaMemcpyAsync(sl.d_n, sl.h_n, sizeof(int), cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess)
@@ -247,11 +314,11 @@ bool fill_and_launch(bem_server* sv, Slot& sl, std::unique_lock<std::mutex>& lk)
     lk.lock();
     if (e != cudaSuccess) {
         sv->thread_error = cudaGetErrorString(e);
-        for (Req* r : sl.reqs) {
-            r->state = kFailed;
-            r->status = BEM_ERR_CUDA;
+        for (const Piece& pc : sl.pieces) {
+            --pc.r->in_flight;
+            fail_request(sv, pc.r, BEM_ERR_CUDA);
         }
-        sl.reqs.clear();
+        sl.pieces.clear();
         sv->cv_done.notify_all();
         return false;
     }
@@ -261,40 +328,42 @@ bool fill_and_launch(bem_server* sv, Slot& sl, std::unique_lock<std::mutex>& lk)
     return true;
 }
 
+
 // Hand a finished tick's results to its requests.  Called without the lock.
 void harvest(bem_server* sv, Slot& sl) {
     const bool overflow = *sl.h_near > sl.view.w.cap_near;
-    std::vector<int> status(sl.reqs.size(), BEM_OK);
-    for (size_t i = 0; i < sl.reqs.size(); ++i) {
-        Req* r = sl.reqs[i];
-        r->phi.resize(r->n);
-        r->E.resize(3 * r->n);
+    std::vector<int> status(sl.pieces.size(), BEM_OK);
+    for (size_t i = 0; i < sl.pieces.size(); ++i) {
+        const Piece& pc = sl.pieces[i];
+        Req* r = pc.r;  // its result arrays were sized at submission; pieces write disjoint ranges
         if (!overflow) {
-            memcpy(r->phi.data(), sl.h_phi + sl.offs[i], sizeof(double) * r->n);
-            memcpy(r->E.data(), sl.h_E + 3 * sl.offs[i], sizeof(double) * 3 * r->n);
+            memcpy(r->phi.data() + pc.roff, sl.h_phi + pc.soff, sizeof(double) * pc.n);
+            memcpy(r->E.data() + 3 * pc.roff, sl.h_E + 3 * pc.soff, sizeof(double) * 3 * pc.n);
         } else {
-            // the tick's near-pair list overflowed: evaluate this request on its own
-            status[i] = bem_eval(sv->mesh, r->pts.data(), r->n, r->phi.data(), r->E.data(), sv->side);
+            // the tick's near-pair list overflowed: evaluate this piece on its own
+            status[i] = bem_eval(sv->mesh, r->pts.data() + 3 * pc.roff, pc.n, r->phi.data() + pc.roff,
+                                 r->E.data() + 3 * pc.roff, sv->side);
         }
     }
     const Clock::time_point now = Clock::now();
     std::lock_guard<std::mutex> lk(sv->mu);
     if (overflow) ++sv->fallbacks;
-    for (size_t i = 0; i < sl.reqs.size(); ++i) {
-        Req* r = sl.reqs[i];
-        r->t_done = now;
-        r->status = status[i];
-        r->state = status[i] == BEM_OK ? kDone : kFailed;
-        if (r->state == kDone) {
+    for (size_t i = 0; i < sl.pieces.size(); ++i) {
+        const Piece& pc = sl.pieces[i];
+        Req* r = pc.r;
+        --r->in_flight;
+        if (status[i] != BEM_OK) fail_request(sv, r, status[i]);
+        r->done_pts += pc.n;
+        if (r->state != kFailed && r->done_pts == r->n) {
+            r->t_done = now;
+            r->state = kDone;
             sv->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+            sv->lat_n.push_back(r->n);
             sv->points_done += r->n;
         }
-        if (r->cancelled) {
-            sv->reqs.erase(r->ticket);
-            delete r;
-        }
+        if (r->cancelled && r->in_flight == 0 && !r->queued) forget(sv, r);
     }
-    sl.reqs.clear();
+    sl.pieces.clear();
     sl.busy = false;
     sv->cv_done.notify_all();
 }
@@ -314,11 +383,13 @@ void server_loop(bem_server* sv) {
             }
         }
         if (sv->stop && sv->pending.empty() && !sv->slot[0].busy && !sv->slot[1].busy) break;
-        // launch into the free slot (ticks run in submission order)
+        // launch into the free slot (ticks run in submission order); pieces of
+        // large requests only while the other slot holds none
         bool launched = false;
         Slot& sl = sv->slot[next];
+        const Slot& other = sv->slot[next ^ 1];
         if (!sl.busy && !sv->paused && !sv->pending.empty()) {
-            launched = fill_and_launch(sv, sl, lk);
+            launched = fill_and_launch(sv, sl, !(other.busy && other.large), lk);
             if (launched) next ^= 1;
         }
         if (launched) continue;
@@ -414,10 +485,6 @@ int bem_submit(bem_server* sv, const double* points, int64_t n, uint64_t* ticket
         set_error("bem_submit: bad arguments (n = %lld)", (long long)n);
         return BEM_ERR_INVALID;
     }
-    if (n > sv->cap) {
-        set_error("bem_submit: %lld points exceed the %lld points of one tick", (long long)n, (long long)sv->cap);
-        return BEM_ERR_INVALID;
-    }
     for (int64_t i = 0; i < 3 * n; ++i)
         if (!isfinite(points[i]) || fabs(points[i]) >= 1e30) {
             set_error("bem_submit: point %lld has a non-finite coordinate", (long long)(i / 3));
@@ -429,7 +496,15 @@ int bem_submit(bem_server* sv, const double* points, int64_t n, uint64_t* ticket
         return BEM_ERR_OOM;
     }
     r->n = n;
-    r->pts.assign(points, points + 3 * n);
+    try {
+        r->pts.assign(points, points + 3 * n);
+        r->phi.resize(n);
+        r->E.resize(3 * n);
+    } catch (const std::bad_alloc&) {
+        delete r;
+        set_error("bem_submit: out of host memory for %lld points", (long long)n);
+        return BEM_ERR_OOM;
+    }
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -473,7 +548,7 @@ int bem_poll(bem_server* sv, uint64_t ticket, double* phi, double* E, int32_t* d
         return BEM_ERR_NOT_FOUND;
     }
     Req* r = it->second;
-    if (r->state != kDone && r->state != kFailed) {
+    if (!finished(r)) {
         *done = 0;
         return BEM_OK;
     }
@@ -495,9 +570,8 @@ int bem_wait(bem_server* sv, uint64_t ticket, double timeout_s, double* phi, dou
     Req* r = it->second;
     const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
                                              std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
-    while (r->state != kDone && r->state != kFailed) {
-        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state != kDone &&
-            r->state != kFailed) {
+    while (!finished(r)) {
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !finished(r)) {
             set_error("bem_wait: request %llu not finished after %.3f s", (unsigned long long)ticket, timeout_s);
             return BEM_ERR_TIMEOUT;
         }
@@ -517,15 +591,14 @@ int bem_cancel(bem_server* sv, uint64_t ticket) {
         return BEM_ERR_NOT_FOUND;
     }
     Req* r = it->second;
-    if (r->state == kPending) {
+    if (r->queued) {
         sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
-        sv->reqs.erase(it);
-        delete r;
-    } else if (r->state == kRunning) {
-        r->cancelled = true;  // dropped when its tick finishes
+        r->queued = false;
+    }
+    if (r->in_flight > 0) {
+        r->cancelled = true;  // dropped when its last piece's tick finishes
     } else {
-        sv->reqs.erase(it);
-        delete r;
+        forget(sv, r);
     }
     return BEM_OK;
 }
@@ -564,8 +637,25 @@ int bem_server_stats(bem_server* sv, int32_t reset, double* out) {
     out[9] = (double)sv->graph_launches;
     if (reset) {
         sv->lat_ms.clear();
+        sv->lat_n.clear();
         sv->ticks = sv->points_done = sv->fallbacks = sv->graph_launches = 0;
     }
+    return BEM_OK;
+}
+
+int bem_server_latencies(bem_server* sv, int64_t cap, double* ms, int64_t* points, int64_t* count) {
+    if (!sv || !count || cap < 0 || (cap > 0 && (!ms || !points))) {
+        set_error("bem_server_latencies: bad arguments");
+        return BEM_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int64_t n = (int64_t)sv->lat_ms.size();
+    const int64_t k = std::min(n, cap);
+    for (int64_t i = 0; i < k; ++i) {
+        ms[i] = sv->lat_ms[i];
+        points[i] = sv->lat_n[i];
+    }
+    *count = n;
     return BEM_OK;
 }
 

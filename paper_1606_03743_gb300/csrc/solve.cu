@@ -279,6 +279,7 @@ using namespace bem;
 
 extern "C" int bem_solve(bem_mesh* m, const double* rhs, double* sigma, const bem_solve_options* opt, double* info,
                          void* stream) {
+    NvtxRange range("bem_solve");
     if (info) info[0] = info[1] = info[2] = 0.0;
     if (!m) {
         set_error("bem_solve: mesh is NULL");

@@ -30,9 +30,13 @@ def rel_E(a, b):
     return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
 
 
-def sampled_check(mesh, pts, phi, E, idx, tol, kappa_max):
+def sampled_check(mesh, pts, phi, E, idx, tol, kappa_max, bands=False):
     rphi, rE, mdr, esum = oracle.eval_field(mesh.types, mesh.verts, mesh.sigma, pts[idx], return_min_dr=True,
                                             return_esum=True)
+    if bands:  # the sample reaches every band of the nearest element (near, 33, 19|17, 12 points)
+        lim = oracle.default_limits()[0]
+        hist = np.histogram(mdr, bins=[0, lim[0], lim[1], lim[2], lim[3], np.inf])[0]
+        assert (hist[:4] > 0).all(), hist
     kappa = esum / np.linalg.norm(rE, axis=1)
     gate = (mdr >= 3) & (kappa <= kappa_max)
     assert gate.sum() >= len(idx) // 2
@@ -44,21 +48,32 @@ def sampled_check(mesh, pts, phi, E, idx, tol, kappa_max):
 
 @pytest.mark.parametrize("prec,tol,kmax", [(1, 1e-6, 100.0), (0, 1e-12, 1e9)])
 def test_coax_150k_1M(bem, prec, tol, kmax):
+    """512 sampled points against the oracle.  Every band of the nearest
+    element is among them, and the run sends a share of its (warp, element)
+    pairs through the per-point band path of straddling tiles; the same
+    points evaluated on their own (other tiles, other straddling pairs) give
+    the same bits, so both paths agree for them."""
     import torch
     mesh = synth.coax_mesh(seed=2)
     pts = synth.coax_points(seed=2, n=1_000_000)
     dev = torch.device("cuda")
     n = len(pts) if prec == 1 else 65536  # the FP64 kernel on a batch that still spans many tiles
+    idx = np.random.default_rng(11).choice(n, 512, replace=False)
     with bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
                   torch.from_numpy(mesh.sigma).to(dev), precision=prec) as m:
         p_d = torch.from_numpy(pts[:n]).to(dev)
         phi = torch.empty(n, dtype=torch.float64, device=dev)
         E = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        m.set_stats(True)
         bem.bem_eval(m.handle, p_d, phi, E)
+        stats = m.last_stats()
+        m.set_stats(False)
         torch.cuda.synchronize()
         phi, E = phi.cpu().numpy(), E.cpu().numpy()
-    idx = np.random.default_rng(11).choice(n, 48, replace=False)
-    sampled_check(mesh, pts[:n], phi, E, idx, tol, kmax)
+        phi1, E1 = m.eval(pts[idx])
+    assert stats[14] > 0.05 * (stats[13] + stats[14])  # straddling (warp, element) pairs took the per-point path
+    assert np.array_equal(phi[idx], phi1) and np.array_equal(E[idx], E1)
+    sampled_check(mesh, pts[:n], phi, E, idx, tol, kmax, bands=True)
 
 
 def test_coax_500k_4M_sliced(bem):
@@ -79,7 +94,7 @@ def test_coax_500k_4M_sliced(bem):
         phi1, E1 = m.eval(pts[idx])
         phi, E = phi.cpu().numpy(), E.cpu().numpy()
     assert np.array_equal(phi[idx], phi1) and np.array_equal(E[idx], E1)
-    sidx = np.random.default_rng(12).choice(len(pts), 24, replace=False)
+    sidx = np.random.default_rng(12).choice(len(pts), 256, replace=False)
     sampled_check(mesh, pts, phi, E, sidx, 1e-6, 100.0)
 
 

@@ -1,12 +1,14 @@
 """The continuous-batching server (bem_server_*): results equal bem_eval's,
-bit for bit, for a request alone and in a mix of concurrent requests of
-uneven size; bounded waits, cancellation and statistics."""
+bit for bit, for a request alone, in a mix of concurrent requests of uneven
+size and split across ticks, and match the FP64 oracle within the path's
+tolerance; bounded waits, cancellation and statistics."""
 import threading
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -58,6 +60,16 @@ def test_alone_and_in_mix_equal_eval(bem, coax, prec):
         assert np.array_equal(alone[i][0], ref[i][0]) and np.array_equal(alone[i][1], ref[i][1])
     for i in range(len(reqs)):
         assert np.array_equal(mixed[i][0], ref[i][0]), i
+    # and the server's own results against the oracle (every request, a sample of points each)
+    tol = 1e-12 if prec == 0 else 1e-6
+    for i, r in enumerate(reqs):
+        sub = np.arange(0, len(r), max(1, len(r) // 40))
+        rphi, rE, mdr = oracle.eval_field(coax.types, coax.verts, coax.sigma, r[sub], return_min_dr=True)
+        far = mdr >= 3
+        ephi = np.abs(mixed[i][0][sub] - rphi) / np.abs(rphi)
+        eE = np.linalg.norm(mixed[i][1][sub] - rE, axis=1) / np.linalg.norm(rE, axis=1)
+        assert ephi[far].max(initial=0) <= tol and eE[far].max(initial=0) <= tol, i
+        assert ephi.max() <= max(tol, 1e-5) and eE.max() <= max(tol, 1e-5), i
         assert np.array_equal(mixed[i][1], ref[i][1]), i
     assert st["completed"] == len(reqs) + 4
     assert st["ticks"] >= 2 and st["ticks"] < st["completed"]  # requests were batched together
@@ -99,8 +111,6 @@ def test_cancel_and_bad_requests(bem, coax):
             srv.pause(False)
             phi, _ = srv.wait(t2, timeout=60)
             assert phi.shape == (200,)
-            with pytest.raises(bem.BemError):
-                srv.submit(np.zeros((5000, 3)))  # larger than one tick
             bad = synth.coax_points(seed=13, n=10)
             bad[3, 1] = np.nan
             with pytest.raises(bem.BemError):
@@ -119,3 +129,36 @@ def test_small_budget_shrinks_tick_and_near_overflow_falls_back(bem, coax):
             st = srv.stats()
     assert st["fallback_ticks"] >= 1
     assert np.array_equal(phi, ref[0]) and np.array_equal(E, ref[1])
+
+
+def test_large_requests_are_split_across_ticks(bem, coax):
+    """A request larger than one tick is evaluated in pieces over several
+    ticks; small requests submitted behind it are admitted ahead of its later
+    pieces.  Every result equals bem_eval's bit for bit and the oracle's
+    within the mixed-path tolerance."""
+    big = synth.coax_points(seed=15, n=10000)
+    small = [synth.coax_points(seed=16 + k, n=n) for k, n in enumerate((1, 37, 200, 450))]
+    with bem.Mesh(coax.types, coax.verts, coax.sigma, precision=1) as m:
+        ref_big = m.eval(big)
+        ref_small = [m.eval(p) for p in small]
+        with bem.Server(m, max_points_per_tick=4096) as srv:
+            srv.pause(True)
+            tb = srv.submit(big)
+            ts = [srv.submit(p) for p in small]
+            srv.pause(False)
+            phi, E = srv.wait(tb, timeout=120)
+            outs = [srv.wait(t, timeout=120) for t in ts]
+            st = srv.stats()
+            ms, sizes = srv.latencies()
+    assert np.array_equal(phi, ref_big[0]) and np.array_equal(E, ref_big[1])
+    for (p, e), (rp, re) in zip(outs, ref_small):
+        assert np.array_equal(p, rp) and np.array_equal(e, re)
+    assert st["ticks"] >= 3  # 10000 points at 4096 per tick
+    assert len(ms) == 5 and sorted(sizes.tolist()) == [1, 37, 200, 450, 10000]
+    # the small requests finished before the large one's last piece
+    assert ms[list(sizes).index(10000)] == ms.max()
+    # and against the oracle on a sample of the split request's points
+    sub = np.arange(0, len(big), 97)
+    rphi, rE, mdr = oracle.eval_field(coax.types, coax.verts, coax.sigma, big[sub], return_min_dr=True)
+    far = mdr >= 3
+    assert (np.abs(phi[sub] - rphi) / np.abs(rphi))[far].max() <= 1e-6

@@ -75,3 +75,35 @@ def test_noalloc_limits_and_host_arrays(env):
         ref = torch.empty_like(phi)
         bem.bem_eval(m.handle, pts, ref, None)
         assert _rel(phi.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-12
+
+
+def test_noalloc_near_capacity_overflow_then_recovers(env):
+    """More near-field pairs than the fixed array holds (16 384 points hugging
+    the plate, a few hundred near pairs each): BEM_ERR_CAPACITY, with every
+    write kept inside the array; the next call of normal size matches
+    bem_eval again, so the overflow left nothing behind."""
+    torch, bem = env
+    mesh = synth.plate_mesh(seed=1)
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(21)
+    n = bem.NOALLOC_MAX_POINTS
+    hug = np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(0.01, 0.05, n)], axis=1)
+    with bem.Mesh(mesh.types, mesh.verts, mesh.sigma) as m:
+        ref_phi = torch.empty(n, dtype=torch.float64, device=dev)
+        bem.bem_eval(m.handle, torch.from_numpy(hug).to(dev), ref_phi, None)
+        assert m.last_stats()[12] > bem.NOALLOC_MAX_NEAR  # the case really overflows
+        phi = torch.empty(n, dtype=torch.float64, device=dev)
+        E = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        with pytest.raises(bem.BemError) as e:
+            bem.bem_eval_noalloc(m.handle, torch.from_numpy(hug).to(dev), phi, E)
+        assert e.value.code == -3  # BEM_ERR_CAPACITY
+        pts = torch.from_numpy(synth.plate_points(seed=22, n=4000)).to(dev)
+        ref = torch.empty(4000, dtype=torch.float64, device=dev)
+        ref_E = torch.empty((4000, 3), dtype=torch.float64, device=dev)
+        bem.bem_eval(m.handle, pts, ref, ref_E)
+        phi2 = torch.empty(4000, dtype=torch.float64, device=dev)
+        E2 = torch.empty((4000, 3), dtype=torch.float64, device=dev)
+        bem.bem_eval_noalloc(m.handle, pts, phi2, E2)
+        torch.cuda.synchronize()
+    assert _rel(phi2.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-12
+    assert _rel(E2.cpu().numpy(), ref_E.cpu().numpy()).max() <= 1e-12
