@@ -433,11 +433,11 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
         return rc;
     }
     if (opt && (opt->flags & BEM_FLAG_NODE_TABLE) && m->precision == kMixed) {
-        cudaError_t e = dev_malloc((void**)&d.nodes, sizeof(float4) * 2 * kTableSlots * nn);
+        cudaError_t e = dev_malloc((void**)&d.nodes, sizeof(float4) * kNodeRecs * kTableSlots * nn);
         if (e != cudaSuccess) {
             cudaGetLastError();
             set_error("bem_create: cudaMalloc of the node table (%zu bytes) failed: %s",
-                      sizeof(float4) * 2 * kTableSlots * nn, cudaGetErrorString(e));
+                      sizeof(float4) * kNodeRecs * kTableSlots * nn, cudaGetErrorString(e));
             rc = BEM_ERR_OOM;
         } else {
             rc = launch_fill_nodes(m, s);

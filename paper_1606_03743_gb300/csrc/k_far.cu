@@ -41,8 +41,10 @@
 //    and the field sum_i b_i (d - o_i) (b_i = w_i q / r_i^3) is rebuilt per
 //    element from B = sum b_i, sum b_i alpha_i, sum b_i beta_i:
 //      d B - e0 sum b_i alpha_i - e1 sum b_i beta_i.
-//    That is 10 FP32 operations and one rsqrt per node and point instead of
-//    13; two points of a lane go through packed f32x2 instructions together.
+//    With the node's weight also stored premultiplied by alpha_i and beta_i,
+//    every sum takes one FMA: 9 FP32 operations and one rsqrt per node and
+//    point instead of 13; two points of a lane go through packed f32x2
+//    instructions together.
 //    At DR >= 3 the terms of r_i^2 cancel by at most a factor of about 4, so
 //    the split costs about two bits of an FP32 result.  rsqrt and the sums
 //    are FP32: each element's node terms (at most 33) are summed on their
@@ -99,21 +101,25 @@ constexpr int kNodeUnroll = BEM_NODE_UNROLL;
 #define BEM_FLUSH 8
 #endif
 constexpr int kFlush = BEM_FLUSH;
-// mixed path: 1 keeps each point pair's d = P - C in shared memory for the
-// element's field rebuild; 0 forms it again there
-#ifndef BEM_D_SMEM
-#define BEM_D_SMEM 0
-#endif
 // 1: the per-band (masked) passes of straddling elements run one generic node
-// loop instead of loops compiled per rule size (less code)
+// loop (unrolled BEM_MASKED_UNROLL deep) instead of loops compiled per rule
+// size.  The kernel is large enough for its code size to cost instruction-
+// fetch stalls: the smaller kernel is 3.4 % faster on the 150 000-element x
+// 1 000 000-point workload, with bit-identical results.
 #ifndef BEM_MASKED_GENERIC
-#define BEM_MASKED_GENERIC 0
+#define BEM_MASKED_GENERIC 1
 #endif
+#ifndef BEM_MASKED_UNROLL
+#define BEM_MASKED_UNROLL 2
+#endif
+constexpr int kMaskedUnroll = BEM_MASKED_UNROLL;
+
+
 static_assert((kFlush & (kFlush - 1)) == 0 && kFlush <= 32, "flush interval: a power of two up to 32");
 
 constexpr int kSlots = 76;    // rule-table slots per element type (75 used at most)
 constexpr int kWarps = 4;     // warps per CTA
-constexpr int kNodeBuf = 36;  // node records per buffer (33 used at most)
+constexpr int kNodeBuf = 33;  // nodes per buffer (the largest rule)
 constexpr int kAsmGroup = 4;  // mixed assembly: elements per staged group (a 32-byte row segment)
 // assembly work items per resident warp (elements are chunked finely enough for this many)
 #ifndef BEM_ASM_ITEMS
@@ -182,9 +188,11 @@ __device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
 
 // Warp-cooperative append of near pairs; want[q] marks point q of this lane.
+// Point q of a lane is sorted point tile_base + 32 q + lane; its near-pair
+// ordinal counter ncnt[32 q + lane] lives in the warp's shared memory.
 template <int PT>
-__device__ __forceinline__ void append_near(const FarK& p, const bool (&want)[PT], const int (&sidx)[PT], int elem,
-                                            int chunk, int (&ncnt)[PT], int lane) {
+__device__ __forceinline__ void append_near(const FarK& p, const bool (&want)[PT], int tile_base, int elem, int chunk,
+                                            int* ncnt, int lane) {
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
         const unsigned m = __ballot_sync(0xffffffffu, want[q]);
@@ -193,10 +201,11 @@ __device__ __forceinline__ void append_near(const FarK& p, const bool (&want)[PT
         unsigned long long base = 0;
         if (lane == leader) base = atomicAdd(p.counters, (unsigned long long)__popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (want[q]) {
+        if (want[q]) {  // only live points want pairs
             const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-            if (idx < p.near_cap) p.near_rec[idx] = make_int4(sidx[q], elem, ncnt[q], chunk);
-            ++ncnt[q];
+            const int o = ncnt[q * 32 + lane];
+            if (idx < p.near_cap) p.near_rec[idx] = make_int4(tile_base + q * 32 + lane, elem, o, chunk);
+            ncnt[q * 32 + lane] = o + 1;
         }
     }
 }
@@ -310,7 +319,8 @@ __device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
 }
 
 // One node of an element at the NP point pairs of a lane, in the frame form:
-// ab = (-alpha, -alpha, -beta, -beta), ow = (|o|^2, |o|^2, w q, w q);
+// ab = (-alpha, -alpha, -beta, -beta), ow = (|o|^2, |o|^2, w q, w q),
+// wab = (-w q alpha, -w q alpha, -w q beta, -w q beta) (read with BEM_NODE3);
 // s, u, v = |d|^2, 2 d.e0, 2 d.e1 per point (r^2 = s + |o|^2 - alpha u -
 // beta v).  acc[k] = (sum a, sum b, -sum b alpha, -sum b beta) with
 // a = w q / r, b = a / r^2 (phi only: sum a).  A point that must not take
@@ -324,7 +334,7 @@ __device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
 // from which the rebuild forms sum q (I / r^3 - 3 r r^T / r^5) with
 // r = d - alpha e0 - beta e1.
 template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
-__device__ __forceinline__ void node2(const float4 ab, const float4 ow, const float2 (&s)[NP],
+__device__ __forceinline__ void node2(const float4 ab, const float4 ow, const float4 wab, const float2 (&s)[NP],
                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
     const float2 al = make_float2(ab.x, ab.y), be = make_float2(ab.z, ab.w);
     const float2 oo = make_float2(ow.x, ow.y), w = make_float2(ow.z, ow.w);
@@ -352,6 +362,23 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
             }
             continue;
         }
+        if constexpr (BEM_NODE3) {
+            // third record: (-w alpha, -w beta): every sum is one FMA of its weight and 1/r or 1/r^3
+            if (INIT) acc[k][0] = mul2(w, inv);
+            else acc[k][0] = fma2(w, inv, acc[k][0]);
+            if (WANT_E) {
+                const float2 i3 = mul2(inv, mul2(inv, inv));  // 1 / r_i^3
+                const float2 wa = make_float2(wab.x, wab.y), wb = make_float2(wab.z, wab.w);
+                if (INIT) {
+                    acc[k][1] = mul2(w, i3); acc[k][2] = mul2(wa, i3); acc[k][3] = mul2(wb, i3);
+                } else {
+                    acc[k][1] = fma2(w, i3, acc[k][1]);
+                    acc[k][2] = fma2(wa, i3, acc[k][2]);
+                    acc[k][3] = fma2(wb, i3, acc[k][3]);
+                }
+            }
+            continue;
+        }
         const float2 a = mul2(w, inv);  // q_i / r_i
         if (INIT) {
             acc[k][0] = a;
@@ -376,15 +403,17 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
 template <int N, int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
 __device__ __forceinline__ void nodes2_n(const float4* __restrict__ nd, const float2 (&s)[NP],
                                          const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
-    if (INIT) node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], s, u, v, acc);
+    if (INIT) node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], nd[kNodeRecs - 1], s, u, v, acc);
     if constexpr (N <= BEM_FULL_UNROLL_MAX) {
 #pragma unroll
         for (int i = INIT ? 1 : 0; i < N; ++i)
-            node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+            node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
+                                            u, v, acc);
     } else {
 #pragma unroll kNodeUnroll
         for (int i = INIT ? 1 : 0; i < N; ++i)
-            node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+            node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
+                                            u, v, acc);
     }
 }
 
@@ -394,10 +423,12 @@ template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
 __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
                                        const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
     if constexpr (!INIT && BEM_MASKED_GENERIC) {
-#pragma unroll 2
-        for (int i = 0; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+#pragma unroll kMaskedUnroll
+        for (int i = 0; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
+                                            u, v, acc);
         return;
     }
+
     switch (n) {
         case 4: nodes2_n<4, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
         case 7: nodes2_n<7, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
@@ -409,11 +440,12 @@ __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, con
     }
     int i = 0;
     if (INIT) {  // every rule has at least four nodes
-        node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], s, u, v, acc);
+        node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], nd[kNodeRecs - 1], s, u, v, acc);
         i = 1;
     }
 #pragma unroll 1
-    for (; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[2 * i], nd[2 * i + 1], s, u, v, acc);
+    for (; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
+                                            u, v, acc);
 }
 
 // Shared memory of one warp.
@@ -425,8 +457,9 @@ struct WarpSmem {
     double at[ATILE ? kAsmGroup * PT * 32 : 1];
     int rows[ATILE ? PT * 32 : 1];
     R4 c[kMixed ? 1 : 32];   // FP64: centroid, w = type
-    R4 e0[32];               // frame e0, w = q (element charge)
-    R4 e1[32];               // frame e1; mixed: w = type (int bits)
+    R4 e0[kMixed ? 1 : 32];  // FP64: frame e0, w = q (element charge)
+    R4 e1[kMixed ? 1 : 32];  // FP64: frame e1
+    float2 qt[kMixed ? 32 : 1];  // mixed: element charge q, type (int bits); the frame is in pr
     R thr[32 * 5];           // squared band limits (tau L)^2
     R sl[2 * 32];            // linear densities: area x (d sigma / d alpha, d sigma / d beta), else 0
     // mixed: per element, the values each node pass and the field rebuild
@@ -434,13 +467,12 @@ struct WarpSmem {
     // -C_hi, -C_lo, e0, e1 (six float4)
     float4 pr[kMixed ? 32 * 6 : 1];
 
-    R4 nd[2][kMixed ? 2 * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: two)
+    R4 nd[2][kMixed ? kNodeRecs * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: kNodeRecs)
     // mixed evaluation (NACC = 4: phi, E) and gradient (NACC = 6): per point pair,
     // component and lane, the running sum as an unevaluated FP32 pair hi + lo
     // (hi.x, hi.y, lo.x, lo.y)
     float4 accdf[NACC ? (PT / 2) * NACC * 32 : 1];
-    // mixed evaluation / gradient with BEM_D_SMEM: d of each point pair of a lane
-    float2 dd[(NACC && BEM_D_SMEM) ? (PT / 2) * 3 * 32 : 1];
+    int ncnt[PT * 32];  // near pairs found so far per point of the tile (their ordinals)
 };
 
 template <typename R>
@@ -548,14 +580,15 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         // ---- field points of this lane
         R px[PT], py[PT], pz[PT];      // FP64: the point; mixed: hi part
         float lx[PT], ly[PT], lz[PT];  // mixed: lo part
-        int sidx[PT];
-        bool valid[PT];
+        // point q of this lane: sorted point base + 32 q + lane; a slot past the end takes a
+        // live point of the tile (its results are not stored).  Formed when needed rather
+        // than held in registers through the element loop.
+        auto valid = [&](int q) { return base + q * 32 + lane < n_pts; };
+        auto sidx = [&](int q) { return valid(q) ? base + q * 32 + lane : base; };
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
-            int i = base + q * 32 + lane;
-            valid[q] = i < n_pts;
-            if (!valid[q]) i = base;  // duplicate a live point of the tile
-            sidx[q] = i;
+            const int i = sidx(q);
+            ws.ncnt[q * 32 + lane] = 0;
             const int src = p.perm[i];
             const double X = p.pts[3 * (size_t)src], Y = p.pts[3 * (size_t)src + 1], Z = p.pts[3 * (size_t)src + 2];
             if constexpr (F64) {
@@ -614,10 +647,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         R accg[MODE == 2 ? PT : 1][6];  // gradient pass: the running sums
         constexpr int NA = GRAD3 ? 6 : 4;
         float2 acc8[NP][NA];  // mixed: FP32 sum of up to 8 element results (point pairs)
-        int ncnt[PT];
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
-            ncnt[q] = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if constexpr (F64) acc[q][c] = (R)0;
@@ -638,7 +669,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         const int el0 = chunk * p.chunk_len, el1 = min(p.n_el, el0 + p.chunk_len);
         if constexpr (ATILE) {
 #pragma unroll
-            for (int q = 0; q < PT; ++q) ws.rows[q * 32 + lane] = valid[q] ? p.perm[sidx[q]] : -1;
+            for (int q = 0; q < PT; ++q) ws.rows[q * 32 + lane] = valid(q) ? p.perm[sidx(q)] : -1;
             __syncwarp();
         }
         int par = 0;    // node buffer parity
@@ -676,8 +707,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         c = p.chi[j];
                         cl = p.clo[j];
                         const float4 a = p.e0f[j], b = p.e1f[j];
-                        ws.e0[lane] = R4{a.x, a.y, a.z, (float)(sg * area)};
-                        ws.e1[lane] = R4{b.x, b.y, b.z, __int_as_float(ty)};
+                        ws.qt[lane] = make_float2((float)(sg * area), __int_as_float(ty));
                         float4* pr = ws.pr + lane * 6;
                         pr[0] = make_float4(-c.x, -c.x, -c.y, -c.y);
                         pr[1] = make_float4(-c.z, -c.z, -cl.x, -cl.x);
@@ -710,7 +740,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 const int cd = __shfl_sync(0xffffffffu, code, e);
                 int ty;
                 if constexpr (F64) ty = (int)ws.c[e].w;
-                else ty = __float_as_int(ws.e1[e].w);
+                else ty = __float_as_int(ws.qt[e].y);
 
                 if constexpr (F64) {
                     // ---------------- FP64 path: P - Q_i = (P - C) - o_i
@@ -771,14 +801,14 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int q = 0; q < PT; ++q) {
                             const R d2 = dx[q] * dx[q] + dy[q] * dy[q] + dz[q] * dz[q];
                             bq[q] = band_of<R>(d2, th);
-                            if (valid[q]) mask |= 1u << bq[q];
+                            if (valid(q)) mask |= 1u << bq[q];
                         }
                         mask = __reduce_or_sync(0xffffffffu, mask);
                         if (mask & 1u) {
                             bool want[PT];
 #pragma unroll
-                            for (int q = 0; q < PT; ++q) want[q] = valid[q] && bq[q] == 0;
-                            append_near<PT>(p, want, sidx, b0 + e, chunk, ncnt, lane);
+                            for (int q = 0; q < PT; ++q) want[q] = valid(q) && bq[q] == 0;
+                            append_near<PT>(p, want, base, b0 + e, chunk, ws.ncnt, lane);
                         }
                         if (kElemSum) {  // near-only points get zero far sums
 #pragma unroll
@@ -810,7 +840,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
                             for (int q = 0; q < PT; ++q) {
                                 for (int band = 0; band <= 5; ++band) {
-                                    const unsigned m = __ballot_sync(0xffffffffu, valid[q] && bq[q] == band);
+                                    const unsigned m = __ballot_sync(0xffffffffu, valid(q) && bq[q] == band);
                                     if (lane == 0 && m) atomicAdd(&rs.stat[6 * ty + band], (unsigned long long)__popc(m));
                                 }
                             }
@@ -820,7 +850,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         // assembly: one potential per pair, times 1/(4 pi eps0); near pairs are filled later
 #pragma unroll
                         for (int q = 0; q < PT; ++q)
-                            if (valid[q]) p.A[(size_t)p.perm[sidx[q]] * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
+                            if (valid(q)) p.A[(size_t)p.perm[sidx(q)] * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
                     }
                 } else {
                     // ---------------- mixed path (frame form, point pairs)
@@ -842,11 +872,6 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
                             diff(k, dx, dy, dz);
-                            if constexpr (BEM_D_SMEM && NACC > 0 && (WANT_E || GRAD3)) {
-                                ws.dd[(3 * k) * 32 + lane] = dx;
-                                ws.dd[(3 * k + 1) * 32 + lane] = dy;
-                                ws.dd[(3 * k + 2) * 32 + lane] = dz;
-                            }
                             sv[k] = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
                             const float2 u = fma2(dx, lo2(r3), fma2(dy, hi2(r3), mul2(dz, lo2(r4))));
                             const float2 v = fma2(dx, hi2(r4), fma2(dy, lo2(r5), mul2(dz, hi2(r5))));
@@ -858,7 +883,10 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     // expand rule r of element e into the free node buffer (lane i: node i)
                     auto expand = [&](int r) -> int {
                         const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
-                        const float4 f0 = ws.e0[e], f1 = ws.e1[e];
+                        // the frame from the duplicated records: (e0x, e0x, e0y, e0y), (e0z, e0z, e1x, e1x),
+                        // (e1y, e1y, e1z, e1z); the charge from qt
+                        const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
+                        const float4 f0 = make_float4(r3.x, r3.z, r4.x, ws.qt[e].x), f1 = make_float4(r4.z, r5.x, r5.z, 0.0f);
                         float ca = 0.0f, cb = 0.0f, cc = 0.0f;
                         if (VARY && p.curv) {  // quadratic densities: area x second-order coefficients
                             const size_t j = (size_t)(b0 + e);
@@ -879,8 +907,12 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                                 if (p.curv) qi = fmaf(al, fmaf(al, ca, be * cb), fmaf(be * be, cc, qi));
                             }
                             const float am = -al, bm = -be, wq = rs.w[st + i] * qi;
-                            ws.nd[par][2 * i] = make_float4(am, am, bm, bm);
-                            ws.nd[par][2 * i + 1] = make_float4(oo, oo, wq, wq);
+                            ws.nd[par][kNodeRecs * i] = make_float4(am, am, bm, bm);
+                            ws.nd[par][kNodeRecs * i + 1] = make_float4(oo, oo, wq, wq);
+                            if constexpr (BEM_NODE3) {
+                                const float wa = wq * am, wb = wq * bm;
+                                ws.nd[par][kNodeRecs * i + 2] = make_float4(wa, wa, wb, wb);
+                            }
                         }
                         __syncwarp();
                         return n;
@@ -889,10 +921,11 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     // asynchronously (lane i: node i); the caller waits and syncs
                     auto fetch = [&](int el, int t, int r, int buf) -> int {
                         const int n = rs.n[t * 5 + r];
-                        const float4* src = p.nodes + ((size_t)el * kTableSlots + rs.start[t * 5 + r]) * 2;
+                        const float4* src = p.nodes + ((size_t)el * kTableSlots + rs.start[t * 5 + r]) * kNodeRecs;
                         for (int i = lane; i < n; i += 32) {
-                            cp_async16(&ws.nd[buf][2 * i], src + 2 * i);
-                            cp_async16(&ws.nd[buf][2 * i + 1], src + 2 * i + 1);
+#pragma unroll
+                            for (int k = 0; k < kNodeRecs; ++k)
+                                cp_async16(&ws.nd[buf][kNodeRecs * i + k], src + kNodeRecs * i + k);
                         }
                         cp_async_commit();
                         return n;
@@ -911,7 +944,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             if (e + 1 < nb) {
                                 const int cdn = __shfl_sync(0xffffffffu, code, e + 1);
                                 if (cdn >= 1 && cdn <= 5)
-                                    pre_n = fetch(b0 + e + 1, __float_as_int(ws.e1[e + 1].w), band_rule(cdn), par ^ 1);
+                                    pre_n = fetch(b0 + e + 1, __float_as_int(ws.qt[e + 1].y), band_rule(cdn), par ^ 1);
                             }
                         } else {
                             n = expand(band_rule(cd));
@@ -943,13 +976,13 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         }
 #pragma unroll
                         for (int q = 0; q < PT; ++q)
-                            if (valid[q]) mask |= 1u << bq[q];
+                            if (valid(q)) mask |= 1u << bq[q];
                         mask = __reduce_or_sync(0xffffffffu, mask);
                         if (mask & 1u) {
                             bool want[PT];
 #pragma unroll
-                            for (int q = 0; q < PT; ++q) want[q] = valid[q] && bq[q] == 0;
-                            append_near<PT>(p, want, sidx, b0 + e, chunk, ncnt, lane);
+                            for (int q = 0; q < PT; ++q) want[q] = valid(q) && bq[q] == 0;
+                            append_near<PT>(p, want, base, b0 + e, chunk, ws.ncnt, lane);
                         }
 #pragma unroll
                         for (int k = 0; k < NP; ++k)
@@ -982,7 +1015,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
                             for (int q = 0; q < PT; ++q) {
                                 for (int band = 0; band <= 5; ++band) {
-                                    const unsigned m = __ballot_sync(0xffffffffu, valid[q] && bq[q] == band);
+                                    const unsigned m = __ballot_sync(0xffffffffu, valid(q) && bq[q] == band);
                                     if (lane == 0 && m) atomicAdd(&rs.stat[6 * ty + band], (unsigned long long)__popc(m));
                                 }
                             }
@@ -990,7 +1023,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     }
 
                     if constexpr (PRE) {  // the table's weights carry no charge: scale the element's sums
-                        const float q = ws.e0[e].w;
+                        const float q = ws.qt[e].x;
                         const float2 q2 = make_float2(q, q);
 #pragma unroll
                         for (int k = 0; k < NP; ++k)
@@ -1007,14 +1040,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int k = 0; k < NP; ++k) {
                             acc8[k][0] = add2(acc8[k][0], eacc[k][0]);
                             if (WANT_E) {
-                                float2 dx, dy, dz;  // not held in registers through the node loop
-                                if constexpr (BEM_D_SMEM) {
-                                    dx = ws.dd[(3 * k) * 32 + lane];
-                                    dy = ws.dd[(3 * k + 1) * 32 + lane];
-                                    dz = ws.dd[(3 * k + 2) * 32 + lane];
-                                } else {
-                                    diff(k, dx, dy, dz);
-                                }
+                                float2 dx, dy, dz;  // formed again rather than held through the node loop
+                                diff(k, dx, dy, dz);
                                 acc8[k][1] = fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], fma2(h1x, eacc[k][3], acc8[k][1])));
                                 acc8[k][2] = fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], fma2(h1y, eacc[k][3], acc8[k][2])));
                                 acc8[k][3] = fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], fma2(h1z, eacc[k][3], acc8[k][3])));
@@ -1046,13 +1073,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
-                            if constexpr (BEM_D_SMEM) {
-                                dx = ws.dd[(3 * k) * 32 + lane];
-                                dy = ws.dd[(3 * k + 1) * 32 + lane];
-                                dz = ws.dd[(3 * k + 2) * 32 + lane];
-                            } else {
-                                diff(k, dx, dy, dz);
-                            }
+                            diff(k, dx, dy, dz);
                             const float2* c = eacc[k];
                             const float2 mx = fma2(c[1], dx, fma2(c[2], h0x, mul2(c[3], h1x)));
                             const float2 my = fma2(c[1], dy, fma2(c[2], h0y, mul2(c[3], h1y)));
@@ -1123,7 +1144,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         if constexpr (MODE == 0) {
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
-                if (!valid[q]) continue;
+                if (!valid(q)) continue;
                 double4 o;
                 if constexpr (F64) {
                     o = make_double4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
@@ -1136,15 +1157,15 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     }
                     o = make_double4(c4[0], c4[1], c4[2], c4[3]);
                 }
-                const size_t slot = (size_t)sidx[q] * p.n_chunks + chunk;
+                const size_t slot = (size_t)sidx(q) * p.n_chunks + chunk;
                 p.part[slot] = o;
-                p.near_cnt[slot] = ncnt[q];
+                p.near_cnt[slot] = ws.ncnt[q * 32 + lane];
             }
         }
         if constexpr (MODE == 2 || MODE == 3) {
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
-                if (!valid[q]) continue;
+                if (!valid(q)) continue;
                 double g6[6];
 #pragma unroll
                 for (int j = 0; j < 6; ++j) {
@@ -1155,10 +1176,10 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         g6[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
                     }
                 }
-                const size_t slot = (size_t)sidx[q] * p.n_chunks + chunk;
+                const size_t slot = (size_t)sidx(q) * p.n_chunks + chunk;
                 p.part_g[2 * slot] = make_double4(g6[0], g6[1], g6[2], g6[3]);
                 p.part_g[2 * slot + 1] = make_double4(g6[4], g6[5], 0.0, 0.0);
-                p.near_cnt[slot] = ncnt[q];
+                p.near_cnt[slot] = ws.ncnt[q * 32 + lane];
             }
         }
     }
@@ -1283,8 +1304,9 @@ __global__ void k_fill_nodes(int n, const float4* __restrict__ e0f, const float4
     const float4 f0 = e0f[j], f1 = e1f[j];
     const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y), oz = fmaf(al, f0.z, be * f1.z);
     const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
-    out[2 * id] = make_float4(-al, -al, -be, -be);
-    out[2 * id + 1] = make_float4(oo, oo, w, w);
+    out[kNodeRecs * id] = make_float4(-al, -al, -be, -be);
+    out[kNodeRecs * id + 1] = make_float4(oo, oo, w, w);
+    if constexpr (BEM_NODE3) out[kNodeRecs * id + 2] = make_float4(-w * al, -w * al, -w * be, -w * be);
 }
 }  // namespace
 
