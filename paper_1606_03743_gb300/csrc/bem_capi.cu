@@ -138,8 +138,13 @@ void free_points(bem_mesh* m) {
     dfree(m, &w.key, c);
     dfree(m, &w.part, cs);
     dfree(m, &w.near_cnt, cs);
-    dfree(m, &w.near_off, cs);
-    dfree(m, &w.scan_tmp, scan_tmp_ints((int)std::max(cs, kCells)));
+    dfree(m, &w.far, c);
+    dfree(m, &w.near_tot, c);
+    dfree(m, &w.near_row, c);
+    dfree(m, &w.near_rows, cs);
+    dfree(m, &w.near_off, c);
+    dfree(m, &w.tile_done, tile_done_ints(c));
+    dfree(m, &w.scan_tmp, scan_tmp_ints((int)std::max(c, kCells)));
     w.cap_pts = 0;
 }
 
@@ -164,7 +169,10 @@ int ensure_points(bem_mesh* m, size_t n) {
     int rc;
     if ((rc = dalloc(m, &w.pts, 3 * c)) || (rc = dalloc(m, &w.out, 4 * c)) || (rc = dalloc(m, &w.perm, c)) ||
         (rc = dalloc(m, &w.key, c)) || (rc = dalloc(m, &w.part, cs)) || (rc = dalloc(m, &w.near_cnt, cs)) ||
-        (rc = dalloc(m, &w.near_off, cs)) || (rc = dalloc(m, &w.scan_tmp, scan_tmp_ints((int)std::max(cs, kCells))))) {
+        (rc = dalloc(m, &w.far, c)) || (rc = dalloc(m, &w.near_tot, c)) || (rc = dalloc(m, &w.near_row, c)) ||
+        (rc = dalloc(m, &w.near_rows, cs)) || (rc = dalloc(m, &w.near_off, c)) ||
+        (rc = dalloc(m, &w.tile_done, tile_done_ints(c))) ||
+        (rc = dalloc(m, &w.scan_tmp, scan_tmp_ints((int)std::max(c, kCells))))) {
         w.cap_pts = c;
         free_points(m);
         return rc;
@@ -260,8 +268,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         a.n_pts = n;
         a.sigma = dsigma;
         a.slope = eval_slope(m, dsigma);
-        a.part = w.part;
-        a.near_cnt = w.near_cnt;
+        far_args_from_work(a, w);
         a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;
@@ -279,7 +286,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[2], s));
         {
             NvtxRange r("bem.near");
-            if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, n * m->n_chunks, w.scan_tmp, s))) return rc;
+            if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, n, w.scan_tmp, s))) return rc;
             if ((rc = launch_near_eval(m, dpts, w.perm, n, dsigma, 0, s, eval_slope(m, dsigma)))) return rc;
         }
         if (m->timing) BEM_CUDA_TRY(cudaEventRecord(m->ev[3], s));
@@ -740,16 +747,17 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
     if ((rc = stage_in(points, sizeof(double) * 3 * n, w.pts, (const void**)&dpts, s, m->device))) return rc;
     if ((rc = launch_sort_points(m, dpts, (int)n, s))) return rc;
     if ((rc = check_points(m, "bem_eval_grad", s))) return rc;
-    const size_t np = (size_t)n * (size_t)m->n_chunks;
+    // tile-major partial slots for whole tiles (of at most 128 points) of every chunk
+    const size_t np = ((size_t)n + 127) / 128 * 128 * (size_t)m->n_chunks;
     const bool g_dev = is_device_ptr(G, m->device);
-    const size_t need = sizeof(double4) * 2 * np + (g_dev ? 0 : sizeof(double) * 6 * (size_t)n);
+    const size_t need = sizeof(double4) * 2 * (np + (size_t)n) + (g_dev ? 0 : sizeof(double) * 6 * (size_t)n);
     if (m->w.bytes + need > m->budget) {
         set_error("bem_eval_grad: needs %zu bytes beyond the %zu in use (budget %zu)", need, m->w.bytes, m->budget);
         return BEM_ERR_OOM;
     }
-    Scratch<double4> part_g;
+    Scratch<double4> part_g, far_g;
     Scratch<double> gout;
-    if ((rc = part_g.alloc(2 * np))) return rc;
+    if ((rc = part_g.alloc(2 * np)) || (rc = far_g.alloc(2 * (size_t)n))) return rc;
     if (!g_dev && (rc = gout.alloc(6 * (size_t)n))) return rc;
     double* dG = g_dev ? G : gout.p;
     for (int attempt = 0; attempt < 3; ++attempt) {
@@ -760,9 +768,9 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         a.n_pts = (int)n;
         a.sigma = m->d.sigma;
         a.slope = eval_slope(m, m->d.sigma);
-        a.part = w.part;
+        far_args_from_work(a, w);
         a.part_g = part_g.p;
-        a.near_cnt = w.near_cnt;
+        a.far_g = far_g.p;
         a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;
@@ -771,7 +779,7 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         a.want_e = 1;
         a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
         if ((rc = launch_far(m, a, s))) return rc;
-        if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)np, w.scan_tmp, s))) return rc;
+        if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, (int)n, w.scan_tmp, s))) return rc;
         unsigned long long n_near = 0;
         BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters, sizeof n_near, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -783,7 +791,7 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         if ((rc = gval.alloc(2 * (size_t)n_near))) return rc;
         if ((rc = launch_near_grad(m, dpts, w.perm, m->d.sigma, gval.p, n_near, s, eval_slope(m, m->d.sigma))))
             return rc;
-        if ((rc = launch_finalize_grad(m, w.perm, (int)n, part_g.p, gval.p, n_near, dG, s))) return rc;
+        if ((rc = launch_finalize_grad(m, w.perm, (int)n, far_g.p, gval.p, n_near, dG, s))) return rc;
         if (!g_dev) BEM_CUDA_TRY(cudaMemcpyAsync(G, dG, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
         m->last_stats[12] = (int64_t)n_near;
@@ -891,7 +899,6 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
         a.perm = w.perm;
         a.n_pts = (int)mrows;
         a.sigma = nullptr;  // assembly: unit charge density
-        a.near_cnt = w.near_cnt;
         a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;

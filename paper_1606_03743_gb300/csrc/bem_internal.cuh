@@ -82,9 +82,18 @@ struct Work {
     unsigned* key = nullptr;      // spatial cell key per point
     int* cell_cnt = nullptr;      // histogram of cells
     int* cell_off = nullptr;      // exclusive scan of cell_cnt
-    double4* part = nullptr;      // far-field sums per (sorted point, element chunk)
-    int* near_cnt = nullptr;      // near pairs per (sorted point, element chunk)
-    int* near_off = nullptr;      // exclusive scan of near_cnt
+    // Far-field sums and near-pair counts of one work item (a tile of points x
+    // an element chunk), laid out tile by tile: [tile][chunk][point of the tile].
+    // They are transient: the tile's last item sums them into far / near_tot
+    // and drops them from L2 without a write-back.
+    double4* part = nullptr;
+    int* near_cnt = nullptr;
+    double4* far = nullptr;       // far-field sums per sorted point (the chunks summed in chunk order)
+    int* near_tot = nullptr;      // near pairs per sorted point
+    int* near_row = nullptr;      // per sorted point with near pairs: its row of near_rows
+    int* near_rows = nullptr;     // [row][chunk]: near pairs of the point in the chunks before
+    int* near_off = nullptr;      // exclusive scan of near_tot: first near value of each point
+    int* tile_done = nullptr;     // work items finished per tile, then the near_rows row counter
     int* scan_tmp = nullptr;      // block sums of the scans
     size_t cap_near = 0;
     int4* near_rec = nullptr;     // (sorted point, element, ordinal, chunk)
@@ -187,9 +196,15 @@ struct FarArgs {
     int n_pts;
     const double* sigma; // per element charge density (eval) or the x of a matvec
     const double* slope; // linear densities: [n][2] slopes, or nullptr (constant densities)
-    double4* part;       // out: far sums per (sorted point, chunk)
-    double4* part_g;     // gradient pass (FP64 kernel): 6 far sums per (sorted point, chunk), two double4
-    int* near_cnt;       // out: near pairs per (sorted point, chunk)
+    double4* part;       // transient: far sums per (tile, chunk, point of the tile)
+    double4* part_g;     // gradient pass: the same, 6 sums as two double4
+    int* near_cnt;       // transient: near pairs per (tile, chunk, point of the tile)
+    double4* far;        // out: far sums per sorted point (gradient pass: two double4, far_g)
+    double4* far_g;
+    int* near_tot;       // out: near pairs per sorted point
+    int* near_row;       // out: row of near_rows per sorted point with near pairs
+    int* near_rows;      // out: per row, the point's near pairs in the chunks before each chunk
+    int* tile_done;      // finished items per tile (zeroed by launch_far), then the row counter
     int* work;           // work-item counter, zero at launch
     int4* near_rec;      // out: near pair list
     unsigned long long* counters;
@@ -201,7 +216,19 @@ struct FarArgs {
     int stats;           // count pairs per band into counters[2..13]
     const int* n_dev;    // if set: the point count is read on the device (n_pts is the capacity)
 };
-// Far-field cubature + near-pair compaction (k_far.cu).
+// The per-call buffers of the far pass (everything but part_g / far_g) from a workspace.
+inline void far_args_from_work(FarArgs& a, Work& w) {
+    a.part = w.part;
+    a.near_cnt = w.near_cnt;
+    a.far = w.far;
+    a.near_tot = w.near_tot;
+    a.near_row = w.near_row;
+    a.near_rows = w.near_rows;
+    a.tile_done = w.tile_done;
+}
+// Ints of Work::tile_done for cap points: one per tile of at least 32 points, plus the row counter.
+constexpr size_t tile_done_ints(size_t cap) { return cap / 32 + 2; }
+// Far-field cubature + near-pair compaction (k_far.cu).  Zeroes a.tile_done itself.
 int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s);
 // Analytic near field over the compacted list and the per-point finalisation (k_near.cu).
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
@@ -221,7 +248,7 @@ int launch_fill_nodes(bem_mesh* m, cudaStream_t s);
 // field gradient over the compacted near list and its per-point finalisation (k_near.cu)
 int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
                      unsigned long long gcap, cudaStream_t s, const double* slope = nullptr);
-int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* part_g, const double4* gval,
+int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* far_g, const double4* gval,
                          unsigned long long gcap, double* G, cudaStream_t s);
 // kc x potential of each element at its own centroid (sigma = 1): the diagonal of the
 // collocation matrix at the centroids (k_near.cu)

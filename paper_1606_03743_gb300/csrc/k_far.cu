@@ -143,9 +143,15 @@ struct FarK {
     const double* sigma;  // nullptr: unit density (assembly)
     const double* slope;  // linear densities: [n_el][2] slopes in the element frame, or nullptr
     const double* curv;   // quadratic densities: [n_el][3] alpha^2, alpha beta, beta^2 coefficients, or nullptr
-    double4* part;        // per (point, chunk) far sums, [n_pts][n_chunks]
-    double4* part_g;      // gradient pass: per (point, chunk) 6 sums as two double4
-    int* near_cnt;        // per (point, chunk) near pairs, [n_pts][n_chunks]
+    double4* part;        // per (tile, chunk, point of the tile) far sums (transient)
+    double4* part_g;      // gradient pass: the same, 6 sums as two double4
+    int* near_cnt;        // per (tile, chunk, point of the tile) near pairs (transient)
+    double4* far;         // per sorted point: far sums over all chunks (gradient: far_g, two double4)
+    double4* far_g;
+    int* near_tot;        // per sorted point: near pairs over all chunks
+    int* near_row;        // per sorted point with near pairs: its row of near_rows
+    int* near_rows;       // [row][chunk]: near pairs of the point in the chunks before
+    int* tile_done;       // [tile] finished work items; [n_tiles] the near_rows row counter
     int4* near_rec;
     unsigned long long* counters;
     unsigned long long near_cap;
@@ -488,6 +494,81 @@ constexpr size_t far_smem_bytes() {
     using R4 = typename std::conditional<F64, double4, float4>::type;
     constexpr int NACC = F64 ? 0 : MODE == 0 ? 4 : MODE == 3 ? 6 : 0;
     return ((sizeof(RuleSmem<R>) + 15) / 16) * 16 + kWarps * sizeof(WarpSmem<R, R4, PT, NACC, !F64 && MODE == 1>);
+}
+
+// A double4 read at L2 (past L1, which may hold stale lines of other SMs' writes).
+__device__ __forceinline__ double4 ldcg4(const double4* a) {
+    const double2 lo = __ldcg(reinterpret_cast<const double2*>(a));
+    const double2 hi = __ldcg(reinterpret_cast<const double2*>(a) + 1);
+    return make_double4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Drop a 128-byte line from L2 without writing it back (its data is used up).
+__device__ __forceinline__ void discard_l2(const void* line) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
+}
+
+// End of a work item that wrote its partial sums (NPART double4 per point) and
+// near-pair counts into the item's slots of the tile-major areas.  The tile's
+// last item to finish -- told by a per-tile counter -- sums every chunk's
+// partials in chunk order (the same additions, in the same order, whatever
+// batch the points came in: the results stay batch-independent), counts the
+// near pairs per point with their per-chunk prefix, and then discards the
+// tile's slots from L2: they are never read again, so they need no write-back
+// to HBM.  The usual split-phase pattern: stores, a device fence, the counter;
+// the last item fences again and reads past L1.
+template <int NPART, int PT>
+__device__ __forceinline__ void finish_tile(const FarK& p, const double4* part, double4* far, int tile, int base,
+                                            int n_pts, int n_tiles, int lane) {
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(p.tile_done + tile, 1) == p.n_chunks - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    const int nc = p.n_chunks, tp = p.tile_pts;
+    const size_t tbase = (size_t)tile * nc * tp;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const int sp = base + q * 32 + lane;
+        if (sp >= n_pts) continue;
+        double s[4 * NPART];
+#pragma unroll
+        for (int k = 0; k < 4 * NPART; ++k) s[k] = 0.0;
+        int tot = 0;
+        for (int c = 0; c < nc; ++c) {
+            const size_t slot = tbase + (size_t)c * tp + q * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < NPART; ++j) {
+                const double4 v = ldcg4(part + NPART * slot + j);
+                if (NPART == 1 && c == 0) {  // the evaluation's sum starts from the first chunk
+                    s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+                } else {
+                    s[4 * j] += v.x; s[4 * j + 1] += v.y; s[4 * j + 2] += v.z; s[4 * j + 3] += v.w;
+                }
+            }
+            tot += __ldcg(p.near_cnt + slot);
+        }
+#pragma unroll
+        for (int j = 0; j < NPART; ++j) far[NPART * (size_t)sp + j] = make_double4(s[4 * j], s[4 * j + 1], s[4 * j + 2], s[4 * j + 3]);
+        p.near_tot[sp] = tot;
+        if (tot > 0) {
+            const int r = atomicAdd(p.tile_done + n_tiles, 1);
+            p.near_row[sp] = r;
+            int run = 0;
+            for (int c = 0; c < nc; ++c) {
+                p.near_rows[(size_t)r * nc + c] = run;
+                run += __ldcg(p.near_cnt + tbase + (size_t)c * tp + q * 32 + lane);
+            }
+        }
+    }
+    const char* pa = reinterpret_cast<const char*>(part + NPART * tbase);
+    const size_t pbytes = sizeof(double4) * NPART * (size_t)nc * tp;
+    for (size_t off = (size_t)lane * 128; off < pbytes; off += 32 * 128) discard_l2(pa + off);
+    const char* pc = reinterpret_cast<const char*>(p.near_cnt + tbase);
+    const size_t cbytes = sizeof(int) * (size_t)nc * tp;
+    for (size_t off = (size_t)lane * 128; off < cbytes; off += 32 * 128) discard_l2(pc + off);
 }
 
 // ------------------------------------------------------------ the kernel
@@ -1141,46 +1222,47 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             }
         }
 
-        if constexpr (MODE == 0) {
+        // ---- this item's partial sums and near-pair counts, then the tile's reduction
+        constexpr int NPART = MODE == 0 ? 1 : (MODE == 2 || MODE == 3) ? 2 : 0;
+        if constexpr (NPART > 0) {
+            double4* part = NPART == 1 ? p.part : p.part_g;
+            const size_t ibase = ((size_t)tile * p.n_chunks + chunk) * p.tile_pts;
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
                 if (!valid(q)) continue;
-                double4 o;
-                if constexpr (F64) {
-                    o = make_double4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
-                } else {
-                    double c4[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float4 v = ws.accdf[((q >> 1) * 4 + j) * 32 + lane];
-                        c4[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
-                    }
-                    o = make_double4(c4[0], c4[1], c4[2], c4[3]);
-                }
-                const size_t slot = (size_t)sidx(q) * p.n_chunks + chunk;
-                p.part[slot] = o;
-                p.near_cnt[slot] = ws.ncnt[q * 32 + lane];
-            }
-        }
-        if constexpr (MODE == 2 || MODE == 3) {
-#pragma unroll
-            for (int q = 0; q < PT; ++q) {
-                if (!valid(q)) continue;
-                double g6[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    if constexpr (MODE == 2) {
-                        g6[j] = accg[q][j];
+                const size_t slot = ibase + q * 32 + lane;
+                if constexpr (MODE == 0) {
+                    double4 o;
+                    if constexpr (F64) {
+                        o = make_double4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
                     } else {
-                        const float4 v = ws.accdf[((q >> 1) * 6 + j) * 32 + lane];
-                        g6[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+                        double c4[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 v = ws.accdf[((q >> 1) * 4 + j) * 32 + lane];
+                            c4[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+                        }
+                        o = make_double4(c4[0], c4[1], c4[2], c4[3]);
                     }
+                    part[slot] = o;
+                } else {
+                    double g6[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        if constexpr (MODE == 2) {
+                            g6[j] = accg[q][j];
+                        } else {
+                            const float4 v = ws.accdf[((q >> 1) * 6 + j) * 32 + lane];
+                            g6[j] = (q & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+                        }
+                    }
+                    part[2 * slot] = make_double4(g6[0], g6[1], g6[2], g6[3]);
+                    part[2 * slot + 1] = make_double4(g6[4], g6[5], 0.0, 0.0);
                 }
-                const size_t slot = (size_t)sidx(q) * p.n_chunks + chunk;
-                p.part_g[2 * slot] = make_double4(g6[0], g6[1], g6[2], g6[3]);
-                p.part_g[2 * slot + 1] = make_double4(g6[4], g6[5], 0.0, 0.0);
                 p.near_cnt[slot] = ws.ncnt[q * 32 + lane];
             }
+            const int n_tiles = (p.n_pts + p.tile_pts - 1) / p.tile_pts;  // capacity tiles (counter layout)
+            finish_tile<NPART, PT>(p, part, NPART == 1 ? p.far : p.far_g, tile, base, n_pts, n_tiles, lane);
         }
     }
     if (STATS) {
@@ -1342,6 +1424,12 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.part = a.part;
     k.part_g = a.part_g;
     k.near_cnt = a.near_cnt;
+    k.far = a.far;
+    k.far_g = a.far_g;
+    k.near_tot = a.near_tot;
+    k.near_row = a.near_row;
+    k.near_rows = a.near_rows;
+    k.tile_done = a.tile_done;
     k.near_rec = a.near_rec;
     k.counters = a.counters;
     k.near_cap = a.near_cap;
@@ -1374,6 +1462,13 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     }
     k.n_items = n_tiles * k.n_chunks;
     k.tile_pts = tile;
+    if (!a.A) {  // per-tile item counters and the near_rows row counter start at zero
+        if (!a.tile_done) {
+            set_error("launch_far: no tile counters");
+            return BEM_ERR_INVALID;
+        }
+        BEM_CUDA_TRY(cudaMemsetAsync(a.tile_done, 0, sizeof(int) * ((size_t)n_tiles + 1), s));
+    }
     const bool st = a.stats != 0;
     if (a.part_g) {  // field gradient: the mesh's precision
         if (f64) return launch_stats<true, kPtFp64, true, 2>(k, s, st);

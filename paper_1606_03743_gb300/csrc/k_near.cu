@@ -147,23 +147,29 @@ __device__ void polygon_grad(int nv, const double* __restrict__ V, D3 P, double 
     out[5] = G[1][2];
 }
 
-// far gradient sums of the chunks in chunk order + near pairs in element
-// order, times 1/(4 pi eps0), written at the point's original position.
-__global__ void k_finalize_grad(int n, int n_chunks, const int* __restrict__ perm, const double4* __restrict__ part_g,
-                                const int* __restrict__ near_cnt, const int* __restrict__ near_off,
+// Slot of near record r = (sorted point, element, ordinal in its chunk, chunk)
+// among all near values: the point's first slot, plus its near pairs in the
+// chunks before r's chunk, plus the ordinal -- so a point's values sit in
+// element order.
+__device__ __forceinline__ unsigned long long near_slot(const int4 r, const int* __restrict__ near_off,
+                                                        const int* __restrict__ near_row,
+                                                        const int* __restrict__ near_rows, int n_chunks) {
+    return (unsigned long long)near_off[r.x] + (unsigned long long)near_rows[(size_t)near_row[r.x] * n_chunks + r.w] +
+           (unsigned long long)r.z;
+}
+
+// far gradient sums (the chunks already summed in chunk order) + near pairs in
+// element order, times 1/(4 pi eps0), written at the point's original position.
+__global__ void k_finalize_grad(int n, const int* __restrict__ perm, const double4* __restrict__ far_g,
+                                const int* __restrict__ near_tot, const int* __restrict__ near_off,
                                 const double4* __restrict__ gval, unsigned long long gcap, double kc,
                                 double* __restrict__ G) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const size_t p0 = (size_t)i * n_chunks;
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    int cnt = 0;
-    for (int c = 0; c < n_chunks; ++c) {
-        const double4 a = part_g[2 * (p0 + c)], b = part_g[2 * (p0 + c) + 1];
-        s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w; s[4] += b.x; s[5] += b.y;
-        cnt += near_cnt[p0 + c];
-    }
-    const unsigned long long off = (unsigned long long)near_off[p0];
+    const double4 a0 = far_g[2 * (size_t)i], b0 = far_g[2 * (size_t)i + 1];
+    double s[6] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y};
+    const int cnt = near_tot[i];
+    const unsigned long long off = (unsigned long long)near_off[i];
     for (int k = 0; k < cnt; ++k) {
         if (off + k >= gcap) break;
         const double4 a = gval[2 * (off + k)], b = gval[2 * (off + k) + 1];
@@ -457,7 +463,8 @@ __device__ void polygon_grad_var(int nv, const double* __restrict__ V, D3 P, con
 // linear / quadratic densities (slope set) by polygon_grad_var.
 __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
-                            const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
+                            const int* __restrict__ near_off, const int* __restrict__ near_row,
+                            const int* __restrict__ near_rows, int n_chunks, const int* __restrict__ type,
                             const double* __restrict__ verts, const double* __restrict__ sigma,
                             const double* __restrict__ slope, const double* __restrict__ curv,
                             const double* __restrict__ fr, const double* __restrict__ cen,
@@ -479,8 +486,7 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
         } else {
             polygon_grad(nv, verts + 12 * (size_t)r.y, P, f);
         }
-        const unsigned long long slot =
-            (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
+        const unsigned long long slot = near_slot(r, near_off, near_row, near_rows, n_chunks);
         if (slot < gcap) {
             gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
             gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
@@ -490,7 +496,8 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
 
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
-                            const int* __restrict__ near_off, int n_chunks, const int* __restrict__ type,
+                            const int* __restrict__ near_off, const int* __restrict__ near_row,
+                            const int* __restrict__ near_rows, int n_chunks, const int* __restrict__ type,
                             const double* __restrict__ verts, const double* __restrict__ sigma,
                             const double* __restrict__ slope, const double* __restrict__ curv,
                             const double* __restrict__ fr, const double* __restrict__ cen,
@@ -513,33 +520,24 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
         } else {
             polygon_field(nv, verts + 12 * (size_t)r.y, P, f);
         }
-        const unsigned long long slot =
-            (unsigned long long)near_off[(size_t)r.x * n_chunks + r.w] + (unsigned long long)r.z;
+        const unsigned long long slot = near_slot(r, near_off, near_row, near_rows, n_chunks);
         if (slot < cap) val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
     }
 }
 
-// far sums of the element chunks in chunk order + near contributions in
-// element order, times 1/(4 pi eps0), written at the point's original position.
-__global__ void k_finalize(int n, const int* n_dev, int n_chunks, const int* __restrict__ perm,
-                           const double4* __restrict__ part, const int* __restrict__ near_cnt,
-                           const int* __restrict__ near_off, const double4* __restrict__ val, unsigned long long cap,
-                           double kc, double* phi, double* E, int stride4) {
+// far sums (the element chunks already summed in chunk order) + near
+// contributions in element order, times 1/(4 pi eps0), written at the point's
+// original position.
+__global__ void k_finalize(int n, const int* n_dev, const int* __restrict__ perm, const double4* __restrict__ far,
+                           const int* __restrict__ near_tot, const int* __restrict__ near_off,
+                           const double4* __restrict__ val, unsigned long long cap, double kc, double* phi, double* E,
+                           int stride4) {
     if (n_dev) n = min(n, *n_dev);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const size_t p0 = (size_t)i * n_chunks;
-    double4 s = part[p0];
-    int cnt = near_cnt[p0];
-    for (int c = 1; c < n_chunks; ++c) {
-        const double4 v = part[p0 + c];
-        s.x += v.x;
-        s.y += v.y;
-        s.z += v.z;
-        s.w += v.w;
-        cnt += near_cnt[p0 + c];
-    }
-    const unsigned long long off = (unsigned long long)near_off[p0];
+    double4 s = far[i];
+    const int cnt = near_tot[i];
+    const unsigned long long off = (unsigned long long)near_off[i];
     for (int k = 0; k < cnt; ++k) {
         if (off + k >= cap) break;
         const double4 v = val[off + k];
@@ -608,7 +606,8 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
     (void)n_pts;
     Work& w = m->w;
     k_near_eval<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
-                                        m->n_chunks, m->d.type, m->d.verts, sigma, slope, eval_curv(m, slope),
+                                        w.near_row, w.near_rows, m->n_chunks, m->d.type, m->d.verts, sigma, slope,
+                                        eval_curv(m, slope),
                                         m->d.fr, m->d.cen, w.near_val);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
@@ -618,8 +617,7 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
 int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double* E, int stride4, cudaStream_t s,
                     const int* n_dev) {
     Work& w = m->w;
-    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, n_dev, m->n_chunks, perm, w.part, w.near_cnt, w.near_off,
-                                                   w.near_val,
+    k_finalize<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, n_dev, perm, w.far, w.near_tot, w.near_off, w.near_val,
                                                    (unsigned long long)w.cap_near, m->kc, phi, E, stride4);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
@@ -630,17 +628,18 @@ int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const doub
                      unsigned long long gcap, cudaStream_t s, const double* slope) {
     Work& w = m->w;
     k_near_grad<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, gcap, pts, perm,
-                                        w.near_off, m->n_chunks, m->d.type, m->d.verts, sigma, slope,
+                                        w.near_off, w.near_row, w.near_rows, m->n_chunks, m->d.type, m->d.verts,
+                                        sigma, slope,
                                         eval_curv(m, slope), m->d.fr, m->d.cen, gval);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
 }
 
-int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* part_g, const double4* gval,
+int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4* far_g, const double4* gval,
                          unsigned long long gcap, double* G, cudaStream_t s) {
     Work& w = m->w;
-    k_finalize_grad<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, m->n_chunks, perm, part_g, w.near_cnt, w.near_off,
+    k_finalize_grad<<<(n_pts + 255) / 256, 256, 0, s>>>(n_pts, perm, far_g, w.near_tot, w.near_off,
                                                         gval, gcap, m->kc, G);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);

@@ -37,8 +37,13 @@ constexpr size_t kOffCellCnt = kOffKey + align_up(4 * kMaxPts);
 constexpr size_t kOffCellOff = kOffCellCnt + align_up(4 * kCellsMax);
 constexpr size_t kOffPart = kOffCellOff + align_up(4 * kCellsMax);
 constexpr size_t kOffNearCnt = kOffPart + align_up(32 * kMaxPts * kChunksCap);
-constexpr size_t kOffNearOff = kOffNearCnt + align_up(4 * kMaxPts * kChunksCap);
-constexpr size_t kOffScan = kOffNearOff + align_up(4 * kMaxPts * kChunksCap);
+constexpr size_t kOffNearRows = kOffNearCnt + align_up(4 * kMaxPts * kChunksCap);
+constexpr size_t kOffFar = kOffNearRows + align_up(4 * kMaxPts * kChunksCap);
+constexpr size_t kOffNearTot = kOffFar + align_up(32 * kMaxPts);
+constexpr size_t kOffNearRow = kOffNearTot + align_up(4 * kMaxPts);
+constexpr size_t kOffNearOff = kOffNearRow + align_up(4 * kMaxPts);
+constexpr size_t kOffTileDone = kOffNearOff + align_up(4 * kMaxPts);
+constexpr size_t kOffScan = kOffTileDone + align_up(4 * tile_done_ints(kMaxPts));
 constexpr size_t kOffRec = kOffScan + align_up(4 * kScanInts);
 constexpr size_t kOffVal = kOffRec + align_up(16 * kMaxNear);
 constexpr size_t kOffCounters = kOffVal + align_up(32 * kMaxNear);
@@ -120,7 +125,12 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     w.cell_off = reinterpret_cast<int*>(base + kOffCellOff);
     w.part = reinterpret_cast<double4*>(base + kOffPart);
     w.near_cnt = reinterpret_cast<int*>(base + kOffNearCnt);
+    w.near_rows = reinterpret_cast<int*>(base + kOffNearRows);
+    w.far = reinterpret_cast<double4*>(base + kOffFar);
+    w.near_tot = reinterpret_cast<int*>(base + kOffNearTot);
+    w.near_row = reinterpret_cast<int*>(base + kOffNearRow);
     w.near_off = reinterpret_cast<int*>(base + kOffNearOff);
+    w.tile_done = reinterpret_cast<int*>(base + kOffTileDone);
     w.scan_tmp = reinterpret_cast<int*>(base + kOffScan);
     w.cap_near = kMaxNear;
     w.near_rec = reinterpret_cast<int4*>(base + kOffRec);
@@ -129,7 +139,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     w.bbox = reinterpret_cast<float4*>(base + kOffBbox);
     view.stats = false;
     view.timing = false;
-    if (m->n_chunks > (int)kChunksCap || scan_tmp_ints((int)(kMaxPts * kChunksCap)) > kScanInts ||
+    if (m->n_chunks > (int)kChunksCap || scan_tmp_ints((int)kMaxPts) > kScanInts ||
         scan_tmp_ints((int)kCellsMax) > kScanInts) {
         set_error("bem_eval_noalloc: internal scan scratch too small");
         return BEM_ERR_CAPACITY;
@@ -152,8 +162,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.n_pts = (int)n;
     a.sigma = m->d.sigma;
     a.slope = eval_slope(m, m->d.sigma);
-    a.part = w.part;
-    a.near_cnt = w.near_cnt;
+    far_args_from_work(a, w);
     a.work = reinterpret_cast<int*>(w.counters + 14);
     a.near_rec = w.near_rec;
     a.counters = w.counters;
@@ -163,7 +172,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.stats = 0;
     a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
     if ((rc = launch_far(&view, a, s))) return rc;
-    if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, (int)n * m->n_chunks, w.scan_tmp, s))) return rc;
+    if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, (int)n, w.scan_tmp, s))) return rc;
     if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s, eval_slope(m, m->d.sigma)))) return rc;
     if ((rc = launch_finalize(&view, w.perm, (int)n, phi, E, 0, s))) return rc;
     unsigned long long n_near = 0;

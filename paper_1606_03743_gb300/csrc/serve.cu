@@ -134,10 +134,8 @@ int enqueue_pipeline(bem_server* sv, Slot& sl) {
     bem_mesh* m = &sl.view;
     Work& w = m->w;
     const int cap = (int)sv->cap;
-    const int ns = cap * m->n_chunks;
     cudaStream_t s = sl.stream;
     BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, kCountersN * sizeof(unsigned long long), s));
-    BEM_CUDA_TRY(cudaMemsetAsync(w.near_cnt, 0, sizeof(int) * (size_t)ns, s));
     int rc = launch_sort_points(m, sl.d_pts, cap, s, sl.d_n);
     if (rc) return rc;
     FarArgs a{};
@@ -147,8 +145,7 @@ int enqueue_pipeline(bem_server* sv, Slot& sl) {
     a.n_dev = sl.d_n;
     a.sigma = m->d.sigma;
     a.slope = eval_slope(m, m->d.sigma);
-    a.part = w.part;
-    a.near_cnt = w.near_cnt;
+    far_args_from_work(a, w);
     a.work = reinterpret_cast<int*>(w.counters + 14);
     a.near_rec = w.near_rec;
     a.counters = w.counters;
@@ -157,7 +154,8 @@ int enqueue_pipeline(bem_server* sv, Slot& sl) {
     a.want_e = 1;
     a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
     if ((rc = launch_far(m, a, s))) return rc;
-    if ((rc = launch_exclusive_scan(w.near_cnt, w.near_off, ns, w.scan_tmp, s))) return rc;
+    // entries past the tick's points are stale but only shift offsets after them
+    if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, cap, w.scan_tmp, s))) return rc;
     if ((rc = launch_near_eval(m, sl.d_pts, w.perm, cap, m->d.sigma, 0, s, eval_slope(m, m->d.sigma)))) return rc;
     return launch_finalize(m, w.perm, cap, sl.d_phi, sl.d_E, 0, s, sl.d_n);
 }
@@ -169,7 +167,9 @@ int slot_setup(bem_server* sv, Slot& sl) {
     sl.view.stats = false;
     sl.view.timing = false;
     Work& w = sl.view.w;
-    const size_t cap = (size_t)sv->cap, ns = cap * (size_t)mesh->n_chunks;
+    const size_t cap = (size_t)sv->cap;
+    const size_t capt = (cap + 127) / 128 * 128;  // whole tiles of the far pass
+    const size_t ns = capt * (size_t)mesh->n_chunks;
     const size_t cells = size_t(1) << 21;
     int rc;
     if ((rc = slot_alloc(sv, sl, &sl.d_pts, 3 * cap)) || (rc = slot_alloc(sv, sl, &sl.d_phi, cap)) ||
@@ -177,8 +177,10 @@ int slot_setup(bem_server* sv, Slot& sl) {
         (rc = slot_alloc(sv, sl, &w.perm, cap)) || (rc = slot_alloc(sv, sl, &w.key, cap)) ||
         (rc = slot_alloc(sv, sl, &w.cell_cnt, cells)) || (rc = slot_alloc(sv, sl, &w.cell_off, cells)) ||
         (rc = slot_alloc(sv, sl, &w.part, ns)) || (rc = slot_alloc(sv, sl, &w.near_cnt, ns)) ||
-        (rc = slot_alloc(sv, sl, &w.near_off, ns)) ||
-        (rc = slot_alloc(sv, sl, &w.scan_tmp, scan_tmp_ints((int)std::max(ns, cells)))) ||
+        (rc = slot_alloc(sv, sl, &w.near_rows, ns)) || (rc = slot_alloc(sv, sl, &w.far, capt)) ||
+        (rc = slot_alloc(sv, sl, &w.near_tot, capt)) || (rc = slot_alloc(sv, sl, &w.near_row, capt)) ||
+        (rc = slot_alloc(sv, sl, &w.near_off, capt)) || (rc = slot_alloc(sv, sl, &w.tile_done, tile_done_ints(capt))) ||
+        (rc = slot_alloc(sv, sl, &w.scan_tmp, scan_tmp_ints((int)std::max(capt, cells)))) ||
         (rc = slot_alloc(sv, sl, &w.near_rec, sv->near_cap)) || (rc = slot_alloc(sv, sl, &w.near_val, sv->near_cap)) ||
         (rc = slot_alloc(sv, sl, &w.counters, kCountersN)) || (rc = slot_alloc(sv, sl, &w.bbox, 2)))
         return rc;
@@ -436,7 +438,7 @@ int bem_server_create(bem_mesh* mesh, const bem_server_options* opt, bem_server*
     // admission by device memory: shrink the per-tick capacity until both slots fit the budget
     auto need = [&](int64_t c) {
         const size_t ns = (size_t)c * mesh->n_chunks;
-        return 2 * (sizeof(double) * 7 * c + sizeof(int) * 2 * c + 40 * ns + 48 * sv->near_cap + (size_t(17) << 20));
+        return 2 * (sizeof(double) * 11 * c + sizeof(int) * 5 * c + 40 * ns + 48 * sv->near_cap + (size_t(17) << 20));
     };
     while (cap > 1024 && need(cap) > budget) cap /= 2;
     if (cap < 1 || cap > (int64_t(1) << 24) || need(cap) > budget) {
