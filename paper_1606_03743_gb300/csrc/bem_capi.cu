@@ -305,15 +305,16 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
                 m->last_times[k] = t;
             }
         }
-        if (cnt[0] <= w.cap_near) {
-            m->last_stats[12] = (int64_t)cnt[0];
+        const unsigned long long pairs = cnt[kPairCounter];  // values; the run records are fewer
+        if (pairs <= w.cap_near) {
+            m->last_stats[12] = (int64_t)pairs;
             if (m->stats) {
                 for (int k = 0; k < 12; ++k) m->last_stats[k] = (int64_t)cnt[2 + k];
                 for (int k = 0; k < 3; ++k) m->last_stats[13 + k] = (int64_t)cnt[16 + k];
             }
             return BEM_OK;
         }
-        if ((rc = ensure_near(m, (size_t)cnt[0]))) return rc;  // grow and run again
+        if ((rc = ensure_near(m, (size_t)pairs))) return rc;  // grow and run again
     }
     set_error("near-pair list did not converge");
     return BEM_ERR_CAPACITY;
@@ -780,8 +781,8 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         a.bbox = reinterpret_cast<const unsigned*>(w.bbox);
         if ((rc = launch_far(m, a, s))) return rc;
         if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, (int)n, w.scan_tmp, s))) return rc;
-        unsigned long long n_near = 0;
-        BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters, sizeof n_near, cudaMemcpyDeviceToHost, s));
+        unsigned long long n_near = 0;  // near pairs (values)
+        BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters + kPairCounter, sizeof n_near, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
         if (n_near > w.cap_near) {
             if ((rc = ensure_near(m, (size_t)n_near))) return rc;  // grow and run again
@@ -916,15 +917,16 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
             rc = cuda_fail(e, "bem_assemble");
             break;
         }
-        if (cnt[0] <= w.cap_near) {
-            m->last_stats[12] = (int64_t)cnt[0];
+        const unsigned long long pairs = cnt[kPairCounter];  // at least the run records
+        if (pairs <= w.cap_near) {
+            m->last_stats[12] = (int64_t)pairs;
             if (m->stats) {
                 for (int k = 0; k < 12; ++k) m->last_stats[k] = (int64_t)cnt[2 + k];
                 for (int k = 0; k < 3; ++k) m->last_stats[13 + k] = (int64_t)cnt[16 + k];
             }
             break;
         }
-        rc = ensure_near(m, (size_t)cnt[0]);
+        rc = ensure_near(m, (size_t)pairs);
         if (!rc && attempt == 2) {
             set_error("near-pair list did not converge");
             rc = BEM_ERR_CAPACITY;

@@ -96,16 +96,18 @@ struct Work {
     int* tile_done = nullptr;     // work items finished per tile, then the near_rows row counter
     int* scan_tmp = nullptr;      // block sums of the scans
     size_t cap_near = 0;
-    int4* near_rec = nullptr;     // (sorted point, element, ordinal, chunk)
+    int4* near_rec = nullptr;     // runs: (sorted point, first element, first ordinal, pairs)
     double4* near_val = nullptr;  // analytic contributions in (point, ordinal) order
-    unsigned long long* counters = nullptr;  // [0] near pairs, [1] bad element, [2..13] band stats,
-                                             // [14] far work-item counter, [15] bad field point,
-                                             // [16..18] far-kernel efficiency counts (statistics runs)
+    unsigned long long* counters = nullptr;  // [0] near-pair runs (records), [1] bad element, [2..13] band
+                                             // stats, [14] far work-item counter, [15] bad field point,
+                                             // [16..18] far-kernel efficiency counts (statistics runs),
+                                             // [19] near pairs (values)
     float4* bbox = nullptr;       // [2] points bbox (min, max)
     size_t bytes = 0;
 };
 
 enum Precision { kFP64 = 0, kMixed = 1 };
+constexpr int kPairCounter = 19;  // counters[kPairCounter]: near pairs of a call
 
 }  // namespace bem
 

@@ -194,26 +194,73 @@ __device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
 
 // Warp-cooperative append of near pairs; want[q] marks point q of this lane.
-// Point q of a lane is sorted point tile_base + 32 q + lane; its near-pair
-// ordinal counter ncnt[32 q + lane] lives in the warp's shared memory.
+// Near pairs are recorded as runs: a run is a sequence of consecutive elements
+// of one chunk that are all in the analytic band for one point, recorded as
+// (sorted point, first element, ordinal of its first pair among the point's
+// near pairs in the chunk, number of pairs).  Point q of a lane is sorted point
+// tile_base + 32 q + lane; its open run (first element, length) and its pair
+// counter (the next ordinal) live in the warp's shared memory.
+constexpr int kMaxRun = 1 << 20;  // a longer run is split
+
+// Append the runs of the lanes marked in `emit` (point q) to the list.
+__device__ __forceinline__ void emit_runs(const FarK& p, bool emit, int sp, int first, int ord, int len, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, emit);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(p.counters, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (emit) {
+        const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+        if (idx < p.near_cap) p.near_rec[idx] = make_int4(sp, first, ord, len);
+    }
+}
+
+// Element `elem` is in the analytic band for the points marked in want[q]:
+// extend their open runs, or close them (append) and open new ones.
 template <int PT>
-__device__ __forceinline__ void append_near(const FarK& p, const bool (&want)[PT], int tile_base, int elem, int chunk,
-                                            int* ncnt, int lane) {
+__device__ __forceinline__ void note_near(const FarK& p, const bool (&want)[PT], int tile_base, int elem, int* run_first,
+                                          int* run_len, int* ncnt, int lane) {
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
-        const unsigned m = __ballot_sync(0xffffffffu, want[q]);
-        if (!m) continue;
-        const int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(p.counters, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
+        const int i = q * 32 + lane;
+        int first = 0, len = 0, cnt = 0;
+        bool close = false;
         if (want[q]) {  // only live points want pairs
-            const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-            const int o = ncnt[q * 32 + lane];
-            if (idx < p.near_cap) p.near_rec[idx] = make_int4(tile_base + q * 32 + lane, elem, o, chunk);
-            ncnt[q * 32 + lane] = o + 1;
+            first = run_first[i];
+            len = run_len[i];
+            cnt = ncnt[i];
+            close = len > 0 && (first + len != elem || len == kMaxRun);
+        }
+        emit_runs(p, close, tile_base + i, first, cnt - len, len, lane);
+        if (want[q]) {
+            if (len == 0 || close) {
+                run_first[i] = elem;
+                run_len[i] = 1;
+            } else {
+                run_len[i] = len + 1;
+            }
+            ncnt[i] = cnt + 1;
         }
     }
+}
+
+// End of a work item: append every open run; add the item's pairs to the pair counter.
+template <int PT>
+__device__ __forceinline__ void close_runs(const FarK& p, int tile_base, int n_pts, int* run_first, int* run_len,
+                                           const int* ncnt, int lane) {
+    int pairs = 0;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const int i = q * 32 + lane;
+        const bool live = tile_base + i < n_pts;
+        const int len = live ? run_len[i] : 0;
+        const int cnt = live ? ncnt[i] : 0;
+        pairs += cnt;
+        emit_runs(p, len > 0, tile_base + i, live ? run_first[i] : 0, cnt - len, len, lane);
+    }
+    for (int o = 16; o; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if (lane == 0 && pairs) atomicAdd(p.counters + kPairCounter, (unsigned long long)pairs);
 }
 
 // One point charge (offset o, charge o.w) at the PT points of a lane.
@@ -479,6 +526,7 @@ struct WarpSmem {
     // (hi.x, hi.y, lo.x, lo.y)
     float4 accdf[NACC ? (PT / 2) * NACC * 32 : 1];
     int ncnt[PT * 32];  // near pairs found so far per point of the tile (their ordinals)
+    int run_first[PT * 32], run_len[PT * 32];  // each point's open run of near pairs
 };
 
 template <typename R>
@@ -670,6 +718,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
         for (int q = 0; q < PT; ++q) {
             const int i = sidx(q);
             ws.ncnt[q * 32 + lane] = 0;
+            ws.run_len[q * 32 + lane] = 0;
             const int src = p.perm[i];
             const double X = p.pts[3 * (size_t)src], Y = p.pts[3 * (size_t)src + 1], Z = p.pts[3 * (size_t)src + 2];
             if constexpr (F64) {
@@ -889,7 +938,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             bool want[PT];
 #pragma unroll
                             for (int q = 0; q < PT; ++q) want[q] = valid(q) && bq[q] == 0;
-                            append_near<PT>(p, want, base, b0 + e, chunk, ws.ncnt, lane);
+                            note_near<PT>(p, want, base, b0 + e, ws.run_first, ws.run_len, ws.ncnt, lane);
                         }
                         if (kElemSum) {  // near-only points get zero far sums
 #pragma unroll
@@ -1063,7 +1112,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             bool want[PT];
 #pragma unroll
                             for (int q = 0; q < PT; ++q) want[q] = valid(q) && bq[q] == 0;
-                            append_near<PT>(p, want, base, b0 + e, chunk, ws.ncnt, lane);
+                            note_near<PT>(p, want, base, b0 + e, ws.run_first, ws.run_len, ws.ncnt, lane);
                         }
 #pragma unroll
                         for (int k = 0; k < NP; ++k)
@@ -1222,6 +1271,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             }
         }
 
+        // ---- the item's open near-pair runs
+        close_runs<PT>(p, base, n_pts, ws.run_first, ws.run_len, ws.ncnt, lane);
         // ---- this item's partial sums and near-pair counts, then the tile's reduction
         constexpr int NPART = MODE == 0 ? 1 : (MODE == 2 || MODE == 3) ? 2 : 0;
         if constexpr (NPART > 0) {

@@ -147,15 +147,72 @@ __device__ void polygon_grad(int nv, const double* __restrict__ V, D3 P, double 
     out[5] = G[1][2];
 }
 
-// Slot of near record r = (sorted point, element, ordinal in its chunk, chunk)
-// among all near values: the point's first slot, plus its near pairs in the
-// chunks before r's chunk, plus the ordinal -- so a point's values sit in
-// element order.
+// Slot, among all near values, of the first pair of near-pair run r =
+// (sorted point, first element, ordinal of its first pair in its chunk, pairs):
+// the point's first slot, plus its near pairs in the chunks before the run's
+// chunk (the element's chunk), plus the ordinal -- so a point's values sit in
+// element order.  The run's other pairs follow in the next slots.
 __device__ __forceinline__ unsigned long long near_slot(const int4 r, const int* __restrict__ near_off,
                                                         const int* __restrict__ near_row,
-                                                        const int* __restrict__ near_rows, int n_chunks) {
-    return (unsigned long long)near_off[r.x] + (unsigned long long)near_rows[(size_t)near_row[r.x] * n_chunks + r.w] +
+                                                        const int* __restrict__ near_rows, int n_chunks,
+                                                        int chunk_len) {
+    const int chunk = r.y / chunk_len;
+    return (unsigned long long)near_off[r.x] + (unsigned long long)near_rows[(size_t)near_row[r.x] * n_chunks + chunk] +
            (unsigned long long)r.z;
+}
+
+// The near-pair passes run with blocks of kNearThreads threads.
+constexpr int kNearThreads = 128;
+constexpr int kNearWarps = kNearThreads / 32;
+
+// Calls f(run, k, P, slot) for pair k of every near-pair run: each warp takes
+// 32 runs at a time, lays their pairs end to end (a warp prefix sum of the run
+// lengths) and deals them out to its lanes, so that a long run does not leave
+// the warp's other lanes idle.  P is the run's field point; slot its pair's
+// slot among the near values (slot_of(run) + k), or the run's index when
+// slot_of is null (assembly writes no values).
+template <typename SlotOf, typename F>
+__device__ __forceinline__ void for_each_near_pair(const int4* __restrict__ rec, unsigned long long n_runs,
+                                                   const double* __restrict__ pts, const int* __restrict__ perm,
+                                                   SlotOf slot_of, F f) {
+    __shared__ int4 s_rec[kNearWarps][32];
+    __shared__ int s_first[kNearWarps][32];
+    __shared__ unsigned long long s_slot[kNearWarps][32];
+    __shared__ double s_P[kNearWarps][32][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kNearWarps * 32;
+    for (unsigned long long b = ((unsigned long long)blockIdx.x * kNearWarps + warp) * 32; b < n_runs; b += stride) {
+        const unsigned long long i = b + lane;
+        const int4 r = i < n_runs ? rec[i] : make_int4(0, 0, 0, 0);
+        int incl = r.w;  // inclusive prefix sum of the run lengths over the lanes
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_rec[warp][lane] = r;
+        s_first[warp][lane] = incl - r.w;
+        if (r.w > 0) {
+            const int src = perm[r.x];
+            s_P[warp][lane][0] = pts[3 * (size_t)src];
+            s_P[warp][lane][1] = pts[3 * (size_t)src + 1];
+            s_P[warp][lane][2] = pts[3 * (size_t)src + 2];
+            s_slot[warp][lane] = slot_of(r);
+        }
+        __syncwarp();
+        for (int j = lane; j < total; j += 32) {
+            int lo = 0, hi = 31;  // the last run whose first pair is at or before j (lengths are >= 1)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_first[warp][mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            const int k = j - s_first[warp][lo];
+            const D3 P{s_P[warp][lo][0], s_P[warp][lo][1], s_P[warp][lo][2]};
+            f(s_rec[warp][lo], k, P, s_slot[warp][lo] + (unsigned long long)k);
+        }
+        __syncwarp();
+    }
 }
 
 // far gradient sums (the chunks already summed in chunk order) + near pairs in
@@ -459,70 +516,66 @@ __device__ void polygon_grad_var(int nv, const double* __restrict__ V, D3 P, con
     out[5] = 0.5 * (Gab(1, 2) + Gab(2, 1));
 }
 
-// Gradient of each compacted near pair, times sigma, at the pair's slot (two double4);
-// linear / quadratic densities (slope set) by polygon_grad_var.
+// Gradient of each near-pair run's pairs, times sigma, at the pairs' slots (two double4
+// each); linear / quadratic densities (slope set) by polygon_grad_var.
 __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, const int* __restrict__ near_row,
-                            const int* __restrict__ near_rows, int n_chunks, const int* __restrict__ type,
-                            const double* __restrict__ verts, const double* __restrict__ sigma,
-                            const double* __restrict__ slope, const double* __restrict__ curv,
-                            const double* __restrict__ fr, const double* __restrict__ cen,
-                            double4* __restrict__ gval) {
+                            const int* __restrict__ near_rows, int n_chunks, int chunk_len,
+                            const int* __restrict__ type, const double* __restrict__ verts,
+                            const double* __restrict__ sigma, const double* __restrict__ slope,
+                            const double* __restrict__ curv, const double* __restrict__ fr,
+                            const double* __restrict__ cen, double4* __restrict__ gval) {
     const unsigned long long n = min(counters[0], cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int4 r = rec[i];
-        const int src = perm[r.x];
-        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
-        const int nv = type[r.y] == BEM_RECTANGLE ? 4 : 3;
+    auto slot_of = [&](const int4 r) { return near_slot(r, near_off, near_row, near_rows, n_chunks, chunk_len); };
+    for_each_near_pair(rec, n, pts, perm, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
+        if (slot >= gcap) return;
+        const int el = r.y + k;
+        const int nv = type[el] == BEM_RECTANGLE ? 4 : 3;
         double f[6];
-        double sg = sigma[r.y];
+        double sg = sigma[el];
         if (slope) {
             Density dn;
-            element_density(r.y, sg, slope, curv, fr, cen, dn);
-            polygon_grad_var(nv, verts + 12 * (size_t)r.y, P, dn, f);
+            element_density(el, sg, slope, curv, fr, cen, dn);
+            polygon_grad_var(nv, verts + 12 * (size_t)el, P, dn, f);
             sg = 1.0;
         } else {
-            polygon_grad(nv, verts + 12 * (size_t)r.y, P, f);
+            polygon_grad(nv, verts + 12 * (size_t)el, P, f);
         }
-        const unsigned long long slot = near_slot(r, near_off, near_row, near_rows, n_chunks);
-        if (slot < gcap) {
-            gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
-            gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
-        }
-    }
+        gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
+        gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
+    });
 }
 
+// phi and E of each near-pair run's pairs, times sigma, at the pairs' slots;
+// linear / quadratic densities (slope set) by the analytic integral of the density.
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
                             const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, const int* __restrict__ near_row,
-                            const int* __restrict__ near_rows, int n_chunks, const int* __restrict__ type,
-                            const double* __restrict__ verts, const double* __restrict__ sigma,
-                            const double* __restrict__ slope, const double* __restrict__ curv,
-                            const double* __restrict__ fr, const double* __restrict__ cen,
-                            double4* __restrict__ val) {
+                            const int* __restrict__ near_rows, int n_chunks, int chunk_len,
+                            const int* __restrict__ type, const double* __restrict__ verts,
+                            const double* __restrict__ sigma, const double* __restrict__ slope,
+                            const double* __restrict__ curv, const double* __restrict__ fr,
+                            const double* __restrict__ cen, double4* __restrict__ val) {
     const unsigned long long n = min(counters[0], cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int4 r = rec[i];
-        const int src = perm[r.x];
-        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
+    auto slot_of = [&](const int4 r) { return near_slot(r, near_off, near_row, near_rows, n_chunks, chunk_len); };
+    for_each_near_pair(rec, n, pts, perm, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
+        if (slot >= cap) return;
+        const int el = r.y + k;
         double f[4];
-        const int nv = type[r.y] == BEM_RECTANGLE ? 4 : 3;
-        double sg = sigma[r.y];
+        const int nv = type[el] == BEM_RECTANGLE ? 4 : 3;
+        double sg = sigma[el];
         if (slope) {
             Density dn;
-            element_density(r.y, sg, slope, curv, fr, cen, dn);
-            if (curv) polygon_field_quad(nv, verts + 12 * (size_t)r.y, P, dn.sc, dn.g, dn.H, dn.C, f);
-            else polygon_field_lin(nv, verts + 12 * (size_t)r.y, P, dn.sc, dn.g, dn.C, f);
+            element_density(el, sg, slope, curv, fr, cen, dn);
+            if (curv) polygon_field_quad(nv, verts + 12 * (size_t)el, P, dn.sc, dn.g, dn.H, dn.C, f);
+            else polygon_field_lin(nv, verts + 12 * (size_t)el, P, dn.sc, dn.g, dn.C, f);
             sg = 1.0;
         } else {
-            polygon_field(nv, verts + 12 * (size_t)r.y, P, f);
+            polygon_field(nv, verts + 12 * (size_t)el, P, f);
         }
-        const unsigned long long slot = near_slot(r, near_off, near_row, near_rows, n_chunks);
-        if (slot < cap) val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
-    }
+        val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
+    });
 }
 
 // far sums (the element chunks already summed in chunk order) + near
@@ -567,15 +620,13 @@ __global__ void k_near_assemble(const int4* __restrict__ rec, const unsigned lon
                                 const int* __restrict__ type, const double* __restrict__ verts, int n_el, double kc,
                                 double* __restrict__ A) {
     const unsigned long long n = min(counters[0], cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int4 r = rec[i];
-        const int src = perm[r.x];
-        const D3 P{pts[3 * (size_t)src], pts[3 * (size_t)src + 1], pts[3 * (size_t)src + 2]};
+    auto no_slot = [](const int4) { return 0ull; };
+    for_each_near_pair(rec, n, pts, perm, no_slot, [&](const int4 r, int k, const D3 P, unsigned long long) {
+        const int el = r.y + k;
         double f[4];
-        polygon_field(type[r.y] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)r.y, P, f);
-        A[(size_t)src * n_el + r.y] = kc * f[0];
-    }
+        polygon_field(type[el] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)el, P, f);
+        A[(size_t)perm[r.x] * n_el + el] = kc * f[0];
+    });
 }
 
 // Self potential of each element at its own centroid (unit sigma), times kc:
@@ -605,9 +656,9 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
                      unsigned long long /*n_near_hint*/, cudaStream_t s, const double* slope) {
     (void)n_pts;
     Work& w = m->w;
-    k_near_eval<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
-                                        w.near_row, w.near_rows, m->n_chunks, m->d.type, m->d.verts, sigma, slope,
-                                        eval_curv(m, slope),
+    k_near_eval<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
+                                        w.near_row, w.near_rows, m->n_chunks, m->chunk_len, m->d.type, m->d.verts,
+                                        sigma, slope, eval_curv(m, slope),
                                         m->d.fr, m->d.cen, w.near_val);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
@@ -627,9 +678,9 @@ int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double
 int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
                      unsigned long long gcap, cudaStream_t s, const double* slope) {
     Work& w = m->w;
-    k_near_grad<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, gcap, pts, perm,
-                                        w.near_off, w.near_row, w.near_rows, m->n_chunks, m->d.type, m->d.verts,
-                                        sigma, slope,
+    k_near_grad<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, gcap, pts, perm,
+                                        w.near_off, w.near_row, w.near_rows, m->n_chunks, m->chunk_len, m->d.type,
+                                        m->d.verts, sigma, slope,
                                         eval_curv(m, slope), m->d.fr, m->d.cen, gval);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
@@ -649,7 +700,7 @@ int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4*
 int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double* A, unsigned long long,
                          cudaStream_t s) {
     Work& w = m->w;
-    k_near_assemble<<<152 * 8, 128, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm,
+    k_near_assemble<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm,
                                             m->d.type, m->d.verts, m->d.n, m->kc, A);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);

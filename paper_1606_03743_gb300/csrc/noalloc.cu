@@ -155,7 +155,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
         set_error("bem_eval_noalloc: a field point has a non-finite (or |x| >= 1e30) coordinate");
         return BEM_ERR_INVALID;
     }
-    BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 15 * sizeof(unsigned long long), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 24 * sizeof(unsigned long long), s));
     FarArgs a{};
     a.pts = points;
     a.perm = w.perm;
@@ -175,8 +175,8 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, (int)n, w.scan_tmp, s))) return rc;
     if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s, eval_slope(m, m->d.sigma)))) return rc;
     if ((rc = launch_finalize(&view, w.perm, (int)n, phi, E, 0, s))) return rc;
-    unsigned long long n_near = 0;
-    BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters, sizeof n_near, cudaMemcpyDeviceToHost, s));
+    unsigned long long n_near = 0;  // near pairs (values; the run records are fewer)
+    BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters + kPairCounter, sizeof n_near, cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (n_near > kMaxNear) {
         set_error("bem_eval_noalloc: %llu near-field pairs; one call takes at most %d (BEM_NOALLOC_MAX_NEAR); "

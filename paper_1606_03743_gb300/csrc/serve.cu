@@ -310,8 +310,8 @@ bool fill_and_launch(bem_server* sv, Slot& sl, bool allow_large, std::unique_loc
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl.h_E, sl.d_E, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sl.h_near, sl.view.w.counters, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                            sl.stream);
+        e = cudaMemcpyAsync(sl.h_near, sl.view.w.counters + kPairCounter, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
     lk.lock();
     if (e != cudaSuccess) {
