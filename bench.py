@@ -605,7 +605,7 @@ def node_table_ablation(a, bem, torch, mesh, p_d, phi, E, stream, far_ms_fly, op
     ms = statistics.mean(far)
     out = {"far_kernel_ms_on_the_fly": far_ms_fly, "far_kernel_ms_node_table": ms,
            "frac_node_table": ops / (ms * 1e-3) / 1e12 / peak,
-           "table_bytes": int(mesh.n * 75 * 32),
+           "table_bytes": int(mesh.n * 75 * 48),  # 75 node slots x three float4 records
            "max_rel_diff_vs_on_the_fly": {"phi": d_phi, "E": d_E}}
     m.close()
     return out

@@ -61,7 +61,7 @@ extern "C" {
 /* bem_options.flags: precomputed node records (mixed meshes only).  The
  * paper compares Gaussian points precomputed for all elements with points
  * computed on the fly (Sec. 6, Table 4).  With this flag bem_create stores,
- * for every element, the node records of all five rules of its type (2400
+ * for every element, the node records of all five rules of its type (3600
  * bytes per element, outside the scratch budget), and the far-field kernel
  * streams them into its node buffers with asynchronous copies, one element
  * ahead, instead of computing them per (warp, element).  Results agree with
