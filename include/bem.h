@@ -420,8 +420,12 @@ typedef struct {
                                         a tick that has more evaluates its
                                         requests one by one with bem_eval */
     size_t device_mem_budget;        /* bound on the server's device memory
-                                        (0: 2 GiB); max_points_per_tick is halved
-                                        until two ticks' buffers fit */
+                                        (0: 2 GiB), and never more than 3/4 of
+                                        the device memory free at creation;
+                                        max_points_per_tick is halved until two
+                                        ticks' buffers fit.  All of it is
+                                        allocated at creation: ticks allocate
+                                        nothing */
     int32_t flags;                   /* reserved, must be 0 */
 } bem_server_options;
 

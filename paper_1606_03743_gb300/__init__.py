@@ -57,15 +57,18 @@ _lib = None
 
 
 def load_library(build_if_missing: bool = True):
-    """Load the in-tree libbem.so (building it first if needed)."""
+    """Load the in-tree libbem.so (building it first if needed).  With
+    BEM_CHECKED=1 in the environment, the checked build (bounds-checked
+    kernels, see build.py) is loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if not os.path.exists(path) or _build._stale():
+    checked = os.environ.get("BEM_CHECKED", "0") == "1"
+    path = _build.lib_path(checked)
+    if not os.path.exists(path) or _build._stale(checked):
         if not build_if_missing:
             raise ImportError(f"libbem.so not built: {path}")
-        _build.build()
+        _build.build(checked=checked)
     lib = C.CDLL(path)
     vp, d, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
     lib.bem_create.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(bem_options), vp, C.POINTER(vp)]

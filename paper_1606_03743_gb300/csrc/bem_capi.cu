@@ -68,6 +68,15 @@ cudaError_t pinned_malloc(void** p, size_t bytes) {
     return cudaMallocHost(p, bytes);
 }
 
+int check_flags(unsigned long long flags, const char* fn) {
+    if (!flags) return BEM_OK;
+    set_error("%s: the checked build skipped out-of-range accesses (flags 0x%llx:%s%s%s%s%s)", fn, flags,
+              flags & kCheckPart ? " partial-sum slot" : "", flags & kCheckPoint ? " per-point array" : "",
+              flags & kCheckRow ? " near-prefix row" : "", flags & kCheckElement ? " near-pair run" : "",
+              flags & kCheckMatrix ? " matrix entry" : "");
+    return BEM_ERR_CUDA;
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
     set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
     return e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA;
@@ -268,7 +277,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
         a.n_pts = n;
         a.sigma = dsigma;
         a.slope = eval_slope(m, dsigma);
-        far_args_from_work(a, w);
+        far_args_from_work(a, w, m->n_chunks);
         a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;
@@ -305,6 +314,7 @@ int run_eval(bem_mesh* m, const double* dpts, int n, const double* dsigma, doubl
                 m->last_times[k] = t;
             }
         }
+        if ((rc = check_flags(cnt[kCheckCounter], "bem_eval"))) return rc;
         const unsigned long long pairs = cnt[kPairCounter];  // values; the run records are fewer
         if (pairs <= w.cap_near) {
             m->last_stats[12] = (int64_t)pairs;
@@ -329,7 +339,9 @@ extern "C" {
 
 const char* bem_last_error(void) { return g_err.c_str(); }
 
-const char* bem_version(void) { return "bem-cubature-gb300 0.1 (sm_103a)"; }
+const char* bem_version(void) {
+    return BEM_CHECKED ? "bem-cubature-gb300 0.1 (sm_103a, checked)" : "bem-cubature-gb300 0.1 (sm_103a)";
+}
 
 int64_t bem_num_elements(const bem_mesh* m) { return m ? m->d.n : 0; }
 
@@ -769,9 +781,11 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
         a.n_pts = (int)n;
         a.sigma = m->d.sigma;
         a.slope = eval_slope(m, m->d.sigma);
-        far_args_from_work(a, w);
+        far_args_from_work(a, w, m->n_chunks);
         a.part_g = part_g.p;
         a.far_g = far_g.p;
+        a.part_cap = std::min<unsigned long long>(a.part_cap, np);
+        a.pts_cap = std::min<unsigned long long>(a.pts_cap, (unsigned long long)n);
         a.work = reinterpret_cast<int*>(w.counters + 14);
         a.near_rec = w.near_rec;
         a.counters = w.counters;
@@ -794,7 +808,10 @@ int grad_slice(bem_mesh* m, const double* points, int64_t n, double* G, cudaStre
             return rc;
         if ((rc = launch_finalize_grad(m, w.perm, (int)n, far_g.p, gval.p, n_near, dG, s))) return rc;
         if (!g_dev) BEM_CUDA_TRY(cudaMemcpyAsync(G, dG, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, s));
+        unsigned long long flags = 0;
+        BEM_CUDA_TRY(cudaMemcpyAsync(&flags, w.counters + kCheckCounter, sizeof flags, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((rc = check_flags(flags, "bem_eval_grad"))) return rc;
         m->last_stats[12] = (int64_t)n_near;
         return BEM_OK;
     }
@@ -917,6 +934,7 @@ int bem_assemble(bem_mesh* m, const double* colloc, int64_t mrows, double* A, vo
             rc = cuda_fail(e, "bem_assemble");
             break;
         }
+        if ((rc = check_flags(cnt[kCheckCounter], "bem_assemble"))) break;
         const unsigned long long pairs = cnt[kPairCounter];  // at least the run records
         if (pairs <= w.cap_near) {
             m->last_stats[12] = (int64_t)pairs;

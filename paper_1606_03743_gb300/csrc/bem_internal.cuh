@@ -109,6 +109,29 @@ struct Work {
 enum Precision { kFP64 = 0, kMixed = 1 };
 constexpr int kPairCounter = 19;  // counters[kPairCounter]: near pairs of a call
 
+// Checked build (-DBEM_CHECKED=1): the kernels compare the global indices they
+// compute with the capacities of the buffers they index, skip an access that
+// would fall outside, and record which check failed in counters[kCheckCounter]
+// (a bit per kind); the host turns a non-zero value into BEM_ERR_CUDA.  There
+// are no device asserts or traps: a failed check leaves the context usable.
+#ifndef BEM_CHECKED
+#define BEM_CHECKED 0
+#endif
+constexpr int kCheckCounter = 21;
+enum CheckBit : unsigned long long {
+    kCheckPart = 1,       // a work item's slot of the tile-major partial areas
+    kCheckPoint = 2,      // a per-point array (far sums, near totals, rows)
+    kCheckRow = 4,        // a row of the near-pair prefix table
+    kCheckElement = 8,    // an element index of a near-pair run
+    kCheckMatrix = 16,    // an entry of the assembled matrix
+};
+__device__ __forceinline__ bool check_ok(bool ok, unsigned long long* counters, unsigned long long bit) {
+    if (BEM_CHECKED && !ok) atomicOr(counters + kCheckCounter, bit);
+    return !BEM_CHECKED || ok;
+}
+// Host side of the checked build: BEM_ERR_CUDA with a message if a kernel recorded a failed check.
+int check_flags(unsigned long long flags, const char* fn);
+
 }  // namespace bem
 
 struct bem_mesh {
@@ -207,6 +230,8 @@ struct FarArgs {
     int* near_row;       // out: row of near_rows per sorted point with near pairs
     int* near_rows;      // out: per row, the point's near pairs in the chunks before each chunk
     int* tile_done;      // finished items per tile (zeroed by launch_far), then the row counter
+    unsigned long long part_cap;  // entries of part / near_cnt (part_g: of its double4 pairs)
+    unsigned long long pts_cap;   // entries of far (far_g: pairs) / near_tot / near_row / near_rows rows
     int* work;           // work-item counter, zero at launch
     int4* near_rec;      // out: near pair list
     unsigned long long* counters;
@@ -219,7 +244,7 @@ struct FarArgs {
     const int* n_dev;    // if set: the point count is read on the device (n_pts is the capacity)
 };
 // The per-call buffers of the far pass (everything but part_g / far_g) from a workspace.
-inline void far_args_from_work(FarArgs& a, Work& w) {
+inline void far_args_from_work(FarArgs& a, Work& w, int n_chunks) {
     a.part = w.part;
     a.near_cnt = w.near_cnt;
     a.far = w.far;
@@ -227,6 +252,8 @@ inline void far_args_from_work(FarArgs& a, Work& w) {
     a.near_row = w.near_row;
     a.near_rows = w.near_rows;
     a.tile_done = w.tile_done;
+    a.part_cap = (unsigned long long)w.cap_pts * (unsigned long long)n_chunks;
+    a.pts_cap = w.cap_pts;
 }
 // Ints of Work::tile_done for cap points: one per tile of at least 32 points, plus the row counter.
 constexpr size_t tile_done_ints(size_t cap) { return cap / 32 + 2; }

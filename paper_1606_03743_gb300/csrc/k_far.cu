@@ -152,6 +152,7 @@ struct FarK {
     int* near_row;        // per sorted point with near pairs: its row of near_rows
     int* near_rows;       // [row][chunk]: near pairs of the point in the chunks before
     int* tile_done;       // [tile] finished work items; [n_tiles] the near_rows row counter
+    unsigned long long part_cap, pts_cap;  // capacities (checked build): see FarArgs
     int4* near_rec;
     unsigned long long* counters;
     unsigned long long near_cap;
@@ -577,10 +578,11 @@ __device__ __forceinline__ void finish_tile(const FarK& p, const double4* part, 
     __threadfence();
     const int nc = p.n_chunks, tp = p.tile_pts;
     const size_t tbase = (size_t)tile * nc * tp;
+    const bool slots_ok = check_ok(tbase + (size_t)nc * tp <= p.part_cap, p.counters, kCheckPart);
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
         const int sp = base + q * 32 + lane;
-        if (sp >= n_pts) continue;
+        if (sp >= n_pts || !slots_ok || !check_ok((unsigned long long)sp < p.pts_cap, p.counters, kCheckPoint)) continue;
         double s[4 * NPART];
 #pragma unroll
         for (int k = 0; k < 4 * NPART; ++k) s[k] = 0.0;
@@ -603,6 +605,7 @@ __device__ __forceinline__ void finish_tile(const FarK& p, const double4* part, 
         p.near_tot[sp] = tot;
         if (tot > 0) {
             const int r = atomicAdd(p.tile_done + n_tiles, 1);
+            if (!check_ok((unsigned long long)r < p.pts_cap, p.counters, kCheckRow)) continue;
             p.near_row[sp] = r;
             int run = 0;
             for (int c = 0; c < nc; ++c) {
@@ -611,6 +614,7 @@ __device__ __forceinline__ void finish_tile(const FarK& p, const double4* part, 
             }
         }
     }
+    if (!slots_ok) return;
     const char* pa = reinterpret_cast<const char*>(part + NPART * tbase);
     const size_t pbytes = sizeof(double4) * NPART * (size_t)nc * tp;
     for (size_t off = (size_t)lane * 128; off < pbytes; off += 32 * 128) discard_l2(pa + off);
@@ -980,7 +984,11 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         // assembly: one potential per pair, times 1/(4 pi eps0); near pairs are filled later
 #pragma unroll
                         for (int q = 0; q < PT; ++q)
-                            if (valid(q)) p.A[(size_t)p.perm[sidx(q)] * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
+                            if (valid(q)) {
+                                const int row = p.perm[sidx(q)];
+                                if (check_ok(row >= 0 && row < p.n_pts && b0 + e < p.n_el, p.counters, kCheckMatrix))
+                                    p.A[(size_t)row * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
+                            }
                     }
                 } else {
                     // ---------------- mixed path (frame form, point pairs)
@@ -1261,7 +1269,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             for (int j = 0; j < PT * 32 / 8; ++j) {
                                 const int ps = j * 8 + (lane >> 2);
                                 const int row = ws.rows[ps];
-                                if (row >= 0 && sub < gn)
+                                if (row >= 0 && sub < gn &&
+                                    check_ok(row < p.n_pts && col0 + sub < p.n_el, p.counters, kCheckMatrix))
                                     p.A[(size_t)row * p.n_el + (col0 + sub)] = ws.at[sub * (PT * 32) + ps];
                             }
                             __syncwarp();
@@ -1282,6 +1291,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
             for (int q = 0; q < PT; ++q) {
                 if (!valid(q)) continue;
                 const size_t slot = ibase + q * 32 + lane;
+                if (!check_ok(slot < p.part_cap, p.counters, kCheckPart)) continue;
                 if constexpr (MODE == 0) {
                     double4 o;
                     if constexpr (F64) {
@@ -1481,6 +1491,8 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
     k.near_row = a.near_row;
     k.near_rows = a.near_rows;
     k.tile_done = a.tile_done;
+    k.part_cap = a.part_cap;
+    k.pts_cap = a.pts_cap;
     k.near_rec = a.near_rec;
     k.counters = a.counters;
     k.near_cap = a.near_cap;

@@ -14,6 +14,9 @@
 // angle of the polygon seen from P with the sign of h (Van Oosterom and
 // Strackee's formula on each triangle).  The edge logarithm is evaluated in
 // whichever of its three equivalent forms has no cancellation.
+#include <algorithm>
+#include <climits>
+
 #include "bem_internal.cuh"
 
 namespace bem {
@@ -161,6 +164,13 @@ __device__ __forceinline__ unsigned long long near_slot(const int4 r, const int*
            (unsigned long long)r.z;
 }
 
+// What the checked build checks near-pair runs against: the point capacity,
+// the element count, and the counters that take the flag.
+struct NearBounds {
+    int n_pts, n_el;
+    unsigned long long* counters;
+};
+
 // The near-pair passes run with blocks of kNearThreads threads.
 constexpr int kNearThreads = 128;
 constexpr int kNearWarps = kNearThreads / 32;
@@ -171,10 +181,13 @@ constexpr int kNearWarps = kNearThreads / 32;
 // the warp's other lanes idle.  P is the run's field point; slot its pair's
 // slot among the near values (slot_of(run) + k), or the run's index when
 // slot_of is null (assembly writes no values).
+//
+// A run whose point or elements fall outside [0, n_pts) x [0, n_el) is a
+// corrupt record: the checked build skips it and flags kCheckElement.
 template <typename SlotOf, typename F>
 __device__ __forceinline__ void for_each_near_pair(const int4* __restrict__ rec, unsigned long long n_runs,
                                                    const double* __restrict__ pts, const int* __restrict__ perm,
-                                                   SlotOf slot_of, F f) {
+                                                   const NearBounds nb, SlotOf slot_of, F f) {
     __shared__ int4 s_rec[kNearWarps][32];
     __shared__ int s_first[kNearWarps][32];
     __shared__ unsigned long long s_slot[kNearWarps][32];
@@ -183,7 +196,10 @@ __device__ __forceinline__ void for_each_near_pair(const int4* __restrict__ rec,
     const unsigned long long stride = (unsigned long long)gridDim.x * kNearWarps * 32;
     for (unsigned long long b = ((unsigned long long)blockIdx.x * kNearWarps + warp) * 32; b < n_runs; b += stride) {
         const unsigned long long i = b + lane;
-        const int4 r = i < n_runs ? rec[i] : make_int4(0, 0, 0, 0);
+        int4 r = i < n_runs ? rec[i] : make_int4(0, 0, 0, 0);
+        if (!check_ok(r.w == 0 || (r.x >= 0 && r.x < nb.n_pts && r.y >= 0 && r.w > 0 && r.y + r.w <= nb.n_el),
+                      nb.counters, kCheckElement))
+            r.w = 0;
         int incl = r.w;  // inclusive prefix sum of the run lengths over the lanes
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -519,7 +535,7 @@ __device__ void polygon_grad_var(int nv, const double* __restrict__ V, D3 P, con
 // Gradient of each near-pair run's pairs, times sigma, at the pairs' slots (two double4
 // each); linear / quadratic densities (slope set) by polygon_grad_var.
 __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
-                            unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
+                            const NearBounds nb, unsigned long long gcap, const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, const int* __restrict__ near_row,
                             const int* __restrict__ near_rows, int n_chunks, int chunk_len,
                             const int* __restrict__ type, const double* __restrict__ verts,
@@ -528,7 +544,7 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
                             const double* __restrict__ cen, double4* __restrict__ gval) {
     const unsigned long long n = min(counters[0], cap);
     auto slot_of = [&](const int4 r) { return near_slot(r, near_off, near_row, near_rows, n_chunks, chunk_len); };
-    for_each_near_pair(rec, n, pts, perm, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
+    for_each_near_pair(rec, n, pts, perm, nb, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
         if (slot >= gcap) return;
         const int el = r.y + k;
         const int nv = type[el] == BEM_RECTANGLE ? 4 : 3;
@@ -550,7 +566,7 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
 // phi and E of each near-pair run's pairs, times sigma, at the pairs' slots;
 // linear / quadratic densities (slope set) by the analytic integral of the density.
 __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long long* counters, unsigned long long cap,
-                            const double* __restrict__ pts, const int* __restrict__ perm,
+                            const NearBounds nb, const double* __restrict__ pts, const int* __restrict__ perm,
                             const int* __restrict__ near_off, const int* __restrict__ near_row,
                             const int* __restrict__ near_rows, int n_chunks, int chunk_len,
                             const int* __restrict__ type, const double* __restrict__ verts,
@@ -559,7 +575,7 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
                             const double* __restrict__ cen, double4* __restrict__ val) {
     const unsigned long long n = min(counters[0], cap);
     auto slot_of = [&](const int4 r) { return near_slot(r, near_off, near_row, near_rows, n_chunks, chunk_len); };
-    for_each_near_pair(rec, n, pts, perm, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
+    for_each_near_pair(rec, n, pts, perm, nb, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
         if (slot >= cap) return;
         const int el = r.y + k;
         double f[4];
@@ -616,12 +632,12 @@ __global__ void k_finalize(int n, const int* n_dev, const int* __restrict__ perm
 }
 
 __global__ void k_near_assemble(const int4* __restrict__ rec, const unsigned long long* counters,
-                                unsigned long long cap, const double* __restrict__ pts, const int* __restrict__ perm,
+                                unsigned long long cap, const NearBounds nb, const double* __restrict__ pts, const int* __restrict__ perm,
                                 const int* __restrict__ type, const double* __restrict__ verts, int n_el, double kc,
                                 double* __restrict__ A) {
     const unsigned long long n = min(counters[0], cap);
     auto no_slot = [](const int4) { return 0ull; };
-    for_each_near_pair(rec, n, pts, perm, no_slot, [&](const int4 r, int k, const D3 P, unsigned long long) {
+    for_each_near_pair(rec, n, pts, perm, nb, no_slot, [&](const int4 r, int k, const D3 P, unsigned long long) {
         const int el = r.y + k;
         double f[4];
         polygon_field(type[el] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)el, P, f);
@@ -652,11 +668,16 @@ int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s) {
     return BEM_OK;
 }
 
+static NearBounds near_bounds(bem_mesh* m) {
+    return NearBounds{(int)std::min<size_t>(m->w.cap_pts, INT_MAX), m->d.n, m->w.counters};
+}
+
 int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts, const double* sigma,
                      unsigned long long /*n_near_hint*/, cudaStream_t s, const double* slope) {
     (void)n_pts;
     Work& w = m->w;
-    k_near_eval<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm, w.near_off,
+    k_near_eval<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near,
+                                        near_bounds(m), pts, perm, w.near_off,
                                         w.near_row, w.near_rows, m->n_chunks, m->chunk_len, m->d.type, m->d.verts,
                                         sigma, slope, eval_curv(m, slope),
                                         m->d.fr, m->d.cen, w.near_val);
@@ -678,7 +699,8 @@ int launch_finalize(bem_mesh* m, const int* perm, int n_pts, double* phi, double
 int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const double* sigma, double4* gval,
                      unsigned long long gcap, cudaStream_t s, const double* slope) {
     Work& w = m->w;
-    k_near_grad<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, gcap, pts, perm,
+    k_near_grad<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near,
+                                        near_bounds(m), gcap, pts, perm,
                                         w.near_off, w.near_row, w.near_rows, m->n_chunks, m->chunk_len, m->d.type,
                                         m->d.verts, sigma, slope,
                                         eval_curv(m, slope), m->d.fr, m->d.cen, gval);
@@ -700,7 +722,8 @@ int launch_finalize_grad(bem_mesh* m, const int* perm, int n_pts, const double4*
 int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double* A, unsigned long long,
                          cudaStream_t s) {
     Work& w = m->w;
-    k_near_assemble<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near, pts, perm,
+    k_near_assemble<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near,
+                                            near_bounds(m), pts, perm,
                                             m->d.type, m->d.verts, m->d.n, m->kc, A);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);

@@ -162,7 +162,7 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     a.n_pts = (int)n;
     a.sigma = m->d.sigma;
     a.slope = eval_slope(m, m->d.sigma);
-    far_args_from_work(a, w);
+    far_args_from_work(a, w, m->n_chunks);
     a.work = reinterpret_cast<int*>(w.counters + 14);
     a.near_rec = w.near_rec;
     a.counters = w.counters;
@@ -175,9 +175,13 @@ extern "C" int bem_eval_noalloc(bem_mesh* m, const double* points, int64_t n, do
     if ((rc = launch_exclusive_scan(w.near_tot, w.near_off, (int)n, w.scan_tmp, s))) return rc;
     if ((rc = launch_near_eval(&view, points, w.perm, (int)n, m->d.sigma, 0, s, eval_slope(m, m->d.sigma)))) return rc;
     if ((rc = launch_finalize(&view, w.perm, (int)n, phi, E, 0, s))) return rc;
-    unsigned long long n_near = 0;  // near pairs (values; the run records are fewer)
-    BEM_CUDA_TRY(cudaMemcpyAsync(&n_near, w.counters + kPairCounter, sizeof n_near, cudaMemcpyDeviceToHost, s));
+    // the pair counter and, two further on, the checked build's flags
+    static_assert(kCheckCounter == kPairCounter + 2, "counter layout");
+    unsigned long long c[3] = {0, 0, 0};
+    BEM_CUDA_TRY(cudaMemcpyAsync(c, w.counters + kPairCounter, sizeof c, cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((rc = check_flags(c[2], "bem_eval_noalloc"))) return rc;
+    const unsigned long long n_near = c[0];  // near pairs (values; the run records are fewer)
     if (n_near > kMaxNear) {
         set_error("bem_eval_noalloc: %llu near-field pairs; one call takes at most %d (BEM_NOALLOC_MAX_NEAR); "
                   "phi and E are incomplete -- split the points or use bem_eval",

@@ -145,7 +145,7 @@ int enqueue_pipeline(bem_server* sv, Slot& sl) {
     a.n_dev = sl.d_n;
     a.sigma = m->d.sigma;
     a.slope = eval_slope(m, m->d.sigma);
-    far_args_from_work(a, w);
+    far_args_from_work(a, w, m->n_chunks);
     a.work = reinterpret_cast<int*>(w.counters + 14);
     a.near_rec = w.near_rec;
     a.counters = w.counters;
@@ -190,7 +190,7 @@ int slot_setup(bem_server* sv, Slot& sl) {
     BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_phi, sizeof(double) * cap));
     BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_E, sizeof(double) * 3 * cap));
     BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_n, sizeof(int)));
-    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_near, sizeof(unsigned long long)));
+    BEM_CUDA_TRY(pinned_malloc((void**)&sl.h_near, 3 * sizeof(unsigned long long)));
     BEM_CUDA_TRY(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
     BEM_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
 
@@ -310,7 +310,7 @@ bool fill_and_launch(bem_server* sv, Slot& sl, bool allow_large, std::unique_loc
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl.h_E, sl.d_E, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sl.h_near, sl.view.w.counters + kPairCounter, sizeof(unsigned long long),
+        e = cudaMemcpyAsync(sl.h_near, sl.view.w.counters + kPairCounter, 3 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
     lk.lock();
@@ -333,9 +333,12 @@ bool fill_and_launch(bem_server* sv, Slot& sl, bool allow_large, std::unique_loc
 
 // Hand a finished tick's results to its requests.  Called without the lock.
 void harvest(bem_server* sv, Slot& sl) {
-    const bool overflow = *sl.h_near > sl.view.w.cap_near;
-    std::vector<int> status(sl.pieces.size(), BEM_OK);
-    for (size_t i = 0; i < sl.pieces.size(); ++i) {
+    // h_near: the pair counter and, two further on, the checked build's flags
+    static_assert(kCheckCounter == kPairCounter + 2, "counter layout");
+    const bool overflow = sl.h_near[0] > sl.view.w.cap_near;
+    const int checked = check_flags(sl.h_near[2], "bem_server tick");
+    std::vector<int> status(sl.pieces.size(), checked);
+    for (size_t i = 0; i < sl.pieces.size() && checked == BEM_OK; ++i) {
         const Piece& pc = sl.pieces[i];
         Req* r = pc.r;  // its result arrays were sized at submission; pieces write disjoint ranges
         if (!overflow) {
@@ -434,15 +437,24 @@ int bem_server_create(bem_mesh* mesh, const bem_server_options* opt, bem_server*
     sv->mesh = mesh;
     int64_t cap = opt && opt->max_points_per_tick > 0 ? opt->max_points_per_tick : 131072;
     sv->near_cap = opt && opt->max_near_pairs_per_tick > 0 ? (size_t)opt->max_near_pairs_per_tick : (size_t(1) << 21);
-    const size_t budget = opt && opt->device_mem_budget ? opt->device_mem_budget : (size_t(2) << 30);
-    // admission by device memory: shrink the per-tick capacity until both slots fit the budget
+    size_t budget = opt && opt->device_mem_budget ? opt->device_mem_budget : (size_t(2) << 30);
+    // admission by device memory: the budget, but no more than 3/4 of what the device has free now
+    // (the slots' buffers are all allocated here; ticks allocate nothing)
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaSetDevice(mesh->device) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            budget = std::min(budget, free_b / 4 * 3);
+        cudaGetLastError();
+    }
+    // shrink the per-tick capacity until both slots fit
     auto need = [&](int64_t c) {
         const size_t ns = (size_t)c * mesh->n_chunks;
         return 2 * (sizeof(double) * 11 * c + sizeof(int) * 5 * c + 40 * ns + 48 * sv->near_cap + (size_t(17) << 20));
     };
     while (cap > 1024 && need(cap) > budget) cap /= 2;
     if (cap < 1 || cap > (int64_t(1) << 24) || need(cap) > budget) {
-        set_error("bem_server_create: device_mem_budget too small for one tick");
+        set_error("bem_server_create: device_mem_budget (or 3/4 of the free device memory, %zu bytes) too small "
+                  "for one tick", budget);
         delete sv;
         return BEM_ERR_OOM;
     }
