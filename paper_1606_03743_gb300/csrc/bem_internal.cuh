@@ -32,14 +32,12 @@ __host__ __device__ inline int band_rule(int band) { return 5 - band; }
 // Structure of arrays, one entry per element, element order as given.
 constexpr int kTableSlots = 75;  // nodes per element in the node table (4 + 7 + 12 + 19 + 33)
 // float4 records per node of the mixed path: (-alpha, -alpha, -beta, -beta),
-// (|o|^2, |o|^2, w, w) and, with BEM_NODE3, (-w alpha, -w alpha, -w beta, -w beta):
+// (|o|^2, |o|^2, w, w) and (-w alpha / 2, -w alpha / 2, -w beta / 2, -w beta / 2):
 // the third record lets each node's four sums take one FMA each (9 packed
-// operations per node and point pair instead of 10; 1.4 % faster on the
-// 150 000-element x 1 000 000-point workload)
-#ifndef BEM_NODE3
-#define BEM_NODE3 1
-#endif
-constexpr int kNodeRecs = BEM_NODE3 ? 3 : 2;
+// operations per node and point pair instead of 10); it is halved because the
+// kernel's frame records hold 2 e0 and 2 e1 (so that 2 d.e0 and 2 d.e1 need no
+// doubling) and the field rebuild multiplies these sums by them
+constexpr int kNodeRecs = 3;
 
 // Element chunks of the far-field pass (fixed per mesh, so that a point's
 // sum is always split the same way): at least kChunkMinElements elements

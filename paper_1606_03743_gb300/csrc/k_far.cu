@@ -374,9 +374,9 @@ __device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
 
 // One node of an element at the NP point pairs of a lane, in the frame form:
 // ab = (-alpha, -alpha, -beta, -beta), ow = (|o|^2, |o|^2, w q, w q),
-// wab = (-w q alpha, -w q alpha, -w q beta, -w q beta) (read with BEM_NODE3);
+// wab = (-w q alpha, -w q alpha, -w q beta, -w q beta) / 2;
 // s, u, v = |d|^2, 2 d.e0, 2 d.e1 per point (r^2 = s + |o|^2 - alpha u -
-// beta v).  acc[k] = (sum a, sum b, -sum b alpha, -sum b beta) with
+// beta v).  acc[k] = (sum a, sum b, -sum b alpha / 2, -sum b beta / 2) with
 // a = w q / r, b = a / r^2 (phi only: sum a).  A point that must not take
 // part carries s = +inf: then r^2 = +inf,
 // rsqrt gives +0 and its terms are exact zeros, while the other points'
@@ -416,37 +416,19 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
             }
             continue;
         }
-        if constexpr (BEM_NODE3) {
-            // third record: (-w alpha, -w beta): every sum is one FMA of its weight and 1/r or 1/r^3
-            if (INIT) acc[k][0] = mul2(w, inv);
-            else acc[k][0] = fma2(w, inv, acc[k][0]);
-            if (WANT_E) {
-                const float2 i3 = mul2(inv, mul2(inv, inv));  // 1 / r_i^3
-                const float2 wa = make_float2(wab.x, wab.y), wb = make_float2(wab.z, wab.w);
-                if (INIT) {
-                    acc[k][1] = mul2(w, i3); acc[k][2] = mul2(wa, i3); acc[k][3] = mul2(wb, i3);
-                } else {
-                    acc[k][1] = fma2(w, i3, acc[k][1]);
-                    acc[k][2] = fma2(wa, i3, acc[k][2]);
-                    acc[k][3] = fma2(wb, i3, acc[k][3]);
-                }
-            }
-            continue;
-        }
-        const float2 a = mul2(w, inv);  // q_i / r_i
-        if (INIT) {
-            acc[k][0] = a;
-        } else {
-            acc[k][0] = add2(acc[k][0], a);
-        }
+        // the third record, (-w alpha / 2, -w beta / 2): every sum is one FMA of its weight and
+        // 1/r or 1/r^3
+        if (INIT) acc[k][0] = mul2(w, inv);
+        else acc[k][0] = fma2(w, inv, acc[k][0]);
         if (WANT_E) {
-            const float2 b = mul2(a, mul2(inv, inv));  // q_i / r_i^3
+            const float2 i3 = mul2(inv, mul2(inv, inv));  // 1 / r_i^3
+            const float2 wa = make_float2(wab.x, wab.y), wb = make_float2(wab.z, wab.w);
             if (INIT) {
-                acc[k][1] = b; acc[k][2] = mul2(b, al); acc[k][3] = mul2(b, be);
+                acc[k][1] = mul2(w, i3); acc[k][2] = mul2(wa, i3); acc[k][3] = mul2(wb, i3);
             } else {
-                acc[k][1] = add2(acc[k][1], b);
-                acc[k][2] = fma2(b, al, acc[k][2]);
-                acc[k][3] = fma2(b, be, acc[k][3]);
+                acc[k][1] = fma2(w, i3, acc[k][1]);
+                acc[k][2] = fma2(wa, i3, acc[k][2]);
+                acc[k][3] = fma2(wb, i3, acc[k][3]);
             }
         }
     }
@@ -518,7 +500,8 @@ struct WarpSmem {
     R sl[2 * 32];            // linear densities: area x (d sigma / d alpha, d sigma / d beta), else 0
     // mixed: per element, the values each node pass and the field rebuild
     // read, duplicated into (x, x, y, y) pairs for the packed f32x2 arithmetic:
-    // -C_hi, -C_lo, e0, e1 (six float4)
+    // -C_hi, -C_lo, 2 e0, 2 e1 (six float4; the doubling is exact and makes the
+    // projections 2 d.e0, 2 d.e1 of the node loop one FMA chain each)
     float4 pr[kMixed ? 32 * 6 : 1];
 
     R4 nd[2][kMixed ? kNodeRecs * kNodeBuf : kNodeBuf];  // node records (FP64: one per node; mixed: kNodeRecs)
@@ -846,9 +829,9 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         pr[0] = make_float4(-c.x, -c.x, -c.y, -c.y);
                         pr[1] = make_float4(-c.z, -c.z, -cl.x, -cl.x);
                         pr[2] = make_float4(-cl.y, -cl.y, -cl.z, -cl.z);
-                        pr[3] = make_float4(a.x, a.x, a.y, a.y);
-                        pr[4] = make_float4(a.z, a.z, b.x, b.x);
-                        pr[5] = make_float4(b.y, b.y, b.z, b.z);
+                        pr[3] = make_float4(2.0f * a.x, 2.0f * a.x, 2.0f * a.y, 2.0f * a.y);
+                        pr[4] = make_float4(2.0f * a.z, 2.0f * a.z, 2.0f * b.x, 2.0f * b.x);
+                        pr[5] = make_float4(2.0f * b.y, 2.0f * b.y, 2.0f * b.z, 2.0f * b.z);
                         const float L = cl.w;
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
@@ -1004,27 +987,30 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     };
                     // s = |d|^2, u = d.e0, v = d.e1 of every pair
                     float2 sv[NP], uv[NP], vv[NP];
+                    float2 dxk[NP], dyk[NP], dzk[NP];  // d, held for the field rebuild
                     {
                         const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             float2 dx, dy, dz;
                             diff(k, dx, dy, dz);
+                            dxk[k] = dx; dyk[k] = dy; dzk[k] = dz;
                             sv[k] = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
                             const float2 u = fma2(dx, lo2(r3), fma2(dy, hi2(r3), mul2(dz, lo2(r4))));
                             const float2 v = fma2(dx, hi2(r4), fma2(dy, lo2(r5), mul2(dz, hi2(r5))));
-                            uv[k] = add2(u, u);  // 2 d.e0, 2 d.e1 (exact doublings)
-                            vv[k] = add2(v, v);
+                            uv[k] = u;  // 2 d.e0, 2 d.e1 (the frame records hold 2 e0, 2 e1)
+                            vv[k] = v;
                         }
                     }
                     float2 eacc[NP][NE];  // this element's sums (started by its first rule pass)
                     // expand rule r of element e into the free node buffer (lane i: node i)
                     auto expand = [&](int r) -> int {
                         const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
-                        // the frame from the duplicated records: (e0x, e0x, e0y, e0y), (e0z, e0z, e1x, e1x),
-                        // (e1y, e1y, e1z, e1z); the charge from qt
+                        // the frame from the duplicated, doubled records: 2 (e0x, e0x, e0y, e0y),
+                        // 2 (e0z, e0z, e1x, e1x), 2 (e1y, e1y, e1z, e1z); the charge from qt
                         const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
-                        const float4 f0 = make_float4(r3.x, r3.z, r4.x, ws.qt[e].x), f1 = make_float4(r4.z, r5.x, r5.z, 0.0f);
+                        const float4 f0 = make_float4(0.5f * r3.x, 0.5f * r3.z, 0.5f * r4.x, ws.qt[e].x),
+                                     f1 = make_float4(0.5f * r4.z, 0.5f * r5.x, 0.5f * r5.z, 0.0f);
                         float ca = 0.0f, cb = 0.0f, cc = 0.0f;
                         if (VARY && p.curv) {  // quadratic densities: area x second-order coefficients
                             const size_t j = (size_t)(b0 + e);
@@ -1047,10 +1033,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             const float am = -al, bm = -be, wq = rs.w[st + i] * qi;
                             ws.nd[par][kNodeRecs * i] = make_float4(am, am, bm, bm);
                             ws.nd[par][kNodeRecs * i + 1] = make_float4(oo, oo, wq, wq);
-                            if constexpr (BEM_NODE3) {
-                                const float wa = wq * am, wb = wq * bm;
-                                ws.nd[par][kNodeRecs * i + 2] = make_float4(wa, wa, wb, wb);
-                            }
+                            const float wa = 0.5f * (wq * am), wb = 0.5f * (wq * bm);  // times the doubled frame
+                            ws.nd[par][kNodeRecs * i + 2] = make_float4(wa, wa, wb, wb);
                         }
                         __syncwarp();
                         return n;
@@ -1169,7 +1153,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             for (int j = 0; j < (WANT_E ? 4 : 1); ++j) eacc[k][j] = mul2(eacc[k][j], q2);
                     }
                     if constexpr (MODE == 0) {
-                        // the element's phi and E = d B - e0 sum b alpha - e1 sum b beta
+                        // the element's phi and E = d B - e0 sum b alpha - e1 sum b beta (the
+                        // records hold 2 e0, 2 e1 and the sums half of sum b alpha, sum b beta)
                         // into the FP32 sums; every kFlush elements move those into the hi + lo sums
                         const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
                         const float2 h0x = lo2(r3), h0y = hi2(r3), h0z = lo2(r4);
@@ -1178,8 +1163,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int k = 0; k < NP; ++k) {
                             acc8[k][0] = add2(acc8[k][0], eacc[k][0]);
                             if (WANT_E) {
-                                float2 dx, dy, dz;  // formed again rather than held through the node loop
-                                diff(k, dx, dy, dz);
+                                const float2 dx = dxk[k], dy = dyk[k], dz = dzk[k];
                                 acc8[k][1] = fma2(dx, eacc[k][1], fma2(h0x, eacc[k][2], fma2(h1x, eacc[k][3], acc8[k][1])));
                                 acc8[k][2] = fma2(dy, eacc[k][1], fma2(h0y, eacc[k][2], fma2(h1y, eacc[k][3], acc8[k][2])));
                                 acc8[k][3] = fma2(dz, eacc[k][1], fma2(h0z, eacc[k][2], fma2(h1z, eacc[k][3], acc8[k][3])));
@@ -1205,8 +1189,9 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         // N1 = Cb d + Cab e0 + Cbb e1 (C the sums of node2, Ca = -sum c alpha, ...)
                         // it is B I - 3 (M d^T + N0 e0^T + N1 e1^T)
                         const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
-                        const float2 h0x = lo2(r3), h0y = hi2(r3), h0z = lo2(r4);
-                        const float2 h1x = hi2(r4), h1y = lo2(r5), h1z = hi2(r5);
+                        const float2 hf = make_float2(0.5f, 0.5f);  // the records hold 2 e0, 2 e1
+                        const float2 h0x = mul2(hf, lo2(r3)), h0y = mul2(hf, hi2(r3)), h0z = mul2(hf, lo2(r4));
+                        const float2 h1x = mul2(hf, hi2(r4)), h1y = mul2(hf, lo2(r5)), h1z = mul2(hf, hi2(r5));
                         const float2 m3 = make_float2(-3.0f, -3.0f);
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
@@ -1449,7 +1434,8 @@ __global__ void k_fill_nodes(int n, const float4* __restrict__ e0f, const float4
     const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
     out[kNodeRecs * id] = make_float4(-al, -al, -be, -be);
     out[kNodeRecs * id + 1] = make_float4(oo, oo, w, w);
-    if constexpr (BEM_NODE3) out[kNodeRecs * id + 2] = make_float4(-w * al, -w * al, -w * be, -w * be);
+    const float wa = 0.5f * (w * -al), wb = 0.5f * (w * -be);  // halved: times the doubled frame
+    out[kNodeRecs * id + 2] = make_float4(wa, wa, wb, wb);
 }
 }  // namespace
 
