@@ -44,7 +44,12 @@
 //    With the node's weight also stored premultiplied by alpha_i and beta_i,
 //    every sum takes one FMA: 9 FP32 operations and one rsqrt per node and
 //    point instead of 13; two points of a lane go through packed f32x2
-//    instructions together.
+//    instructions together.  The rectangle rules (App. B) are centrally
+//    symmetric: their nodes o and -o (equal weights) share s + |o|^2 and the
+//    projection, r_+-^2 = s + |o|^2 -+ (alpha u + beta v), and their two
+//    alpha, beta moments combine into one, w alpha (1/r_+^3 - 1/r_-^3): 16
+//    operations for the two nodes.  A rule's centre node (alpha = beta = 0,
+//    several rules of both types) needs r^2 = s only: 4 operations.
 //    At DR >= 3 the terms of r_i^2 cancel by at most a factor of about 4, so
 //    the split costs about two bits of an FP32 result.  rsqrt and the sums
 //    are FP32: each element's node terms (at most 33) are summed on their
@@ -87,28 +92,15 @@ constexpr int kPtAsm = BEM_ASM_PT, kPtPhi = BEM_PHI_PT;
 #define BEM_NODE_UNROLL 4
 #endif
 constexpr int kNodeUnroll = BEM_NODE_UNROLL;
-// rules with at most this many nodes get fully unrolled node loops
-// 1: a one-band element's first node starts its sums (its own compiled node
-// loops); 0: the sums are zeroed and every pass shares one set of loops
-#ifndef BEM_INIT_PASS
-#define BEM_INIT_PASS 1
-#endif
-#ifndef BEM_FULL_UNROLL_MAX
-#define BEM_FULL_UNROLL_MAX 12
-#endif
 // mixed path: elements per FP32 sum before it moves into the hi + lo running sums (a power of two)
 #ifndef BEM_FLUSH
 #define BEM_FLUSH 8
 #endif
 constexpr int kFlush = BEM_FLUSH;
-// 1: the per-band (masked) passes of straddling elements run one generic node
-// loop (unrolled BEM_MASKED_UNROLL deep) instead of loops compiled per rule
-// size.  The kernel is large enough for its code size to cost instruction-
-// fetch stalls: the smaller kernel is 3.4 % faster on the 150 000-element x
-// 1 000 000-point workload, with bit-identical results.
-#ifndef BEM_MASKED_GENERIC
-#define BEM_MASKED_GENERIC 1
-#endif
+// the per-band (masked) passes of straddling elements run one generic node
+// loop per element type (unrolled BEM_MASKED_UNROLL deep) instead of loops
+// compiled per rule: the kernel is large enough for its code size to cost
+// instruction-fetch stalls
 #ifndef BEM_MASKED_UNROLL
 #define BEM_MASKED_UNROLL 2
 #endif
@@ -129,6 +121,10 @@ constexpr int kAsmGroup = 4;  // mixed assembly: elements per staged group (a 32
 __constant__ float c_alpha_f[2 * kSlots], c_beta_f[2 * kSlots], c_w_f[2 * kSlots];
 __constant__ double c_alpha_d[2 * kSlots], c_beta_d[2 * kSlots], c_w_d[2 * kSlots];
 __constant__ int c_rule_n[10], c_rule_start[10];
+// mixed path: the rules as node records (c_alpha_f, c_beta_f, c_w_f): per rule the centre node (if
+// any), then one record per pair (o, -o) on rectangles or per node on triangles; the first record
+// of each rule and its shape (centre records | other records << 1)
+__constant__ int c_rec_start[10], c_rule_shape[10];
 
 struct FarK {
     const double* pts;
@@ -358,16 +354,20 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// hi + lo += x exactly up to the rounding of lo (Knuth's two-sum on packed
-// pairs; fma(a, -1, b) is b - a rounded once).  It keeps the running sums
-// of the mixed path on the FP32 pipe: a warp-wide FP64 add occupies this
-// GPU's FP64 pipe for tens of cycles.
+// hi + lo += x exactly up to the rounding of lo: the two addends ordered by
+// magnitude (selects, off the FP32 pipe), then Dekker's fast two-sum, whose
+// error term is exact for ordered addends -- the same hi and lo as Knuth's
+// branch-free two-sum with two FP32 operations fewer (fma(a, -1, b) is b - a
+// rounded once).  It keeps the running sums of the mixed path on the FP32
+// pipe: a warp-wide FP64 add occupies this GPU's FP64 pipe for tens of cycles.
 __device__ __forceinline__ void two_sum_add(float2& hi, float2& lo, float2 x) {
     const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 sm = add2(hi, x);
-    const float2 bv = fma2(hi, m1, sm);  // sm - hi
-    const float2 av = fma2(bv, m1, sm);  // sm - bv
-    const float2 er = add2(fma2(av, m1, hi), fma2(bv, m1, x));
+    const bool ox = fabsf(hi.x) >= fabsf(x.x), oy = fabsf(hi.y) >= fabsf(x.y);
+    const float2 a = make_float2(ox ? hi.x : x.x, oy ? hi.y : x.y);  // the larger magnitude
+    const float2 b = make_float2(ox ? x.x : hi.x, oy ? x.y : hi.y);
+    const float2 sm = add2(a, b);
+    const float2 z = fma2(a, m1, sm);  // sm - a, exact since |a| >= |b|
+    const float2 er = fma2(z, m1, b);  // b - z: the exact rounding error of sm
     hi = sm;
     lo = add2(lo, er);
 }
@@ -434,54 +434,175 @@ __device__ __forceinline__ void node2(const float4 ab, const float4 ow, const fl
     }
 }
 
-// All N nodes of one rule (two records per node in nd, broadcast reads),
-// with the trip count known at compile time.
-template <int N, int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
-__device__ __forceinline__ void nodes2_n(const float4* __restrict__ nd, const float2 (&s)[NP],
-                                         const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
-    if (INIT) node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], nd[kNodeRecs - 1], s, u, v, acc);
-    if constexpr (N <= BEM_FULL_UNROLL_MAX) {
+// The centre node of a rule (alpha = beta = 0, so |o|^2 = 0 and r^2 = s):
+// the point charge w q at the centroid.  ow = (0, 0, w q, w q).
+template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
+__device__ __forceinline__ void node2_centre(const float4 ow, const float2 (&s)[NP], float2 (&acc)[NP][NS]) {
+    const float2 w = make_float2(ow.z, ow.w), z = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = INIT ? 1 : 0; i < N; ++i)
-            node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
-                                            u, v, acc);
-    } else {
-#pragma unroll kNodeUnroll
-        for (int i = INIT ? 1 : 0; i < N; ++i)
-            node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
-                                            u, v, acc);
+    for (int k = 0; k < NP; ++k) {
+        const float2 inv = make_float2(rsqrtf(s[k].x), rsqrtf(s[k].y));
+        if constexpr (GRAD) {
+            static_assert(NS == 7, "gradient sums");
+            const float2 i2 = mul2(inv, inv);
+            const float2 b = mul2(mul2(w, inv), i2);  // q / r^3
+            const float2 c = mul2(b, i2);             // q / r^5
+            if (INIT) {
+                acc[k][0] = b; acc[k][1] = c;
+#pragma unroll
+                for (int j = 2; j < 7; ++j) acc[k][j] = z;
+            } else {
+                acc[k][0] = add2(acc[k][0], b);
+                acc[k][1] = add2(acc[k][1], c);
+            }
+            continue;
+        }
+        if (INIT) acc[k][0] = mul2(w, inv);
+        else acc[k][0] = fma2(w, inv, acc[k][0]);
+        if (WANT_E) {
+            const float2 i3 = mul2(inv, mul2(inv, inv));
+            if (INIT) {
+                acc[k][1] = mul2(w, i3); acc[k][2] = z; acc[k][3] = z;
+            } else {
+                acc[k][1] = fma2(w, i3, acc[k][1]);
+            }
+        }
     }
 }
 
-// All n nodes of one rule: the node counts of the paper's rules (App. A, B)
-// get their own compiled loops.
-template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
-__device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int n, const float2 (&s)[NP],
-                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
-    if constexpr (!INIT && BEM_MASKED_GENERIC) {
-#pragma unroll kMaskedUnroll
-        for (int i = 0; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
-                                            u, v, acc);
-        return;
+// The gradient sums of one node with its own (-alpha, -beta) = (al, be), weight w and 1 / r.
+template <bool INIT>
+__device__ __forceinline__ void grad_terms(const float2 al, const float2 be, const float2 w, const float2 inv,
+                                           float2 (&acc)[7]) {
+    const float2 i2 = mul2(inv, inv);
+    const float2 b = mul2(mul2(w, inv), i2);  // q_i / r_i^3
+    const float2 c = mul2(b, i2);             // q_i / r_i^5
+    const float2 ca = mul2(c, al), cb = mul2(c, be);
+    if (INIT) {
+        acc[0] = b; acc[1] = c; acc[2] = ca; acc[3] = cb;
+        acc[4] = mul2(ca, al); acc[5] = mul2(ca, be); acc[6] = mul2(cb, be);
+    } else {
+        acc[0] = add2(acc[0], b);
+        acc[1] = add2(acc[1], c);
+        acc[2] = add2(acc[2], ca);
+        acc[3] = add2(acc[3], cb);
+        acc[4] = fma2(ca, al, acc[4]);
+        acc[5] = fma2(ca, be, acc[5]);
+        acc[6] = fma2(cb, be, acc[6]);
     }
+}
 
-    switch (n) {
-        case 4: nodes2_n<4, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
-        case 7: nodes2_n<7, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
-        case 12: nodes2_n<12, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
-        case 17: nodes2_n<17, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
-        case 19: nodes2_n<19, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
-        case 33: nodes2_n<33, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc); return;
-        default: break;
+// Two nodes at o and -o with the same weight (the rectangle rules of App. B
+// are centrally symmetric), records as node2() for the node at o.  They share
+// s + |o|^2 and the projection m = -(alpha u + beta v):
+//   r_+^2 = s + |o|^2 + m,  r_-^2 = s + |o|^2 - m,
+// and the two alpha, beta moments combine: w alpha (1/r_+^3 - 1/r_-^3).
+// 16 packed operations for the two nodes instead of 18.
+template <int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
+__device__ __forceinline__ void node2_pair(const float4 ab, const float4 ow, const float4 wab, const float2 (&s)[NP],
+                                           const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
+    const float2 al = make_float2(ab.x, ab.y), be = make_float2(ab.z, ab.w);
+    const float2 oo = make_float2(ow.x, ow.y), w = make_float2(ow.z, ow.w);
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const float2 t = add2(s[k], oo);
+        const float2 m = fma2(al, u[k], mul2(be, v[k]));
+        const float2 rp = add2(t, m), rm = fma2(m, m1, t);
+        const float2 ip = make_float2(rsqrtf(rp.x), rsqrtf(rp.y)), im = make_float2(rsqrtf(rm.x), rsqrtf(rm.y));
+        if constexpr (GRAD) {
+            static_assert(NS == 7, "gradient sums");
+            grad_terms<INIT>(al, be, w, ip, acc[k]);
+            grad_terms<false>(mul2(al, m1), mul2(be, m1), w, im, acc[k]);
+            continue;
+        }
+        if (INIT) acc[k][0] = mul2(w, ip);
+        else acc[k][0] = fma2(w, ip, acc[k][0]);
+        acc[k][0] = fma2(w, im, acc[k][0]);
+        if (WANT_E) {
+            const float2 i3p = mul2(ip, mul2(ip, ip)), i3m = mul2(im, mul2(im, im));
+            const float2 dd = fma2(i3m, m1, i3p);  // 1/r_+^3 - 1/r_-^3
+            const float2 wa = make_float2(wab.x, wab.y), wb = make_float2(wab.z, wab.w);
+            if (INIT) {
+                acc[k][1] = mul2(w, i3p); acc[k][2] = mul2(wa, dd); acc[k][3] = mul2(wb, dd);
+            } else {
+                acc[k][1] = fma2(w, i3p, acc[k][1]);
+                acc[k][2] = fma2(wa, dd, acc[k][2]);
+                acc[k][3] = fma2(wb, dd, acc[k][3]);
+            }
+            acc[k][1] = fma2(w, i3m, acc[k][1]);
+        }
     }
+}
+
+// Shape of a rule's node records: c centre records (0 or 1) | r other records << 1
+__host__ __device__ inline int shape_c(int sh) { return sh & 1; }
+__host__ __device__ inline int shape_r(int sh) { return sh >> 1; }
+
+// Record i of a node buffer (kNodeRecs float4 per record).
+#define BEM_REC(nd, i) (nd)[kNodeRecs * (i)], (nd)[kNodeRecs * (i) + 1], (nd)[kNodeRecs * (i) + kNodeRecs - 1]
+
+// One node record of a rule: a pair (o, -o) on rectangles, a single node on triangles.
+template <bool PAIR, int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
+__device__ __forceinline__ void node2_rec(const float4* __restrict__ nd, int i, const float2 (&s)[NP],
+                                          const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
+    if constexpr (PAIR) node2_pair<NP, WANT_E, GRAD, INIT>(BEM_REC(nd, i), s, u, v, acc);
+    else node2<NP, WANT_E, GRAD, INIT>(BEM_REC(nd, i), s, u, v, acc);
+}
+
+// All records of one rule with the shape known at compile time: C centre
+// records (0 or 1) first, then R other records (pairs if PAIR), fully unrolled.
+template <int C, int R, bool PAIR, int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
+__device__ __forceinline__ void nodes2_shape(const float4* __restrict__ nd, const float2 (&s)[NP],
+                                             const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
+    if constexpr (C) {
+        node2_centre<NP, WANT_E, GRAD, INIT>(nd[1], s, acc);
+    } else {
+        node2_rec<PAIR, NP, WANT_E, GRAD, INIT>(nd, 0, s, u, v, acc);
+    }
+#pragma unroll
+    for (int i = 1; i < C + R; ++i) node2_rec<PAIR, NP, WANT_E, GRAD, false>(nd, i, s, u, v, acc);
+}
+
+// The same with the shape read at run time (c centre records, r others).
+template <int UNROLL, bool PAIR, int NP, bool WANT_E, bool GRAD, bool INIT, int NS>
+__device__ __forceinline__ void nodes2_loop(const float4* __restrict__ nd, int c, int r, const float2 (&s)[NP],
+                                            const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
     int i = 0;
-    if (INIT) {  // every rule has at least four nodes
-        node2<NP, WANT_E, GRAD, true>(nd[0], nd[1], nd[kNodeRecs - 1], s, u, v, acc);
+    if (c) {
+        node2_centre<NP, WANT_E, GRAD, INIT>(nd[1], s, acc);
+        i = 1;
+    } else if (INIT) {  // every rule has at least two records
+        node2_rec<PAIR, NP, WANT_E, GRAD, true>(nd, 0, s, u, v, acc);
         i = 1;
     }
-#pragma unroll 1
-    for (; i < n; ++i) node2<NP, WANT_E, GRAD, false>(nd[kNodeRecs * i], nd[kNodeRecs * i + 1], nd[kNodeRecs * i + kNodeRecs - 1], s,
-                                            u, v, acc);
+#pragma unroll UNROLL
+    for (; i < c + r; ++i) node2_rec<PAIR, NP, WANT_E, GRAD, false>(nd, i, s, u, v, acc);
+}
+
+// All records of one rule of an element of type ty, shape = c | r << 1.  The
+// rules with 7 and 12 nodes, which carry most of the work, get their own
+// fully unrolled code; the per-band passes of straddling elements (INIT
+// false) share one loop per element type.  PAIRS false (varying densities,
+// whose paired nodes carry different charges): every record is one node.
+template <int NP, bool WANT_E, bool GRAD, bool INIT, bool PAIRS, int NS>
+__device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int ty, int shape, const float2 (&s)[NP],
+                                       const float2 (&u)[NP], const float2 (&v)[NP], float2 (&acc)[NP][NS]) {
+    const int c = shape_c(shape), r = shape_r(shape);
+    if (PAIRS && ty == BEM_RECTANGLE) {
+        if constexpr (INIT) {
+            if (shape == (1 | 3 << 1)) return nodes2_shape<1, 3, true, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc);
+            if (shape == (0 | 6 << 1)) return nodes2_shape<0, 6, true, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc);
+            return nodes2_loop<kNodeUnroll / 2, true, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
+        }
+        return nodes2_loop<1, true, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
+    }
+    if constexpr (INIT) {
+        if (shape == (1 | 6 << 1)) return nodes2_shape<1, 6, false, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc);
+        if (shape == (0 | 12 << 1)) return nodes2_shape<0, 12, false, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc);
+        return nodes2_loop<kNodeUnroll, false, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
+    }
+    return nodes2_loop<kMaskedUnroll, false, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
 }
 
 // Shared memory of one warp.
@@ -516,7 +637,7 @@ struct WarpSmem {
 template <typename R>
 struct RuleSmem {
     R al[2 * kSlots], be[2 * kSlots], w[2 * kSlots];
-    int n[10], start[10];
+    int n[10], start[10], shape[10];  // nodes, first slot (mixed: first record), shape (mixed)
     unsigned long long stat[15];  // 12 band counts, uniform / mixed (warp, element) pairs, node evaluations
 };
 
@@ -655,7 +776,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
     }
     if (tid < 10) {
         rs.n[tid] = c_rule_n[tid];
-        rs.start[tid] = c_rule_start[tid];
+        rs.start[tid] = F64 ? c_rule_start[tid] : c_rec_start[tid];
+        rs.shape[tid] = c_rule_shape[tid];
     }
     if (STATS && tid < 15) rs.stat[tid] = 0ull;
     // absolute margin of the warp band test: coordinates enter it rounded to
@@ -1003,14 +1125,20 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         }
                     }
                     float2 eacc[NP][NE];  // this element's sums (started by its first rule pass)
+                    // shape of rule r's records in the node buffer (varying densities: rectangle pairs split)
+                    auto rule_shape = [&](int r) -> int {
+                        const int sh = rs.shape[ty * 5 + r];
+                        return VARY && ty == BEM_RECTANGLE ? shape_c(sh) | shape_r(sh) << 2 : sh;
+                    };
                     // expand rule r of element e into the free node buffer (lane i: node i)
                     auto expand = [&](int r) -> int {
                         const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
-                        // the frame from the duplicated, doubled records: 2 (e0x, e0x, e0y, e0y),
-                        // 2 (e0z, e0z, e1x, e1x), 2 (e1y, e1y, e1z, e1z); the charge from qt
+                        const int shape = rs.shape[ty * 5 + r], nrec = shape_c(shape) + shape_r(shape);
+                        // the doubled frame from the duplicated records: 2 (e0x, e0x, e0y, e0y),
+                        // 2 (e0z, e0z, e1x, e1x), 2 (e1y, e1y, e1z, e1z), taken with alpha / 2 and
+                        // beta / 2 (exact scalings); the charge from qt
                         const float4 r3 = pr[3], r4 = pr[4], r5 = pr[5];
-                        const float4 f0 = make_float4(0.5f * r3.x, 0.5f * r3.z, 0.5f * r4.x, ws.qt[e].x),
-                                     f1 = make_float4(0.5f * r4.z, 0.5f * r5.x, 0.5f * r5.z, 0.0f);
+                        const float4 f0 = make_float4(r3.x, r3.z, r4.x, ws.qt[e].x), f1 = make_float4(r4.z, r5.x, r5.z, 0.0f);
                         float ca = 0.0f, cb = 0.0f, cc = 0.0f;
                         if (VARY && p.curv) {  // quadratic densities: area x second-order coefficients
                             const size_t j = (size_t)(b0 + e);
@@ -1019,10 +1147,20 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             cb = (float)(p.curv[3 * j + 1] * ar);
                             cc = (float)(p.curv[3 * j + 2] * ar);
                         }
-                        for (int i = lane; i < n; i += 32) {
-                            const float al = rs.al[st + i], be = rs.be[st + i];
-                            const float ox = fmaf(al, f0.x, be * f1.x), oy = fmaf(al, f0.y, be * f1.y),
-                                        oz = fmaf(al, f0.z, be * f1.z);
+                        // varying densities: the two nodes of a pair carry different charges, so a
+                        // rectangle's pair record i >= c becomes the single records c + 2 (i - c) (node
+                        // o) and the one after it (node -o)
+                        const bool split = VARY && ty == BEM_RECTANGLE;
+                        const int c = shape_c(shape), nout = split ? 2 * nrec - c : nrec;
+                        for (int k = lane; k < nout; k += 32) {
+                            // output record k: table record i, its node o or (odd split records) -o
+                            const int i = split && k >= c ? c + ((k - c) >> 1) : k;
+                            const bool neg = split && k >= c && ((k - c) & 1);
+                            const float al = neg ? -rs.al[st + i] : rs.al[st + i];
+                            const float be = neg ? -rs.be[st + i] : rs.be[st + i];
+                            const float ah = 0.5f * al, bh = 0.5f * be;
+                            const float ox = fmaf(ah, f0.x, bh * f1.x), oy = fmaf(ah, f0.y, bh * f1.y),
+                                        oz = fmaf(ah, f0.z, bh * f1.z);
                             const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
                             // charge w_i area sigma(Q_i) (linear / quadratic densities: sigma at the node)
                             float qi = f0.w;
@@ -1030,11 +1168,11 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                                 qi = fmaf(al, ws.sl[2 * e], fmaf(be, ws.sl[2 * e + 1], qi));
                                 if (p.curv) qi = fmaf(al, fmaf(al, ca, be * cb), fmaf(be * be, cc, qi));
                             }
-                            const float am = -al, bm = -be, wq = rs.w[st + i] * qi;
-                            ws.nd[par][kNodeRecs * i] = make_float4(am, am, bm, bm);
-                            ws.nd[par][kNodeRecs * i + 1] = make_float4(oo, oo, wq, wq);
-                            const float wa = 0.5f * (wq * am), wb = 0.5f * (wq * bm);  // times the doubled frame
-                            ws.nd[par][kNodeRecs * i + 2] = make_float4(wa, wa, wb, wb);
+                            const float am = -al, bm = -be, wq = rs.w[st + i] * qi, wh = 0.5f * wq;
+                            ws.nd[par][kNodeRecs * k] = make_float4(am, am, bm, bm);
+                            ws.nd[par][kNodeRecs * k + 1] = make_float4(oo, oo, wq, wq);
+                            const float wa = wh * am, wb = wh * bm;  // halved: times the doubled frame
+                            ws.nd[par][kNodeRecs * k + 2] = make_float4(wa, wa, wb, wb);
                         }
                         __syncwarp();
                         return n;
@@ -1042,9 +1180,9 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                     // node table: copy rule r of element el (type t) into buffer buf
                     // asynchronously (lane i: node i); the caller waits and syncs
                     auto fetch = [&](int el, int t, int r, int buf) -> int {
-                        const int n = rs.n[t * 5 + r];
+                        const int n = rs.n[t * 5 + r], shape = rs.shape[t * 5 + r];
                         const float4* src = p.nodes + ((size_t)el * kTableSlots + rs.start[t * 5 + r]) * kNodeRecs;
-                        for (int i = lane; i < n; i += 32) {
+                        for (int i = lane; i < shape_c(shape) + shape_r(shape); i += 32) {
 #pragma unroll
                             for (int k = 0; k < kNodeRecs; ++k)
                                 cp_async16(&ws.nd[buf][kNodeRecs * i + k], src + kNodeRecs * i + k);
@@ -1071,15 +1209,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         } else {
                             n = expand(band_rule(cd));
                         }
-                        if constexpr (BEM_INIT_PASS) {
-                            nodes2<NP, WANT_E, GRAD3, true>(ws.nd[par], n, sv, uv, vv, eacc);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < NP; ++k)
-#pragma unroll
-                                for (int j = 0; j < NE; ++j) eacc[k][j] = make_float2(0.0f, 0.0f);
-                            nodes2<NP, WANT_E, GRAD3, false>(ws.nd[par], n, sv, uv, vv, eacc);
-                        }
+                        // the element's first node starts its sums
+                        nodes2<NP, WANT_E, GRAD3, true, !VARY>(ws.nd[par], ty, rule_shape(band_rule(cd)), sv, uv, vv, eacc);
                         par ^= 1;
                         if (STATS && lane == 0) {
                             atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -1128,7 +1259,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             } else {
                                 n = expand(band_rule(band));
                             }
-                            nodes2<NP, WANT_E, GRAD3, false>(ws.nd[par], n, sm, uv, vv, eacc);
+                            nodes2<NP, WANT_E, GRAD3, false, !VARY>(ws.nd[par], ty, rule_shape(band_rule(band)), sm, uv, vv, eacc);
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                         }
@@ -1328,11 +1459,12 @@ int uploaded_mask = 0;  // devices whose constant rule tables are loaded
 // 1e-8, which scales the charge of every element that uses the rule by the
 // same factor: a systematic error that, unlike independent rounding errors,
 // does not average out over many elements.
-void round_weights(const double* w, int n, float* out) {
+// A record that stands for a pair of nodes (mult 2) counts twice.
+void round_weights(const double* w, const int* mult, int n, float* out) {
     for (int i = 0; i < n; ++i) out[i] = (float)w[i];
     for (int it = 0; it < 4 * n; ++it) {
         double sum = 0.0;  // exact: at most 33 floats within a few binades
-        for (int i = 0; i < n; ++i) sum += (double)out[i];
+        for (int i = 0; i < n; ++i) sum += mult[i] * (double)out[i];
         const double res = 1.0 - sum;
         if (res == 0.0) break;
         int best = -1;
@@ -1340,7 +1472,7 @@ void round_weights(const double* w, int n, float* out) {
         float best_val = 0.0f;
         for (int i = 0; i < n; ++i) {
             const float c = nextafterf(out[i], res > 0.0 ? INFINITY : -INFINITY);
-            const double err = fabs(res - ((double)c - (double)out[i]));
+            const double err = fabs(res - mult[i] * ((double)c - (double)out[i]));
             if (err < best_err) {
                 best_err = err;
                 best = i;
@@ -1352,23 +1484,71 @@ void round_weights(const double* w, int n, float* out) {
     }
 }
 
+// The mixed path's node records of every rule: the centre node first (alpha =
+// beta = 0, if the rule has one), then on rectangles one record per pair of
+// nodes o, -o of equal weight (every rule of App. B is centrally symmetric),
+// on triangles one record per node.  The FP32 weights are rounded so that the
+// rule's weights, pairs counted twice, still sum to one.
+int build_records(const RuleSet& rs, float* af, float* bf, float* wf, int* rec_start, int* shape) {
+    for (int t = 0; t < 2; ++t) {
+        int slot = 0;
+        for (int r = 0; r < 5; ++r) {
+            const int s0 = rs.start[t][r], n = rs.n[t][r];
+            const double *al = &rs.alpha[t][s0], *be = &rs.beta[t][s0], *w = &rs.w[t][s0];
+            double rw[kSlots];
+            int idx[kSlots], mult[kSlots], nrec = 0, ncen = 0;
+            bool used[kSlots] = {};
+            for (int i = 0; i < n; ++i)
+                if (al[i] == 0.0 && be[i] == 0.0) { idx[nrec] = i; mult[nrec++] = 1; used[i] = true; ++ncen; }
+            for (int i = 0; i < n; ++i) {
+                if (used[i]) continue;
+                used[i] = true;
+                int mate = -1;
+                if (t == BEM_RECTANGLE)
+                    for (int j = i + 1; j < n && mate < 0; ++j)
+                        if (!used[j] && al[j] == -al[i] && be[j] == -be[i] && w[j] == w[i]) mate = j;
+                if (t == BEM_RECTANGLE && mate < 0) {
+                    set_error("rule tables: rectangle rule %d is not centrally symmetric", r);
+                    return BEM_ERR_INVALID;
+                }
+                if (mate >= 0) used[mate] = true;
+                idx[nrec] = i;
+                mult[nrec++] = mate >= 0 ? 2 : 1;
+            }
+            if (ncen > 1 || nrec - ncen < 1) {
+                set_error("rule tables: unexpected shape of rule %d", r);
+                return BEM_ERR_INVALID;
+            }
+            for (int k = 0; k < nrec; ++k) {
+                af[t * kSlots + slot + k] = (float)al[idx[k]];
+                bf[t * kSlots + slot + k] = (float)be[idx[k]];
+                rw[k] = w[idx[k]];
+            }
+            round_weights(rw, mult, nrec, &wf[t * kSlots + slot]);
+            rec_start[t * 5 + r] = slot;
+            shape[t * 5 + r] = ncen | (nrec - ncen) << 1;
+            slot += nrec;
+        }
+    }
+    return BEM_OK;
+}
+
 int upload_rules(int dev) {
     if (dev < 32 && (uploaded_mask >> dev) & 1) return BEM_OK;
     const RuleSet& rs = rules();
-    float af[2 * kSlots], bf[2 * kSlots], wf[2 * kSlots];
+    float af[2 * kSlots] = {}, bf[2 * kSlots] = {}, wf[2 * kSlots] = {};
     double ad[2 * kSlots], bd[2 * kSlots], wd[2 * kSlots];
     for (int t = 0; t < 2; ++t)
         for (int s = 0; s < kSlots; ++s) {
             ad[t * kSlots + s] = rs.alpha[t][s];
             bd[t * kSlots + s] = rs.beta[t][s];
             wd[t * kSlots + s] = rs.w[t][s];
-            af[t * kSlots + s] = (float)rs.alpha[t][s];
-            bf[t * kSlots + s] = (float)rs.beta[t][s];
-            wf[t * kSlots + s] = (float)rs.w[t][s];
         }
-    for (int t = 0; t < 2; ++t)
-        for (int r = 0; r < 5; ++r)
-            round_weights(&rs.w[t][rs.start[t][r]], rs.n[t][r], &wf[t * kSlots + rs.start[t][r]]);
+    int rec_start[10], shape[10];
+    const int rc = build_records(rs, af, bf, wf, rec_start, shape);
+    if (rc) return rc;
+    BEM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_start, rec_start, sizeof rec_start));
+    BEM_CUDA_TRY(cudaMemcpyToSymbol(c_rule_shape, shape, sizeof shape));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_alpha_f, af, sizeof af));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_beta_f, bf, sizeof bf));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_w_f, wf, sizeof wf));
@@ -1420,8 +1600,9 @@ int launch_stats(const FarK& k, cudaStream_t s, bool stats) {
 }
 
 // Node records of every rule for every element (BEM_FLAG_NODE_TABLE): thread
-// (element j, slot) writes what the kernel's on-the-fly expansion writes,
-// with the bare weight w in place of w q.
+// (element j, record slot) writes what the kernel's on-the-fly expansion
+// writes, with the bare weight w in place of w q (rectangles use fewer slots:
+// one record per pair of nodes).
 __global__ void k_fill_nodes(int n, const float4* __restrict__ e0f, const float4* __restrict__ e1f,
                              const int* __restrict__ type, float4* __restrict__ out) {
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -106,6 +106,25 @@ def test_library_rules_match_oracle_tables():
             assert np.allclose(key(lib), key(o), rtol=0, atol=1e-15)
 
 
+def test_rectangle_rules_centrally_symmetric():
+    """The mixed far kernel evaluates the rectangle rules' nodes in pairs o, -o
+    of equal weight (plus the centre node), so every rectangle rule of App. B
+    must map onto itself under (x, y) -> (-x, -y): exactly in the library's
+    tables (the kernel pairs nodes by exact equality), and in the oracle's
+    independently typed tables up to rounding."""
+    for r in range(5):
+        lib = bem.bem_rule(1, r)
+        centre = (lib[:, 0] == 0.0) & (lib[:, 1] == 0.0)
+        assert centre.sum() <= 1
+        mirrored = np.stack([-lib[:, 0], -lib[:, 1], lib[:, 2]], 1)
+        key = lambda a: a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+        assert np.array_equal(key(lib) + 0.0, key(mirrored) + 0.0)
+        orc = oracle.rule(1, r)
+        o = np.stack([orc[:, 0], orc[:, 1], orc[:, 3]], 1)
+        om = np.stack([-orc[:, 0], -orc[:, 1], orc[:, 3]], 1)
+        assert np.allclose(key(o), key(om), rtol=0, atol=1e-15)
+
+
 def test_library_default_limits_match_oracle():
     """The library's default DR band limits (bem_default_limits) are the
     oracle's frozen table, which tests/test_oracle_field.py pins against the

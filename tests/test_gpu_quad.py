@@ -94,7 +94,12 @@ def test_zero_second_order_equals_linear_and_reset(bem, case):
             m.set_sigma_quadratic(np.concatenate([mesh.sigma[:, None], np.zeros((mesh.n, 5))], axis=1))
             phi5, E5 = m.eval(pts)
         assert np.array_equal(phi1, phi3) and np.array_equal(E1, E3)
-        assert rel_phi(phi5, phi4).max() <= 1e-13 and rel_E(E5, E4).max() <= 1e-13
+        # the constant-density kernel sums a rectangle rule's nodes o and -o together, the
+        # varying-density kernel one by one: the same to rounding (FP64) or within the mixed
+        # path's tolerance
+        t5 = 1e-13 if prec == 0 else 1e-6
+        assert rel_phi(phi5, phi4)[far].max() <= t5 and rel_E(E5, E4)[far].max() <= t5
+        assert rel_phi(phi5, phi4).max() <= 10 * t5 and rel_E(E5, E4).max() <= 10 * t5
         assert rel_phi(phi2, phi1).max() <= 1e-11 and rel_E(E2, E1).max() <= 1e-11
         # the far sums take the same node charges: only the near pairs can differ
         assert np.array_equal(phi2[far], phi1[far]) and np.array_equal(E2[far], E1[far])
