@@ -511,9 +511,26 @@ __device__ __forceinline__ void node2_pair(const float4 ab, const float4 ow, con
         const float2 rp = add2(t, m), rm = fma2(m, m1, t);
         const float2 ip = make_float2(rsqrtf(rp.x), rsqrtf(rp.y)), im = make_float2(rsqrtf(rm.x), rsqrtf(rm.y));
         if constexpr (GRAD) {
+            // the two nodes' sums: b = w/r^3 and c = w/r^5 add up, the odd moments
+            // (c alpha, c beta) take the difference c_+ - c_-, the even ones the sum
             static_assert(NS == 7, "gradient sums");
-            grad_terms<INIT>(al, be, w, ip, acc[k]);
-            grad_terms<false>(mul2(al, m1), mul2(be, m1), w, im, acc[k]);
+            const float2 i2p = mul2(ip, ip), i2m = mul2(im, im);
+            const float2 bp = mul2(mul2(w, ip), i2p), bm = mul2(mul2(w, im), i2m);
+            const float2 cp = mul2(bp, i2p), cm = mul2(bm, i2m);
+            const float2 bs = add2(bp, bm), cs = add2(cp, cm), cd = fma2(cm, m1, cp);
+            const float2 ta = mul2(cs, al), tb = mul2(cs, be);
+            if (INIT) {
+                acc[k][0] = bs; acc[k][1] = cs; acc[k][2] = mul2(al, cd); acc[k][3] = mul2(be, cd);
+                acc[k][4] = mul2(ta, al); acc[k][5] = mul2(ta, be); acc[k][6] = mul2(tb, be);
+            } else {
+                acc[k][0] = add2(acc[k][0], bs);
+                acc[k][1] = add2(acc[k][1], cs);
+                acc[k][2] = fma2(al, cd, acc[k][2]);
+                acc[k][3] = fma2(be, cd, acc[k][3]);
+                acc[k][4] = fma2(ta, al, acc[k][4]);
+                acc[k][5] = fma2(ta, be, acc[k][5]);
+                acc[k][6] = fma2(tb, be, acc[k][6]);
+            }
             continue;
         }
         if (INIT) acc[k][0] = mul2(w, ip);
