@@ -28,7 +28,10 @@
 //    adds them back in element order.
 //
 // Arithmetic:
-//  * FP64 path: everything in double precision.
+//  * FP64 path: everything in double precision.  Evaluation and assembly use
+//    the frame form below (r_i^2 = s + |o_i|^2 + A_i u + B_i v, the field
+//    rebuilt per element, rectangle nodes in pairs o, -o), the field
+//    gradient takes P - Q_i node by node.
 //  * Mixed path: points and centroids are split into FP32 hi + lo parts with
 //    the hi parts on one power-of-two grid fixed by the mesh, so that in
 //    d = P - C = (P_hi - C_hi) + (P_lo - C_lo) the first difference is exact
@@ -120,10 +123,10 @@ constexpr int kAsmGroup = 4;  // mixed assembly: elements per staged group (a 32
 
 __constant__ float c_alpha_f[2 * kSlots], c_beta_f[2 * kSlots], c_w_f[2 * kSlots];
 __constant__ double c_alpha_d[2 * kSlots], c_beta_d[2 * kSlots], c_w_d[2 * kSlots];
-__constant__ int c_rule_n[10], c_rule_start[10];
-// mixed path: the rules as node records (c_alpha_f, c_beta_f, c_w_f): per rule the centre node (if
-// any), then one record per pair (o, -o) on rectangles or per node on triangles; the first record
-// of each rule and its shape (centre records | other records << 1)
+__constant__ int c_rule_n[10];
+// the rules as node records (FP32: c_alpha_f, c_beta_f, c_w_f; FP64: c_alpha_d, ...): per rule the
+// centre node (if any), then one record per pair (o, -o) on rectangles or per node on triangles; the
+// first record of each rule and its shape (centre records | other records << 1)
 __constant__ int c_rec_start[10], c_rule_shape[10];
 
 struct FarK {
@@ -260,51 +263,80 @@ __device__ __forceinline__ void close_runs(const FarK& p, int tile_base, int n_p
     if (lane == 0 && pairs) atomicAdd(p.counters + kPairCounter, (unsigned long long)pairs);
 }
 
-// One point charge (offset o, charge o.w) at the PT points of a lane.
-// MASKED: point q's charge is scaled by mq[q] (1 or 0); masked-off points
-// have been moved far away by the caller, so r^2 > 0 and their terms are
-// exact zeros, while an active point's arithmetic is bit-for-bit that of
-// the unmasked path.  INIT: the sums start from this term.
-template <typename R, typename R4, int PT, bool WANT_E, bool MASKED, bool INIT>
-__device__ __forceinline__ void node(const R4 o, const R (&dx)[PT], const R (&dy)[PT], const R (&dz)[PT],
-                                     R (&acc)[PT][4], const R (&mq)[PT]) {
+// ---- FP64 path, frame form.  A node record is (A, B, |o|^2, w q) with
+// A = -2 alpha, B = -2 beta, and per point s = |d|^2, u = d.e0, v = d.e1, so
+// r^2 = s + |o|^2 + A u + B v.  The element's sums per point are
+// (sum w q / r, sum b, sum b A, sum b B) with b = w q / r^3, and its field is
+// d sum b + (e0 / 2) sum b A + (e1 / 2) sum b B.  A point that must not take
+// part carries s = +inf: r^2 = +inf, rsqrt gives +0 and its terms are exact
+// zeros.
+template <int PT, bool WANT_E>
+__device__ __forceinline__ void node64(const double4 o, const double (&s)[PT], const double (&u)[PT],
+                                       const double (&v)[PT], double (&acc)[PT][4]) {
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
-        const R rx = dx[q] - o.x, ry = dy[q] - o.y, rz = dz[q] - o.z;
-        const R r2 = fmad(rx, rx, fmad(ry, ry, rz * rz));
-        R wq = o.w;
-        if (MASKED) wq *= mq[q];
-        const R inv = rsq(r2);
-        const R a = wq * inv;          // q_i / r_i
-        const R b = a * (inv * inv);   // q_i / r_i^3
-        if (INIT) {
-            acc[q][0] = a;
-            if (WANT_E) { acc[q][1] = b * rx; acc[q][2] = b * ry; acc[q][3] = b * rz; }
-        } else {
-            acc[q][0] += a;
-            if (WANT_E) {
-                acc[q][1] = fmad(b, rx, acc[q][1]);
-                acc[q][2] = fmad(b, ry, acc[q][2]);
-                acc[q][3] = fmad(b, rz, acc[q][3]);
-            }
+        const double r2 = fma(o.x, u[q], fma(o.y, v[q], s[q] + o.z));
+        const double inv = rsqrt(r2);
+        acc[q][0] = fma(o.w, inv, acc[q][0]);
+        if (WANT_E) {
+            const double b = o.w * (inv * (inv * inv));
+            acc[q][1] += b;
+            acc[q][2] = fma(o.x, b, acc[q][2]);
+            acc[q][3] = fma(o.y, b, acc[q][3]);
         }
     }
 }
 
-// Accumulate the point charges of one rule of one element into
-// acc[q] = (phi, Ex, Ey, Ez) sums.  nd: the rule's (offset, w_i q) records in
-// shared memory (warp-uniform addresses: broadcast).  MASKED: point q counts
-// with weight mq[q].  INIT: the first node starts the sums.
-template <typename R, typename R4, int PT, bool WANT_E, bool MASKED, bool INIT>
-__device__ __forceinline__ void nodes(const R4* __restrict__ nd, int n, const R (&dx)[PT], const R (&dy)[PT],
-                                      const R (&dz)[PT], R (&acc)[PT][4], const R (&mq)[PT]) {
+// Nodes o and -o of equal weight (rectangle rules, App. B), record of the node
+// at o: they share s + |o|^2 and m = A u + B v (r_+-^2 = s + |o|^2 +- m), and
+// their A, B moments combine into A (b_+ - b_-).
+template <int PT, bool WANT_E>
+__device__ __forceinline__ void node64_pair(const double4 o, const double (&s)[PT], const double (&u)[PT],
+                                            const double (&v)[PT], double (&acc)[PT][4]) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const double t = s[q] + o.z, m = fma(o.x, u[q], o.y * v[q]);
+        const double ip = rsqrt(t + m), im = rsqrt(t - m);
+        acc[q][0] = fma(o.w, im, fma(o.w, ip, acc[q][0]));
+        if (WANT_E) {
+            const double bp = o.w * (ip * (ip * ip)), bm = o.w * (im * (im * im));
+            acc[q][1] = (acc[q][1] + bp) + bm;
+            const double bd = bp - bm;
+            acc[q][2] = fma(o.x, bd, acc[q][2]);
+            acc[q][3] = fma(o.y, bd, acc[q][3]);
+        }
+    }
+}
+
+// A rule's centre node (alpha = beta = 0): r^2 = s.
+template <int PT, bool WANT_E>
+__device__ __forceinline__ void node64_centre(const double4 o, const double (&s)[PT], double (&acc)[PT][4]) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const double inv = rsqrt(s[q]);
+        acc[q][0] = fma(o.w, inv, acc[q][0]);
+        if (WANT_E) acc[q][1] += o.w * (inv * (inv * inv));
+    }
+}
+
+// All records of one rule (shape = c | r << 1): the centre node, then pairs
+// (rectangles, PAIRS) or single nodes.
+template <int PT, bool WANT_E, bool PAIRS>
+__device__ __forceinline__ void nodes64(const double4* __restrict__ nd, int ty, int shape, const double (&s)[PT],
+                                        const double (&u)[PT], const double (&v)[PT], double (&acc)[PT][4]) {
+    const int c = shape & 1, n = c + (shape >> 1);
     int i = 0;
-    if (INIT) {  // every rule has at least four nodes
-        node<R, R4, PT, WANT_E, MASKED, true>(nd[0], dx, dy, dz, acc, mq);
+    if (c) {
+        node64_centre<PT, WANT_E>(nd[0], s, acc);
         i = 1;
     }
-#pragma unroll kNodeUnroll
-    for (; i < n; ++i) node<R, R4, PT, WANT_E, MASKED, false>(nd[i], dx, dy, dz, acc, mq);
+    if (PAIRS && ty == BEM_RECTANGLE) {
+#pragma unroll 2
+        for (; i < n; ++i) node64_pair<PT, WANT_E>(nd[i], s, u, v, acc);
+    } else {
+#pragma unroll 4
+        for (; i < n; ++i) node64<PT, WANT_E>(nd[i], s, u, v, acc);
+    }
 }
 
 // Field gradient of one point charge (offset o, charge o.w) at the PT points
@@ -793,7 +825,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
     }
     if (tid < 10) {
         rs.n[tid] = c_rule_n[tid];
-        rs.start[tid] = F64 ? c_rule_start[tid] : c_rec_start[tid];
+        rs.start[tid] = c_rec_start[tid];
         rs.shape[tid] = c_rule_shape[tid];
     }
     if (STATS && tid < 15) rs.stat[tid] = 0ull;
@@ -999,21 +1031,27 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 else ty = __float_as_int(ws.qt[e].y);
 
                 if constexpr (F64) {
-                    // ---------------- FP64 path: P - Q_i = (P - C) - o_i
+                    // ---------------- FP64 path: d = P - C; the field gradient takes P - Q_i = d - o_i
+                    // node by node, evaluation and assembly the frame form (node64)
                     const R4 c = ws.c[e];
                     R dx[PT], dy[PT], dz[PT];
 #pragma unroll
                     for (int q = 0; q < PT; ++q) {
                         dx[q] = px[q] - c.x; dy[q] = py[q] - c.y; dz[q] = pz[q] - c.z;
                     }
-                    // assembly: per-element sums; evaluation: the running sums
-                    constexpr bool kElemSum = MODE == 1;
-                    R eacc[PT][4];
-                    R(&dst)[PT][4] = kElemSum ? eacc : acc;
-
-                    // expand rule r of element e into the free node buffer (lane i: node i)
+                    constexpr bool kGrad = MODE == 2;
+                    // varying densities and the gradient: the two nodes of a rectangle's pair as two records
+                    const bool split = (VARY || kGrad) && ty == BEM_RECTANGLE;
+                    auto rule_shape64 = [&](int r) -> int {
+                        const int sh = rs.shape[ty * 5 + r];
+                        return split ? shape_c(sh) | shape_r(sh) << 2 : sh;
+                    };
+                    // expand rule r of element e into the free node buffer (lane k: output record k);
+                    // returns the rule's node count
                     auto expand = [&](int r) -> int {
                         const int n = rs.n[ty * 5 + r], st = ty * kSlots + rs.start[ty * 5 + r];
+                        const int shape = rs.shape[ty * 5 + r], c0 = shape_c(shape), nrec = c0 + shape_r(shape);
+                        const int nout = split ? 2 * nrec - c0 : nrec;
                         const R4 a = ws.e0[e], b = ws.e1[e];
                         R ca = (R)0, cb = (R)0, cc = (R)0;
                         if (VARY && p.curv) {  // quadratic densities: area x second-order coefficients
@@ -1023,25 +1061,46 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             cb = (R)(p.curv[3 * j + 1] * ar);
                             cc = (R)(p.curv[3 * j + 2] * ar);
                         }
-                        for (int i = lane; i < n; i += 32) {
-                            const R al = rs.al[st + i], be = rs.be[st + i];
+                        for (int k = lane; k < nout; k += 32) {
+                            // output record k: table record i, its node o or (odd split records) -o
+                            const int i = split && k >= c0 ? c0 + ((k - c0) >> 1) : k;
+                            const bool neg = split && k >= c0 && ((k - c0) & 1);
+                            const R al = neg ? -rs.al[st + i] : rs.al[st + i];
+                            const R be = neg ? -rs.be[st + i] : rs.be[st + i];
                             // charge w_i area sigma(Q_i) (linear / quadratic densities: sigma at the node)
                             R qi = a.w;
                             if constexpr (VARY) {
                                 qi = fmad(al, ws.sl[2 * e], fmad(be, ws.sl[2 * e + 1], qi));
                                 if (p.curv) qi = fmad(al, fmad(al, ca, be * cb), fmad(be * be, cc, qi));
                             }
-                            ws.nd[par][i] = R4{fmad(al, a.x, be * b.x), fmad(al, a.y, be * b.y),
-                                               fmad(al, a.z, be * b.z), rs.w[st + i] * qi};
+                            const R ox = fmad(al, a.x, be * b.x), oy = fmad(al, a.y, be * b.y), oz = fmad(al, a.z, be * b.z);
+                            const R wq = rs.w[st + i] * qi;
+                            if constexpr (kGrad) ws.nd[par][k] = R4{ox, oy, oz, wq};
+                            else ws.nd[par][k] = R4{-2.0 * al, -2.0 * be, fmad(ox, ox, fmad(oy, oy, oz * oz)), wq};
                         }
                         __syncwarp();
                         return n;
                     };
 
+                    // frame form: s = |d|^2, u = d.e0, v = d.e1; the element's sums (eacc)
+                    R sv[PT], uv[PT], vv[PT];
+                    R eacc[PT][4];
+                    if constexpr (!kGrad) {
+                        const R4 a = ws.e0[e], b = ws.e1[e];
+#pragma unroll
+                        for (int q = 0; q < PT; ++q) {
+                            sv[q] = fmad(dx[q], dx[q], fmad(dy[q], dy[q], dz[q] * dz[q]));
+                            uv[q] = fmad(dx[q], a.x, fmad(dy[q], a.y, dz[q] * a.z));
+                            vv[q] = fmad(dx[q], b.x, fmad(dy[q], b.y, dz[q] * b.z));
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) eacc[q][k] = (R)0;
+                        }
+                    }
+
                     if (cd >= 1 && cd <= 5) {
                         const int n = expand(band_rule(cd));
-                        if constexpr (MODE == 2) nodes_grad<R, R4, PT, false>(ws.nd[par], n, dx, dy, dz, accg, ones);
-                        else nodes<R, R4, PT, WANT_E, false, kElemSum>(ws.nd[par], n, dx, dy, dz, dst, ones);
+                        if constexpr (kGrad) nodes_grad<R, R4, PT, false>(ws.nd[par], n, dx, dy, dz, accg, ones);
+                        else nodes64<PT, WANT_E, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(cd)), sv, uv, vv, eacc);
                         par ^= 1;
                         if (STATS && lane == 0) {
                             atomicAdd(&rs.stat[6 * ty + cd], (unsigned long long)nvalid);
@@ -1055,7 +1114,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         unsigned mask = 0;
 #pragma unroll
                         for (int q = 0; q < PT; ++q) {
-                            const R d2 = dx[q] * dx[q] + dy[q] * dy[q] + dz[q] * dz[q];
+                            const R d2 = fmad(dx[q], dx[q], fmad(dy[q], dy[q], dz[q] * dz[q]));
                             bq[q] = band_of<R>(d2, th);
                             if (valid(q)) mask |= 1u << bq[q];
                         }
@@ -1066,28 +1125,29 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             for (int q = 0; q < PT; ++q) want[q] = valid(q) && bq[q] == 0;
                             note_near<PT>(p, want, base, b0 + e, ws.run_first, ws.run_len, ws.ncnt, lane);
                         }
-                        if (kElemSum) {  // near-only points get zero far sums
-#pragma unroll
-                            for (int q = 0; q < PT; ++q)
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) eacc[q][k] = (R)0;
-                        }
 #pragma unroll 1
                         for (int band = 1; band <= 5; ++band) {
                             if (!(mask & (1u << band))) continue;
-                            // points of other bands: zero charge, parked far from every node
-                            R mq[PT], mx[PT], my[PT], mz[PT];
-#pragma unroll
-                            for (int q = 0; q < PT; ++q) {
-                                const bool on = bq[q] == band;
-                                mq[q] = on ? (R)1 : (R)0;
-                                mx[q] = on ? dx[q] : (R)1e3;
-                                my[q] = on ? dy[q] : (R)1e3;
-                                mz[q] = on ? dz[q] : (R)1e3;
-                            }
                             const int n = expand(band_rule(band));
-                            if constexpr (MODE == 2) nodes_grad<R, R4, PT, true>(ws.nd[par], n, mx, my, mz, accg, mq);
-                            else nodes<R, R4, PT, WANT_E, true, false>(ws.nd[par], n, mx, my, mz, dst, mq);
+                            if constexpr (kGrad) {
+                                // points of other bands: zero charge, parked far from every node
+                                R mq[PT], mx[PT], my[PT], mz[PT];
+#pragma unroll
+                                for (int q = 0; q < PT; ++q) {
+                                    const bool on = bq[q] == band;
+                                    mq[q] = on ? (R)1 : (R)0;
+                                    mx[q] = on ? dx[q] : (R)1e3;
+                                    my[q] = on ? dy[q] : (R)1e3;
+                                    mz[q] = on ? dz[q] : (R)1e3;
+                                }
+                                nodes_grad<R, R4, PT, true>(ws.nd[par], n, mx, my, mz, accg, mq);
+                            } else {
+                                // points of other bands sit at infinite distance in this pass
+                                R sm[PT];
+#pragma unroll
+                                for (int q = 0; q < PT; ++q) sm[q] = bq[q] == band ? sv[q] : (R)INFINITY;
+                                nodes64<PT, WANT_E, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(band)), sm, uv, vv, eacc);
+                            }
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                         }
@@ -1099,6 +1159,20 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                                     const unsigned m = __ballot_sync(0xffffffffu, valid(q) && bq[q] == band);
                                     if (lane == 0 && m) atomicAdd(&rs.stat[6 * ty + band], (unsigned long long)__popc(m));
                                 }
+                            }
+                        }
+                    }
+                    if constexpr (MODE == 0) {
+                        // the element's phi and E = d B + (e0 / 2) sum b A + (e1 / 2) sum b B into the running sums
+                        const R4 a = ws.e0[e], b = ws.e1[e];
+#pragma unroll
+                        for (int q = 0; q < PT; ++q) {
+                            acc[q][0] += eacc[q][0];
+                            if (WANT_E) {
+                                const R ha = 0.5 * eacc[q][2], hb = 0.5 * eacc[q][3];
+                                acc[q][1] += fmad(dx[q], eacc[q][1], fmad(a.x, ha, b.x * hb));
+                                acc[q][2] += fmad(dy[q], eacc[q][1], fmad(a.y, ha, b.y * hb));
+                                acc[q][3] += fmad(dz[q], eacc[q][1], fmad(a.z, ha, b.z * hb));
                             }
                         }
                     }
@@ -1506,7 +1580,8 @@ void round_weights(const double* w, const int* mult, int n, float* out) {
 // nodes o, -o of equal weight (every rule of App. B is centrally symmetric),
 // on triangles one record per node.  The FP32 weights are rounded so that the
 // rule's weights, pairs counted twice, still sum to one.
-int build_records(const RuleSet& rs, float* af, float* bf, float* wf, int* rec_start, int* shape) {
+int build_records(const RuleSet& rs, float* af, float* bf, float* wf, double* ad, double* bd, double* wd,
+                  int* rec_start, int* shape) {
     for (int t = 0; t < 2; ++t) {
         int slot = 0;
         for (int r = 0; r < 5; ++r) {
@@ -1540,6 +1615,9 @@ int build_records(const RuleSet& rs, float* af, float* bf, float* wf, int* rec_s
                 af[t * kSlots + slot + k] = (float)al[idx[k]];
                 bf[t * kSlots + slot + k] = (float)be[idx[k]];
                 rw[k] = w[idx[k]];
+                ad[t * kSlots + slot + k] = al[idx[k]];
+                bd[t * kSlots + slot + k] = be[idx[k]];
+                wd[t * kSlots + slot + k] = w[idx[k]];
             }
             round_weights(rw, mult, nrec, &wf[t * kSlots + slot]);
             rec_start[t * 5 + r] = slot;
@@ -1554,15 +1632,9 @@ int upload_rules(int dev) {
     if (dev < 32 && (uploaded_mask >> dev) & 1) return BEM_OK;
     const RuleSet& rs = rules();
     float af[2 * kSlots] = {}, bf[2 * kSlots] = {}, wf[2 * kSlots] = {};
-    double ad[2 * kSlots], bd[2 * kSlots], wd[2 * kSlots];
-    for (int t = 0; t < 2; ++t)
-        for (int s = 0; s < kSlots; ++s) {
-            ad[t * kSlots + s] = rs.alpha[t][s];
-            bd[t * kSlots + s] = rs.beta[t][s];
-            wd[t * kSlots + s] = rs.w[t][s];
-        }
+    double ad[2 * kSlots] = {}, bd[2 * kSlots] = {}, wd[2 * kSlots] = {};
     int rec_start[10], shape[10];
-    const int rc = build_records(rs, af, bf, wf, rec_start, shape);
+    const int rc = build_records(rs, af, bf, wf, ad, bd, wd, rec_start, shape);
     if (rc) return rc;
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_start, rec_start, sizeof rec_start));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_rule_shape, shape, sizeof shape));
@@ -1573,7 +1645,6 @@ int upload_rules(int dev) {
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_beta_d, bd, sizeof bd));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_w_d, wd, sizeof wd));
     BEM_CUDA_TRY(cudaMemcpyToSymbol(c_rule_n, rs.n, sizeof rs.n));
-    BEM_CUDA_TRY(cudaMemcpyToSymbol(c_rule_start, rs.start, sizeof rs.start));
     if (dev < 32) uploaded_mask |= 1 << dev;
     return BEM_OK;
 }
