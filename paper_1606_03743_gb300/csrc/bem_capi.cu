@@ -220,6 +220,7 @@ void free_mesh(bem_mesh* m) {
     cudaFree(d.fr);
     cudaFree(d.geo);
     cudaFree(d.verts);
+    cudaFree(d.egeo);
     cudaFree(d.type);
     cudaFree(d.sigma);
     cudaFree(d.slope);
@@ -418,6 +419,7 @@ int bem_create(const int32_t* types, const double* verts, const double* sigma, i
     BEM_ALLOC(d.fr, 6 * nn);
     BEM_ALLOC(d.geo, 2 * nn);
     BEM_ALLOC(d.verts, 12 * nn);
+    BEM_ALLOC(d.egeo, kEgeo * nn);
     BEM_ALLOC(d.type, nn);
     BEM_ALLOC(d.sigma, nn);
     BEM_ALLOC(m->w.cell_cnt, kCells);

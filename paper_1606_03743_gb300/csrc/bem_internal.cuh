@@ -52,6 +52,11 @@ constexpr int kNodeRecs = 3;
 constexpr int kMaxChunks = BEM_MAX_CHUNKS;
 constexpr int kChunkMinElements = BEM_CHUNK_MIN;
 
+// Element geometry of the analytic near field (FP64, per element): the unit
+// normal n of the corners' plane, for each edge k (corner k to k + 1) its unit
+// tangent t_k and in-plane outward normal m_k = t_k x n, and the mean side.
+constexpr int kEgeo = 28;  // 3 + 4 x 6 + 1 (triangles leave the fourth edge zero)
+
 struct MeshDev {
     int n = 0;
     // mixed path records (float4, 64 B per element)
@@ -65,6 +70,7 @@ struct MeshDev {
     double* fr = nullptr;     // [n][6] e0, e1 (FP64)
     double* geo = nullptr;    // [n][2] L, area
     double* verts = nullptr;  // [n][12] corners as given
+    double* egeo = nullptr;   // [n][kEgeo] near field: unit normal, per edge unit tangent and outward normal, mean side
     int* type = nullptr;      // [n]
     double* sigma = nullptr;  // [n] (linear density: the value at the centroid)
     double* slope = nullptr;  // [n][2] linear density: d sigma / d alpha, d sigma / d beta (bem_set_sigma_linear)

@@ -33,33 +33,30 @@ __device__ __forceinline__ D3 cross(D3 a, D3 b) {
 }
 __device__ __forceinline__ D3 scale(D3 a, double s) { return D3{a.x * s, a.y * s, a.z * s}; }
 
-// Signed solid angle of triangle (a, b, c) (relative positions from P), with
-// the sign of h for a triangle counter-clockwise about the normal.
-__device__ double solid_angle(D3 a, D3 b, D3 c) {
-    const double la = sqrt(dot(a, a)), lb = sqrt(dot(b, b)), lc = sqrt(dot(c, c));
+// Signed solid angle of triangle (a, b, c) (relative positions from P, at
+// distances la, lb, lc), with the sign of h for a triangle counter-clockwise
+// about the normal.
+__device__ double solid_angle(D3 a, D3 b, D3 c, double la, double lb, double lc) {
     const double trip = dot(a, cross(b, c));  // = -2 area h
     const double den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
     return -2.0 * atan2(trip, den);
 }
 
 // phi and E (unit sigma, without 1/(4 pi eps0)) of element with corners V
-// (3 for a triangle, 4 for a rectangle) at P.
-__device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double out[4]) {
+// (3 for a triangle, 4 for a rectangle) at P; G: the element's normal, edge
+// tangents and outward normals and mean side (kEgeo doubles, from bem_create).
+__device__ void polygon_field(int nv, const double* __restrict__ V, const double* __restrict__ G, D3 P,
+                              double out[4]) {
     D3 c[4];
     for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);  // corners relative to P
-    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
-    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    const D3 nrm{G[0], G[1], G[2]};
     const double h = -dot(c[0], nrm);  // (P - V0)·n
-    double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0, perim = 0.0;
+    double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
     double r[4];
     for (int k = 0; k < nv; ++k) r[k] = sqrt(dot(c[k], c[k]));
     for (int k = 0; k < nv; ++k) {
         const int k2 = (k + 1 == nv) ? 0 : k + 1;
-        D3 t = sub(c[k2], c[k]);
-        const double len = sqrt(dot(t, t));
-        perim += len;
-        t = scale(t, 1.0 / len);
-        const D3 m = cross(t, nrm);
+        const D3 t{G[3 + 6 * k], G[4 + 6 * k], G[5 + 6 * k]}, m{G[6 + 6 * k], G[7 + 6 * k], G[8 + 6 * k]};
         const double s1 = dot(c[k], t), s2 = dot(c[k2], t);
         const double d = dot(c[k], m);
         double num, den;
@@ -85,9 +82,9 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, D3 P, double
     // such as its centroid, counts as on it whatever the rounding of h): h Omega = 0, and on the
     // element the mean of both sides of the normal-field jump (0)
     double om = 0.0;
-    if (fabs(h) > 1e-12 * (perim / nv)) {
-        if (nv == 3) om = solid_angle(c[0], c[1], c[2]);
-        else om = solid_angle(c[0], c[1], c[3]) + solid_angle(c[1], c[2], c[3]);
+    if (fabs(h) > 1e-12 * G[27]) {
+        if (nv == 3) om = solid_angle(c[0], c[1], c[2], r[0], r[1], r[2]);
+        else om = solid_angle(c[0], c[1], c[3], r[0], r[1], r[3]) + solid_angle(c[1], c[2], c[3], r[1], r[2], r[3]);
     }
     out[0] = phi - h * om;
     out[1] = fma(nrm.x, om, ex);
@@ -262,9 +259,10 @@ __global__ void k_finalize_grad(int n, const int* __restrict__ perm, const doubl
 // (the in-plane divergence theorem on grad R = w / R, grad (1/R) = -w / R^3
 // and on w / R; rho_e^2 = d_e^2 + h^2 is the squared distance of P from the
 // edge line).
-__device__ void polygon_field_lin(int nv, const double* __restrict__ V, D3 P, double sc, D3 g, D3 C, double out[4]) {
+__device__ void polygon_field_lin(int nv, const double* __restrict__ V, const double* __restrict__ G, D3 P, double sc, D3 g,
+                                  D3 C, double out[4]) {
     double f0[4];
-    polygon_field(nv, V, P, f0);
+    polygon_field(nv, V, G, P, f0);
     D3 c[4];
     for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
     D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
@@ -332,10 +330,11 @@ __device__ __forceinline__ D3 hmul(const double* H, D3 x) {
 // w = d_e m_e + s t_e on the edge); then
 //   phi = sP I0 + gP . int w / R dA + (H : int w w^T / R dA) / 2
 //   E   = sP E0 + [linear terms with gP] + [h n (H : int w w^T / R^3 dA) - int (w^T H w) w / R^3 dA] / 2.
-__device__ void polygon_field_quad(int nv, const double* __restrict__ V, D3 P, double sc, D3 g, const double* H, D3 C,
+__device__ void polygon_field_quad(int nv, const double* __restrict__ V, const double* __restrict__ G, D3 P, double sc, D3 g,
+                                   const double* H, D3 C,
                                    double out[4]) {
     double f0[4];
-    polygon_field(nv, V, P, f0);
+    polygon_field(nv, V, G, P, f0);
     D3 c[4];
     for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
     D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
@@ -486,7 +485,8 @@ __device__ D3 edge_density_field(D3 c1, D3 c2, D3 P, const Density& dn) {
 //   dE/dtau = E[d sigma / dtau] - sum_e (tau.m_e) int_e sigma (P - Q) / R^3 ds,
 // with E[d sigma / dtau] the field of the linear density tau.g + (H tau).(Q - C).  The
 // normal column follows from the symmetry of the tensor and its zero trace off the element.
-__device__ void polygon_grad_var(int nv, const double* __restrict__ V, D3 P, const Density& dn, double out[6]) {
+__device__ void polygon_grad_var(int nv, const double* __restrict__ V, const double* __restrict__ G, D3 P, const Density& dn,
+                                 double out[6]) {
     D3 c[4];
     for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
     D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
@@ -498,7 +498,7 @@ __device__ void polygon_grad_var(int nv, const double* __restrict__ V, D3 P, con
     D3 col[3];
     for (int q = 0; q < 2; ++q) {
         double f[4];
-        polygon_field_lin(nv, V, P, dot(tau[q], dn.g), hmul(dn.H, tau[q]), dn.C, f);
+        polygon_field_lin(nv, V, G, P, dot(tau[q], dn.g), hmul(dn.H, tau[q]), dn.C, f);
         D3 v{f[1], f[2], f[3]};
         for (int k = 0; k < nv; ++k) {
             const int k2 = (k + 1 == nv) ? 0 : k + 1;
@@ -541,7 +541,7 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
                             const int* __restrict__ type, const double* __restrict__ verts,
                             const double* __restrict__ sigma, const double* __restrict__ slope,
                             const double* __restrict__ curv, const double* __restrict__ fr,
-                            const double* __restrict__ cen, double4* __restrict__ gval) {
+                            const double* __restrict__ cen, const double* __restrict__ egeo, double4* __restrict__ gval) {
     const unsigned long long n = min(counters[0], cap);
     auto slot_of = [&](const int4 r) { return near_slot(r, near_off, near_row, near_rows, n_chunks, chunk_len); };
     for_each_near_pair(rec, n, pts, perm, nb, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
@@ -553,7 +553,7 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
         if (slope) {
             Density dn;
             element_density(el, sg, slope, curv, fr, cen, dn);
-            polygon_grad_var(nv, verts + 12 * (size_t)el, P, dn, f);
+            polygon_grad_var(nv, verts + 12 * (size_t)el, egeo + (size_t)kEgeo * el, P, dn, f);
             sg = 1.0;
         } else {
             polygon_grad(nv, verts + 12 * (size_t)el, P, f);
@@ -572,7 +572,7 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
                             const int* __restrict__ type, const double* __restrict__ verts,
                             const double* __restrict__ sigma, const double* __restrict__ slope,
                             const double* __restrict__ curv, const double* __restrict__ fr,
-                            const double* __restrict__ cen, double4* __restrict__ val) {
+                            const double* __restrict__ cen, const double* __restrict__ egeo, double4* __restrict__ val) {
     const unsigned long long n = min(counters[0], cap);
     auto slot_of = [&](const int4 r) { return near_slot(r, near_off, near_row, near_rows, n_chunks, chunk_len); };
     for_each_near_pair(rec, n, pts, perm, nb, slot_of, [&](const int4 r, int k, const D3 P, unsigned long long slot) {
@@ -584,11 +584,12 @@ __global__ void k_near_eval(const int4* __restrict__ rec, const unsigned long lo
         if (slope) {
             Density dn;
             element_density(el, sg, slope, curv, fr, cen, dn);
-            if (curv) polygon_field_quad(nv, verts + 12 * (size_t)el, P, dn.sc, dn.g, dn.H, dn.C, f);
-            else polygon_field_lin(nv, verts + 12 * (size_t)el, P, dn.sc, dn.g, dn.C, f);
+            const double* G = egeo + (size_t)kEgeo * el;
+            if (curv) polygon_field_quad(nv, verts + 12 * (size_t)el, G, P, dn.sc, dn.g, dn.H, dn.C, f);
+            else polygon_field_lin(nv, verts + 12 * (size_t)el, G, P, dn.sc, dn.g, dn.C, f);
             sg = 1.0;
         } else {
-            polygon_field(nv, verts + 12 * (size_t)el, P, f);
+            polygon_field(nv, verts + 12 * (size_t)el, egeo + (size_t)kEgeo * el, P, f);
         }
         val[slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
     });
@@ -633,14 +634,14 @@ __global__ void k_finalize(int n, const int* n_dev, const int* __restrict__ perm
 
 __global__ void k_near_assemble(const int4* __restrict__ rec, const unsigned long long* counters,
                                 unsigned long long cap, const NearBounds nb, const double* __restrict__ pts, const int* __restrict__ perm,
-                                const int* __restrict__ type, const double* __restrict__ verts, int n_el, double kc,
-                                double* __restrict__ A) {
+                                const int* __restrict__ type, const double* __restrict__ verts,
+                                const double* __restrict__ egeo, int n_el, double kc, double* __restrict__ A) {
     const unsigned long long n = min(counters[0], cap);
     auto no_slot = [](const int4) { return 0ull; };
     for_each_near_pair(rec, n, pts, perm, nb, no_slot, [&](const int4 r, int k, const D3 P, unsigned long long) {
         const int el = r.y + k;
         double f[4];
-        polygon_field(type[el] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)el, P, f);
+        polygon_field(type[el] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)el, egeo + (size_t)kEgeo * el, P, f);
         A[(size_t)perm[r.x] * n_el + el] = kc * f[0];
     });
 }
@@ -648,11 +649,12 @@ __global__ void k_near_assemble(const int4* __restrict__ rec, const unsigned lon
 // Self potential of each element at its own centroid (unit sigma), times kc:
 // the diagonal of the collocation matrix at the centroids.
 __global__ void k_self_potential(int n, const int* __restrict__ type, const double* __restrict__ verts,
-                                 const double* __restrict__ cen, double kc, double* __restrict__ out) {
+                                 const double* __restrict__ egeo, const double* __restrict__ cen, double kc,
+                                 double* __restrict__ out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double f[4];
-    polygon_field(type[j] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)j,
+    polygon_field(type[j] == BEM_RECTANGLE ? 4 : 3, verts + 12 * (size_t)j, egeo + (size_t)kEgeo * j,
                   D3{cen[3 * j], cen[3 * j + 1], cen[3 * j + 2]}, f);
     out[j] = kc * f[0];
 }
@@ -662,7 +664,7 @@ __global__ void k_self_potential(int n, const int* __restrict__ type, const doub
 int launch_self_potential(bem_mesh* m, double* out, cudaStream_t s) {
     const int n = m->d.n;
     if (n == 0) return BEM_OK;
-    k_self_potential<<<(n + 255) / 256, 256, 0, s>>>(n, m->d.type, m->d.verts, m->d.cen, m->kc, out);
+    k_self_potential<<<(n + 255) / 256, 256, 0, s>>>(n, m->d.type, m->d.verts, m->d.egeo, m->d.cen, m->kc, out);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
@@ -680,7 +682,7 @@ int launch_near_eval(bem_mesh* m, const double* pts, const int* perm, int n_pts,
                                         near_bounds(m), pts, perm, w.near_off,
                                         w.near_row, w.near_rows, m->n_chunks, m->chunk_len, m->d.type, m->d.verts,
                                         sigma, slope, eval_curv(m, slope),
-                                        m->d.fr, m->d.cen, w.near_val);
+                                        m->d.fr, m->d.cen, m->d.egeo, w.near_val);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
@@ -703,7 +705,7 @@ int launch_near_grad(bem_mesh* m, const double* pts, const int* perm, const doub
                                         near_bounds(m), gcap, pts, perm,
                                         w.near_off, w.near_row, w.near_rows, m->n_chunks, m->chunk_len, m->d.type,
                                         m->d.verts, sigma, slope,
-                                        eval_curv(m, slope), m->d.fr, m->d.cen, gval);
+                                        eval_curv(m, slope), m->d.fr, m->d.cen, m->d.egeo, gval);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;
@@ -724,7 +726,7 @@ int launch_near_assemble(bem_mesh* m, const double* pts, const int* perm, double
     Work& w = m->w;
     k_near_assemble<<<152 * 8, kNearThreads, 0, s>>>(w.near_rec, w.counters, (unsigned long long)w.cap_near,
                                             near_bounds(m), pts, perm,
-                                            m->d.type, m->d.verts, m->d.n, m->kc, A);
+                                            m->d.type, m->d.verts, m->d.egeo, m->d.n, m->kc, A);
     BEM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return BEM_OK;

@@ -92,6 +92,29 @@ __global__ void k_prep(int n, const int* __restrict__ type, const double* __rest
     d.type[j] = ty;
     d.sigma[j] = sigma[j];
     for (int k = 0; k < 12; ++k) d.verts[12 * (size_t)j + k] = k < 3 * nv ? v[k] : 0.0;
+    {
+        // near-field geometry: the unit normal, per edge the unit tangent and the in-plane outward
+        // normal, the mean side
+        double* g = d.egeo + (size_t)kEgeo * j;
+        const V3 c0 = ld3(v), c1 = ld3(v + 3), c2 = ld3(v + 6);
+        V3 nrm = cross(c1 - c0, c2 - c0);
+        nrm = (1.0 / len(nrm)) * nrm;
+        g[0] = nrm.x; g[1] = nrm.y; g[2] = nrm.z;
+        double perim = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            V3 t = {0, 0, 0}, m = {0, 0, 0};
+            if (k < nv) {
+                t = ld3(v + 3 * ((k + 1) % nv)) - ld3(v + 3 * k);
+                const double l = len(t);
+                perim += l;
+                t = (1.0 / l) * t;
+                m = cross(t, nrm);
+            }
+            g[3 + 6 * k] = t.x; g[4 + 6 * k] = t.y; g[5 + 6 * k] = t.z;
+            g[6 + 6 * k] = m.x; g[7 + 6 * k] = m.y; g[8 + 6 * k] = m.z;
+        }
+        g[27] = perim / nv;
+    }
     d.cen[3 * j] = cen.x; d.cen[3 * j + 1] = cen.y; d.cen[3 * j + 2] = cen.z;
     d.fr[6 * j] = e0.x; d.fr[6 * j + 1] = e0.y; d.fr[6 * j + 2] = e0.z;
     d.fr[6 * j + 3] = e1.x; d.fr[6 * j + 4] = e1.y; d.fr[6 * j + 5] = e1.z;
