@@ -33,13 +33,21 @@ __device__ __forceinline__ D3 cross(D3 a, D3 b) {
 }
 __device__ __forceinline__ D3 scale(D3 a, double s) { return D3{a.x * s, a.y * s, a.z * s}; }
 
+// Van Oosterom and Strackee: the solid angle of triangle (a, b, c) is
+// -2 atan2(y, x) with y = a.(b x c) and x = |a||b||c| + (a.b)|c| + (a.c)|b| + (b.c)|a|.
+__device__ __forceinline__ void solid_angle_args(D3 a, D3 b, D3 c, double la, double lb, double lc, double& y,
+                                                 double& x) {
+    y = dot(a, cross(b, c));  // = -2 area h
+    x = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
+}
+
 // Signed solid angle of triangle (a, b, c) (relative positions from P, at
 // distances la, lb, lc), with the sign of h for a triangle counter-clockwise
 // about the normal.
 __device__ double solid_angle(D3 a, D3 b, D3 c, double la, double lb, double lc) {
-    const double trip = dot(a, cross(b, c));  // = -2 area h
-    const double den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
-    return -2.0 * atan2(trip, den);
+    double y, x;
+    solid_angle_args(a, b, c, la, lb, lc, y, x);
+    return -2.0 * atan2(y, x);
 }
 
 // phi and E (unit sigma, without 1/(4 pi eps0)) of element with corners V
@@ -84,7 +92,16 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, const double
     double om = 0.0;
     if (fabs(h) > 1e-12 * G[27]) {
         if (nv == 3) om = solid_angle(c[0], c[1], c[2], r[0], r[1], r[2]);
-        else om = solid_angle(c[0], c[1], c[3], r[0], r[1], r[3]) + solid_angle(c[1], c[2], c[3], r[1], r[2], r[3]);
+        else {
+            // the rectangle's two triangles: their half-angles add up as the arguments of the
+            // complex numbers (x1 + i y1)(x2 + i y2); one atan2 does while the sum stays within
+            // +-pi/2 (real part positive), away from atan2's branch cut
+            double y1, x1, y2, x2;
+            solid_angle_args(c[0], c[1], c[3], r[0], r[1], r[3], y1, x1);
+            solid_angle_args(c[1], c[2], c[3], r[1], r[2], r[3], y2, x2);
+            const double xr = fma(x1, x2, -y1 * y2), yr = fma(y1, x2, y2 * x1);
+            om = xr > 0.0 ? -2.0 * atan2(yr, xr) : -2.0 * (atan2(y1, x1) + atan2(y2, x2));
+        }
     }
     out[0] = phi - h * om;
     out[1] = fma(nrm.x, om, ex);
