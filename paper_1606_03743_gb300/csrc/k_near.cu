@@ -113,11 +113,9 @@ __device__ void polygon_field(int nv, const double* __restrict__ V, const double
 // = -rho (u2/R2 - u1/R1) / |rho|^2 + t (1/R2 - 1/R1), with t the unit tangent,
 // u_k = (V_k - P)·t, rho = (V1 - P) - u1 t; the differences are rewritten as
 // quotients without cancellation.  A point on the closed edge gives 0.
-__device__ D3 edge_line_field(D3 c1, D3 c2) {  // corners relative to P
-    D3 t = sub(c2, c1);
-    t = scale(t, 1.0 / sqrt(dot(t, t)));
+// (corners c1, c2 relative to P at distances R1, R2; t the edge's unit tangent)
+__device__ D3 edge_line_field(D3 c1, D3 c2, D3 t, double R1, double R2) {
     const double u1 = dot(c1, t), u2 = dot(c2, t);
-    const double R1 = sqrt(dot(c1, c1)), R2 = sqrt(dot(c2, c2));
     const D3 rho = sub(c1, scale(t, u1));
     const double rho2 = dot(rho, rho);
     if (R1 == 0.0 || R2 == 0.0) return D3{0.0, 0.0, 0.0};
@@ -134,19 +132,22 @@ __device__ D3 edge_line_field(D3 c1, D3 c2) {  // corners relative to P
 // 1/(4 pi eps0)) of the polygon at P, from the decomposition above: the
 // gradient of l_e is -J_e and that of Omega is -sum_e t_e x J_e, so
 //   dE/dx = -sum_e m_e J_e^T - n (sum_e t_e x J_e)^T.
-__device__ void polygon_grad(int nv, const double* __restrict__ V, D3 P, double out[6]) {
+// Eg: the element's normal, edge tangents and outward normals (kEgeo doubles, from bem_create).
+__device__ void polygon_grad(int nv, const double* __restrict__ V, const double* __restrict__ Eg, D3 P,
+                             double out[6]) {
     D3 c[4];
-    for (int k = 0; k < nv; ++k) c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
-    D3 nrm = cross(sub(c[1], c[0]), sub(c[2], c[0]));
-    nrm = scale(nrm, 1.0 / sqrt(dot(nrm, nrm)));
+    double r[4];
+    for (int k = 0; k < nv; ++k) {
+        c[k] = sub(D3{V[3 * k], V[3 * k + 1], V[3 * k + 2]}, P);
+        r[k] = sqrt(dot(c[k], c[k]));
+    }
+    const D3 nrm{Eg[0], Eg[1], Eg[2]};
     double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     D3 w{0.0, 0.0, 0.0};
     for (int k = 0; k < nv; ++k) {
         const int k2 = (k + 1 == nv) ? 0 : k + 1;
-        D3 t = sub(c[k2], c[k]);
-        t = scale(t, 1.0 / sqrt(dot(t, t)));
-        const D3 m = cross(t, nrm);
-        const D3 J = edge_line_field(c[k], c[k2]);
+        const D3 t{Eg[3 + 6 * k], Eg[4 + 6 * k], Eg[5 + 6 * k]}, m{Eg[6 + 6 * k], Eg[7 + 6 * k], Eg[8 + 6 * k]};
+        const D3 J = edge_line_field(c[k], c[k2], t, r[k], r[k2]);
         const double mv[3] = {m.x, m.y, m.z}, Jv[3] = {J.x, J.y, J.z};
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) G[a][b] = fma(-mv[a], Jv[b], G[a][b]);
@@ -573,7 +574,7 @@ __global__ void k_near_grad(const int4* __restrict__ rec, const unsigned long lo
             polygon_grad_var(nv, verts + 12 * (size_t)el, egeo + (size_t)kEgeo * el, P, dn, f);
             sg = 1.0;
         } else {
-            polygon_grad(nv, verts + 12 * (size_t)el, P, f);
+            polygon_grad(nv, verts + 12 * (size_t)el, egeo + (size_t)kEgeo * el, P, f);
         }
         gval[2 * slot] = make_double4(sg * f[0], sg * f[1], sg * f[2], sg * f[3]);
         gval[2 * slot + 1] = make_double4(sg * f[4], sg * f[5], 0.0, 0.0);
