@@ -810,6 +810,14 @@ def assembly(a, bem, torch, peaks):
         bem.bem_matvec(m.handle, x, y)
         torch.cuda.synchronize()
         tm = time.perf_counter() - t0
+        # the product's phases from the library's CUDA events: its far kernel does the assembly's
+        # far pairs (potential only), which lean on the MUFU pipe (one rsqrt per node)
+        m.set_timing(True)
+        bem.bem_matvec(m.handle, x, y)
+        torch.cuda.synchronize()
+        ph = [float(t) for t in m.last_times()]
+        m.set_timing(False)
+        _, rsq_a, _ = algorithmic_work(st)
         nbytes = 8.0 * mesh.n * mesh.n
         out[name] = {"assemble_ms": ta * 1e3, "matrix_write_GBps": nbytes / ta / 1e9,
                      "hbm_frac": nbytes / ta / 1e9 / hbm, "hbm_peak_gbs": hbm, "hbm_peak_note": hbm_note,
@@ -819,7 +827,14 @@ def assembly(a, bem, torch, peaks):
                                    ("DFMA" if prec == bem.FP64 else "FP32 FMA") + " rate"),
                      "entries_per_s": mesh.n * mesh.n / ta, "matvec_ms": tm * 1e3,
                      "matvec_pairs_per_s": mesh.n * mesh.n / tm,
+                     "matvec_phases_ms": {"sort": ph[0], "far": ph[1], "near": ph[2], "finalize": ph[3]},
+                     "matvec_far_pipe_frac": ops_a / (ph[1] * 1e-3) / 1e12 / pipe,
                      "timing": "median of 3 calls, host clock with a device synchronize"}
+        if prec == bem.MIXED:
+            out[name]["matvec_far_mufu_frac"] = rsq_a / (ph[1] * 1e-3) / (peaks["rsqrt"]["tops"] * 1e12)
+            out[name]["mufu_note"] = ("algorithmic rsqrt (one per node of the far pairs) over the product's far-kernel "
+                                      "time, against the measured MUFU rsqrt rate: the potential-only node needs 4 "
+                                      "packed FP32 operations and one rsqrt, so MUFU bounds it")
         # the electrode problem: sphere (triangles) at 1 V, inner cylinder at 0 V
         rhs = torch.from_numpy(np.where(mesh.types == 0, 1.0, 0.0)).to(dev)
         sig = torch.empty(mesh.n, dtype=torch.float64, device=dev)

@@ -642,7 +642,7 @@ __device__ __forceinline__ void nodes2(const float4* __restrict__ nd, int ty, in
         if constexpr (INIT) {
             if (shape == (1 | 3 << 1)) return nodes2_shape<1, 3, true, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc);
             if (shape == (0 | 6 << 1)) return nodes2_shape<0, 6, true, NP, WANT_E, GRAD, INIT>(nd, s, u, v, acc);
-            return nodes2_loop<kNodeUnroll / 2, true, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
+            return nodes2_loop<1, true, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
         }
         return nodes2_loop<1, true, NP, WANT_E, GRAD, INIT>(nd, c, r, s, u, v, acc);
     }
