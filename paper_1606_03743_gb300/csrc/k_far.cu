@@ -28,10 +28,9 @@
 //    adds them back in element order.
 //
 // Arithmetic:
-//  * FP64 path: everything in double precision.  Evaluation and assembly use
-//    the frame form below (r_i^2 = s + |o_i|^2 + A_i u + B_i v, the field
-//    rebuilt per element, rectangle nodes in pairs o, -o), the field
-//    gradient takes P - Q_i node by node.
+//  * FP64 path: everything in double precision, in the frame form below
+//    (r_i^2 = s + |o_i|^2 + A_i u + B_i v, the field or its gradient rebuilt
+//    per element, rectangle nodes in pairs o, -o).
 //  * Mixed path: points and centroids are split into FP32 hi + lo parts with
 //    the hi parts on one power-of-two grid fixed by the mesh, so that in
 //    d = P - C = (P_hi - C_hi) + (P_lo - C_lo) the first difference is exact
@@ -339,37 +338,71 @@ __device__ __forceinline__ void nodes64(const double4* __restrict__ nd, int ty, 
     }
 }
 
-// Field gradient of one point charge (offset o, charge o.w) at the PT points
-// of a lane: g += q (I / r^3 - 3 r r^T / r^5), components (xx, yy, zz, xy,
-// xz, yz) of dE_i / dx_j (the point-charge derivatives of Sec. 7).  MASKED as
-// node(): point q's charge is scaled by mq[q].
-template <typename R, typename R4, int PT, bool MASKED>
-__device__ __forceinline__ void node_grad(const R4 o, const R (&dx)[PT], const R (&dy)[PT], const R (&dz)[PT],
-                                          R (&g)[PT][6], const R (&mq)[PT]) {
-#pragma unroll
-    for (int q = 0; q < PT; ++q) {
-        const R rx = dx[q] - o.x, ry = dy[q] - o.y, rz = dz[q] - o.z;
-        const R r2 = fmad(rx, rx, fmad(ry, ry, rz * rz));
-        R wq = o.w;
-        if (MASKED) wq *= mq[q];
-        const R inv = rsq(r2), i2 = inv * inv;
-        const R b = wq * inv * i2;   // q_i / r^3
-        const R c = (R)3 * b * i2;   // 3 q_i / r^5
-        const R cx = c * rx, cy = c * ry;
-        g[q][0] = fmad(-cx, rx, g[q][0] + b);
-        g[q][1] = fmad(-cy, ry, g[q][1] + b);
-        g[q][2] = fmad(-c * rz, rz, g[q][2] + b);
-        g[q][3] = fmad(-cx, ry, g[q][3]);
-        g[q][4] = fmad(-cx, rz, g[q][4]);
-        g[q][5] = fmad(-cy, rz, g[q][5]);
-    }
+// ---- FP64 field gradient, frame form (records as node64).  Per point the
+// element's sums are g = (sum b, sum c, sum c A, sum c B, sum c A^2,
+// sum c A B, sum c B^2) with b = w q / r^3, c = w q / r^5, from which the
+// rebuild forms sum w q (I / r^3 - 3 r r^T / r^5) (the point-charge
+// derivatives of Sec. 7), r = d - alpha e0 - beta e1.  Points that must not
+// take part carry s = +inf.
+template <int PT>
+__device__ __forceinline__ void grad64_terms(double A, double B, double w, double inv, double (&g)[7]) {
+    const double i2 = inv * inv, b = w * inv * i2, c = b * i2, ca = c * A, cb = c * B;
+    g[0] += b;
+    g[1] += c;
+    g[2] += ca;
+    g[3] += cb;
+    g[4] = fma(ca, A, g[4]);
+    g[5] = fma(ca, B, g[5]);
+    g[6] = fma(cb, B, g[6]);
 }
 
-template <typename R, typename R4, int PT, bool MASKED>
-__device__ __forceinline__ void nodes_grad(const R4* __restrict__ nd, int n, const R (&dx)[PT], const R (&dy)[PT],
-                                           const R (&dz)[PT], R (&g)[PT][6], const R (&mq)[PT]) {
+template <int PT, bool PAIRS>
+__device__ __forceinline__ void nodes64_grad(const double4* __restrict__ nd, int ty, int shape, const double (&s)[PT],
+                                             const double (&u)[PT], const double (&v)[PT], double (&g)[PT][7]) {
+    const int c = shape & 1, n = c + ((shape >> 1) & 127);
+    int i = 0;
+    if (c) {  // centre node: r^2 = s, no alpha, beta moments
+        const double w = nd[0].w;
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const double inv = rsqrt(s[q]), i2 = inv * inv, b = w * inv * i2;
+            g[q][0] += b;
+            g[q][1] += b * i2;
+        }
+        i = 1;
+    }
+    if (PAIRS && ty == BEM_RECTANGLE) {
+        // nodes o, -o: b and c add up, the odd moments take c_+ - c_-, the even ones the sum
 #pragma unroll 2
-    for (int i = 0; i < n; ++i) node_grad<R, R4, PT, MASKED>(nd[i], dx, dy, dz, g, mq);
+        for (; i < n; ++i) {
+            const double4 o = nd[i];
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                const double t = s[q] + o.z, m = fma(o.x, u[q], o.y * v[q]);
+                const double ip = rsqrt(t + m), im = rsqrt(t - m);
+                const double i2p = ip * ip, i2m = im * im;
+                const double bp = o.w * ip * i2p, bm = o.w * im * i2m, cp = bp * i2p, cm = bm * i2m;
+                const double cs = cp + cm, cd = cp - cm, ta = cs * o.x, tb = cs * o.y;
+                g[q][0] += bp + bm;
+                g[q][1] += cs;
+                g[q][2] = fma(cd, o.x, g[q][2]);
+                g[q][3] = fma(cd, o.y, g[q][3]);
+                g[q][4] = fma(ta, o.x, g[q][4]);
+                g[q][5] = fma(ta, o.y, g[q][5]);
+                g[q][6] = fma(tb, o.y, g[q][6]);
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (; i < n; ++i) {
+            const double4 o = nd[i];
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                const double r2 = fma(o.x, u[q], fma(o.y, v[q], s[q] + o.z));
+                grad64_terms<PT>(o.x, o.y, o.w, rsqrt(r2), g[q]);
+            }
+        }
+    }
 }
 
 // ---- mixed path: two field points per packed f32x2 operation
@@ -843,9 +876,6 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
 
     static_assert(F64 || PT % 2 == 0, "the mixed path works on point pairs");
     constexpr int NP = F64 ? 1 : PT / 2;  // point pairs of a lane (mixed path)
-    R ones[PT];
-#pragma unroll
-    for (int q = 0; q < PT; ++q) ones[q] = (R)1;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(p.work, 1);
@@ -1031,8 +1061,7 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                 else ty = __float_as_int(ws.qt[e].y);
 
                 if constexpr (F64) {
-                    // ---------------- FP64 path: d = P - C; the field gradient takes P - Q_i = d - o_i
-                    // node by node, evaluation and assembly the frame form (node64)
+                    // ---------------- FP64 path: d = P - C, the frame form (node64, nodes64_grad)
                     const R4 c = ws.c[e];
                     R dx[PT], dy[PT], dz[PT];
 #pragma unroll
@@ -1040,8 +1069,8 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         dx[q] = px[q] - c.x; dy[q] = py[q] - c.y; dz[q] = pz[q] - c.z;
                     }
                     constexpr bool kGrad = MODE == 2;
-                    // varying densities and the gradient: the two nodes of a rectangle's pair as two records
-                    const bool split = (VARY || kGrad) && ty == BEM_RECTANGLE;
+                    // varying densities: the two nodes of a rectangle's pair as two records
+                    const bool split = VARY && ty == BEM_RECTANGLE;
                     auto rule_shape64 = [&](int r) -> int {
                         const int sh = rs.shape[ty * 5 + r];
                         return split ? shape_c(sh) | shape_r(sh) << 2 : sh;
@@ -1075,31 +1104,35 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                             }
                             const R ox = fmad(al, a.x, be * b.x), oy = fmad(al, a.y, be * b.y), oz = fmad(al, a.z, be * b.z);
                             const R wq = rs.w[st + i] * qi;
-                            if constexpr (kGrad) ws.nd[par][k] = R4{ox, oy, oz, wq};
-                            else ws.nd[par][k] = R4{-2.0 * al, -2.0 * be, fmad(ox, ox, fmad(oy, oy, oz * oz)), wq};
+                            ws.nd[par][k] = R4{-2.0 * al, -2.0 * be, fmad(ox, ox, fmad(oy, oy, oz * oz)), wq};
                         }
                         __syncwarp();
                         return n;
                     };
 
-                    // frame form: s = |d|^2, u = d.e0, v = d.e1; the element's sums (eacc)
+                    // frame form: s = |d|^2, u = d.e0, v = d.e1; the element's sums (eacc, gacc)
                     R sv[PT], uv[PT], vv[PT];
-                    R eacc[PT][4];
-                    if constexpr (!kGrad) {
+                    R eacc[kGrad ? 1 : PT][4], gacc[kGrad ? PT : 1][7];
+                    {
                         const R4 a = ws.e0[e], b = ws.e1[e];
 #pragma unroll
                         for (int q = 0; q < PT; ++q) {
                             sv[q] = fmad(dx[q], dx[q], fmad(dy[q], dy[q], dz[q] * dz[q]));
                             uv[q] = fmad(dx[q], a.x, fmad(dy[q], a.y, dz[q] * a.z));
                             vv[q] = fmad(dx[q], b.x, fmad(dy[q], b.y, dz[q] * b.z));
+                            if constexpr (kGrad) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) eacc[q][k] = (R)0;
+                                for (int k = 0; k < 7; ++k) gacc[q][k] = (R)0;
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) eacc[q][k] = (R)0;
+                            }
                         }
                     }
 
                     if (cd >= 1 && cd <= 5) {
                         const int n = expand(band_rule(cd));
-                        if constexpr (kGrad) nodes_grad<R, R4, PT, false>(ws.nd[par], n, dx, dy, dz, accg, ones);
+                        if constexpr (kGrad) nodes64_grad<PT, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(cd)), sv, uv, vv, gacc);
                         else nodes64<PT, WANT_E, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(cd)), sv, uv, vv, eacc);
                         par ^= 1;
                         if (STATS && lane == 0) {
@@ -1129,25 +1162,12 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                         for (int band = 1; band <= 5; ++band) {
                             if (!(mask & (1u << band))) continue;
                             const int n = expand(band_rule(band));
-                            if constexpr (kGrad) {
-                                // points of other bands: zero charge, parked far from every node
-                                R mq[PT], mx[PT], my[PT], mz[PT];
+                            // points of other bands sit at infinite distance in this pass
+                            R sm[PT];
 #pragma unroll
-                                for (int q = 0; q < PT; ++q) {
-                                    const bool on = bq[q] == band;
-                                    mq[q] = on ? (R)1 : (R)0;
-                                    mx[q] = on ? dx[q] : (R)1e3;
-                                    my[q] = on ? dy[q] : (R)1e3;
-                                    mz[q] = on ? dz[q] : (R)1e3;
-                                }
-                                nodes_grad<R, R4, PT, true>(ws.nd[par], n, mx, my, mz, accg, mq);
-                            } else {
-                                // points of other bands sit at infinite distance in this pass
-                                R sm[PT];
-#pragma unroll
-                                for (int q = 0; q < PT; ++q) sm[q] = bq[q] == band ? sv[q] : (R)INFINITY;
-                                nodes64<PT, WANT_E, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(band)), sm, uv, vv, eacc);
-                            }
+                            for (int q = 0; q < PT; ++q) sm[q] = bq[q] == band ? sv[q] : (R)INFINITY;
+                            if constexpr (kGrad) nodes64_grad<PT, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(band)), sm, uv, vv, gacc);
+                            else nodes64<PT, WANT_E, !VARY>(ws.nd[par], ty, rule_shape64(band_rule(band)), sm, uv, vv, eacc);
                             par ^= 1;
                             if (STATS && lane == 0) atomicAdd(&rs.stat[14], (unsigned long long)n * 32 * PT);
                         }
@@ -1185,6 +1205,35 @@ __global__ void __launch_bounds__(kWarps * 32, BEM_MIN_BLOCKS) k_far(const FarK 
                                 if (check_ok(row >= 0 && row < p.n_pts && b0 + e < p.n_el, p.counters, kCheckMatrix))
                                     p.A[(size_t)row * p.n_el + (b0 + e)] = p.kc * (double)eacc[q][0];
                             }
+                    }
+                    if constexpr (kGrad) {
+                        // the element's sum w q (I / r^3 - 3 r r^T / r^5), r = d - alpha e0 - beta e1:
+                        // with S = sum c, S_a = sum c alpha, ... (alpha = -A / 2), it is
+                        // sum b I - 3 (M d^T + N0 e0^T + N1 e1^T), M = S d - S_a e0 - S_b e1,
+                        // N0 = -S_a d + S_aa e0 + S_ab e1, N1 = -S_b d + S_ab e0 + S_bb e1
+                        const R4 a = ws.e0[e], b = ws.e1[e];
+                        const R f0[3] = {a.x, a.y, a.z}, f1[3] = {b.x, b.y, b.z};
+#pragma unroll
+                        for (int q = 0; q < PT; ++q) {
+                            const R* G = gacc[q];
+                            const R Sa = -0.5 * G[2], Sb = -0.5 * G[3], Saa = 0.25 * G[4], Sab = 0.25 * G[5],
+                                    Sbb = 0.25 * G[6];
+                            const R dv[3] = {dx[q], dy[q], dz[q]};
+                            R M[3], N0[3], N1[3];
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                M[k] = fmad(G[1], dv[k], fmad(-Sa, f0[k], -Sb * f1[k]));
+                                N0[k] = fmad(-Sa, dv[k], fmad(Saa, f0[k], Sab * f1[k]));
+                                N1[k] = fmad(-Sb, dv[k], fmad(Sab, f0[k], Sbb * f1[k]));
+                            }
+                            auto T = [&](int i, int j) { return fmad(M[i], dv[j], fmad(N0[i], f0[j], N1[i] * f1[j])); };
+                            accg[q][0] += fmad(-3.0, T(0, 0), G[0]);
+                            accg[q][1] += fmad(-3.0, T(1, 1), G[0]);
+                            accg[q][2] += fmad(-3.0, T(2, 2), G[0]);
+                            accg[q][3] -= 3.0 * T(0, 1);
+                            accg[q][4] -= 3.0 * T(0, 2);
+                            accg[q][5] -= 3.0 * T(1, 2);
+                        }
                     }
                 } else {
                     // ---------------- mixed path (frame form, point pairs)
