@@ -34,6 +34,20 @@ int64_t bem_test_alloc_count(void);
  * GPU's memory (every entry point rejects it with BEM_ERR_INVALID). */
 int32_t bem_test_ptr_location(const void* p, int32_t dev);
 
+/*
+ * bem_test_rule_records -- the far-field kernels' node records of rule r
+ * (0..4, the 4-, 7-, 12-, 19|17- and 33-point rule) of element type `type`
+ * (BEM_TRIANGLE or BEM_RECTANGLE), as built on the host for the mixed
+ * (precision 1, FP32 values) or the FP64 (precision 0) path: the centre node
+ * first (if the rule has one), then one record per pair of nodes o, -o of
+ * equal weight (rectangles) or one per node (triangles).  Writes one row
+ * (alpha, beta, w, multiplicity) per record to out (at most 33 rows, host
+ * memory), the multiplicity being 2 for a pair and 1 otherwise, and *shape =
+ * centre records | other records << 1.  Returns the number of records, or
+ * BEM_ERR_INVALID for bad arguments.  Needs no GPU.
+ */
+int32_t bem_test_rule_records(int32_t type, int32_t r, int32_t precision, double* out /* 33 x 4 */, int32_t* shape);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@
 #include <type_traits>
 
 #include "bem_internal.cuh"
+#include "bem_test.h"
 
 namespace bem {
 
@@ -1854,3 +1855,27 @@ int launch_far(bem_mesh* m, const FarArgs& a, cudaStream_t s) {
 }
 
 }  // namespace bem
+
+extern "C" int32_t bem_test_rule_records(int32_t type, int32_t r, int32_t precision, double* out, int32_t* shape) {
+    using namespace bem;
+    if ((type != BEM_TRIANGLE && type != BEM_RECTANGLE) || r < 0 || r > 4 || !out || !shape ||
+        (precision != 0 && precision != 1)) {
+        set_error("bem_test_rule_records: bad arguments");
+        return BEM_ERR_INVALID;
+    }
+    float af[2 * kSlots] = {}, bf[2 * kSlots] = {}, wf[2 * kSlots] = {};
+    double ad[2 * kSlots] = {}, bd[2 * kSlots] = {}, wd[2 * kSlots] = {};
+    int rec_start[10], sh[10];
+    const int rc = build_records(rules(), af, bf, wf, ad, bd, wd, rec_start, sh);
+    if (rc) return rc;
+    const int k = type * 5 + r, n = shape_c(sh[k]) + shape_r(sh[k]);
+    for (int i = 0; i < n; ++i) {
+        const int j = type * kSlots + rec_start[k] + i;
+        out[4 * i] = precision ? (double)af[j] : ad[j];
+        out[4 * i + 1] = precision ? (double)bf[j] : bd[j];
+        out[4 * i + 2] = precision ? (double)wf[j] : wd[j];
+        out[4 * i + 3] = (type == BEM_RECTANGLE && !(i == 0 && shape_c(sh[k]))) ? 2.0 : 1.0;
+    }
+    *shape = sh[k];
+    return n;
+}

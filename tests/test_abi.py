@@ -125,6 +125,48 @@ def test_rectangle_rules_centrally_symmetric():
         assert np.allclose(key(o), key(om), rtol=0, atol=1e-15)
 
 
+def _rule_records(type_, r, precision):
+    lib = ctypes.CDLL(bem_build.build())
+    lib.bem_test_rule_records.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
+    lib.bem_test_rule_records.restype = ctypes.c_int32
+    out = np.zeros((33, 4))
+    shape = ctypes.c_int32(0)
+    n = lib.bem_test_rule_records(type_, r, precision, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.byref(shape))
+    assert n > 0
+    return out[:n], shape.value
+
+
+@pytest.mark.parametrize("type_", [0, 1])
+@pytest.mark.parametrize("r", range(5))
+def test_rule_records_reproduce_the_rules(type_, r):
+    """The far kernels' node records (host-built, no GPU): expanded (a pair
+    record stands for o and -o) they are the rule's nodes -- exactly in FP64,
+    to FP32 rounding in the mixed path; the centre node comes first; the
+    mixed path's FP32 weights, pairs counted twice, sum to one as closely as
+    single-ulp changes of the weights allow (Eq. 4.1 keeps each element's
+    charge)."""
+    rule = bem.bem_rule(type_, r)
+    key = lambda a: a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+    for prec in (0, 1):
+        rec, shape = _rule_records(type_, r, prec)
+        c = shape & 1
+        assert len(rec) == c + (shape >> 1)
+        if c:
+            assert rec[0, 0] == 0.0 and rec[0, 1] == 0.0 and rec[0, 3] == 1.0
+        assert set(rec[c:, 3]) == ({2.0} if type_ == 1 else {1.0})
+        nodes = [rec[:, :3]] + [np.stack([-rec[k:k + 1, 0], -rec[k:k + 1, 1], rec[k:k + 1, 2]], 1)
+                                for k in range(len(rec)) if rec[k, 3] == 2.0]
+        nodes = key(np.concatenate(nodes) + 0.0)
+        assert len(nodes) == len(rule)
+        tol = 0.0 if prec == 0 else 1e-7
+        assert np.allclose(nodes, key(rule + 0.0), rtol=tol, atol=tol)
+        if prec == 1:
+            total = float(np.sum(rec[:, 2] * rec[:, 3]))  # exact: FP32 weights summed in FP64
+            assert abs(total - 1.0) <= 2 * np.spacing(np.float32(np.abs(rec[:, 2]).min()))
+
+
 def test_library_default_limits_match_oracle():
     """The library's default DR band limits (bem_default_limits) are the
     oracle's frozen table, which tests/test_oracle_field.py pins against the
