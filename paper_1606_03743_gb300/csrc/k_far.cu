@@ -15,8 +15,9 @@
 //    warp's shared memory and tests, conservatively, whether every point of
 //    the warp lies in one distance-ratio band of that element.
 //  * Per element the warp expands only the rule it needs (lane i computes
-//    node i from the element frame: Eq. 3.2 / Eq. 3.3), as (offset, w_i q)
-//    records in a double-buffered shared-memory slot, then every lane runs
+//    node record i from the element frame: Eq. 3.2 / Eq. 3.3; a record is
+//    one node, or on rectangles the pair of nodes o, -o), as offset and
+//    weight records in a double-buffered shared-memory slot, then every lane runs
 //    the node loop for its PT points reading the records by broadcast.
 //    Elements whose band differs between points of the warp fall back to
 //    per-point bands: the warp runs each band present with the other
@@ -407,7 +408,6 @@ __device__ __forceinline__ void nodes64_grad(const double4* __restrict__ nd, int
 }
 
 // ---- mixed path: two field points per packed f32x2 operation
-__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
