@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--large-points", type=int, default=4_000_000)
     ap.add_argument("--large-fp64-points", type=int, default=32768)
     ap.add_argument("--large-oracle-points", type=int, default=2048)
+    ap.add_argument("--band-fit", action="store_true",
+                    help="instead of the benchmark: time the far kernel with every far pair forced into one rule, "
+                         "for each rule, and fit its cycles per node and per (warp, element)")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -264,6 +267,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         return run_reference(a, rank, world)
+    if a.band_fit:
+        return band_fit(a)
 
     import torch
     import paper_1606_03743_gb300 as bem
@@ -855,6 +860,58 @@ def assembly(a, bem, torch, peaks):
         m.close()
     del A
     return out
+
+
+def band_fit(a) -> int:
+    """The far kernel (mixed, phi and E) on the benchmark workload with every
+    far pair forced into one rule by the band limits (the near limit kept),
+    for each of the five rules: its CUDA-event time, the (warp, element)
+    pairs and node evaluations from the kernel's statistics, and a
+    least-squares fit of SM sub-partition cycles per (warp, element) pair
+    against the nodes per pair: slope = cycles per node (128 points of a
+    warp), intercept = the per-(warp, element) work around the node loop."""
+    import torch
+    import paper_1606_03743_gb300 as bem
+
+    dev = torch.device("cuda", 0)
+    mesh = synth.coax_mesh(seed=2)
+    p_d = torch.from_numpy(synth.coax_points(seed=2, n=a.points)).to(dev)
+    phi = torch.empty(a.points, dtype=torch.float64, device=dev)
+    E = torch.empty((a.points, 3), dtype=torch.float64, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    near = bem.bem_default_limits()[:, 0]
+    rows = []
+    for band in range(1, 6):  # band b: the rule with 33, 19|17, 12, 7, 4 nodes
+        lim = np.zeros((2, 5))
+        for t in range(2):
+            for k in range(5):
+                lim[t, k] = near[t] * (1.0 + 1e-9 * k) if k < band else 1e30 * (k + 1)
+        m = bem.Mesh(torch.from_numpy(mesh.types).to(dev), torch.from_numpy(mesh.verts).to(dev),
+                     torch.from_numpy(mesh.sigma).to(dev), precision=bem.MIXED, limits=lim)
+        m.set_stats(True)
+        bem.bem_eval(m.handle, p_d, phi, E)
+        st = m.last_stats()
+        m.set_stats(False)
+        m.set_timing(True)
+        far = []
+        for _ in range(3):
+            bem.bem_eval(m.handle, p_d, phi, E)
+            torch.cuda.synchronize()
+            far.append(float(m.last_times()[1]))
+        m.close()
+        wel = float(st[13] + st[14])  # (warp, element) pairs: one band, per-point bands
+        nodes = float(st[15]) / (32 * 4) / wel  # node evaluations per (warp, element) pair
+        cyc = statistics.median(far) * 1e-3 * 2070e6 * sms * 4 / wel  # sub-partition cycles per pair
+        rows.append({"band": band, "far_ms": statistics.median(far), "warp_element_pairs": wel,
+                     "nodes_per_pair": nodes, "cycles_per_pair": cyc})
+    x = np.array([r["nodes_per_pair"] for r in rows])
+    y = np.array([r["cycles_per_pair"] for r in rows])
+    slope, icpt = np.polyfit(x, y, 1)
+    print(json.dumps({"mode": "band_fit", "workload": WORKLOAD, "n_points": a.points, "rules": rows,
+                      "fit": {"cycles_per_node": float(slope), "cycles_per_warp_element": float(icpt),
+                              "note": "cycles of one SM sub-partition at 2070 MHz per (warp, element) pair of "
+                                      "128 points; least squares over the five rules"}}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
